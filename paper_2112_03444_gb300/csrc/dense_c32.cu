@@ -1,0 +1,20 @@
+// Dense total-degree tracking kernels: degree 3, mixed FP32/FP64, n = 1..8.
+#include "dense_kernel.cuh"
+
+namespace hc {
+
+KernelRef dense_ref_d3_32(int n) {
+  switch (n) {
+    case 1: return dense_ref<3, true, 1>();
+    case 2: return dense_ref<3, true, 2>();
+    case 3: return dense_ref<3, true, 3>();
+    case 4: return dense_ref<3, true, 4>();
+    case 5: return dense_ref<3, true, 5>();
+    case 6: return dense_ref<3, true, 6>();
+    case 7: return dense_ref<3, true, 7>();
+    case 8: return dense_ref<3, true, 8>();
+    default: return KernelRef{nullptr, 0};
+  }
+}
+
+}  // namespace hc

@@ -1,0 +1,20 @@
+// Dense total-degree tracking kernels: degree 3, FP64, n = 1..8.
+#include "dense_kernel.cuh"
+
+namespace hc {
+
+KernelRef dense_ref_d3_64(int n) {
+  switch (n) {
+    case 1: return dense_ref<3, false, 1>();
+    case 2: return dense_ref<3, false, 2>();
+    case 3: return dense_ref<3, false, 3>();
+    case 4: return dense_ref<3, false, 4>();
+    case 5: return dense_ref<3, false, 5>();
+    case 6: return dense_ref<3, false, 6>();
+    case 7: return dense_ref<3, false, 7>();
+    case 8: return dense_ref<3, false, 8>();
+    default: return KernelRef{nullptr, 0};
+  }
+}
+
+}  // namespace hc

@@ -1,0 +1,24 @@
+// Dense total-degree tracking kernels: degree 2, FP64, n = 1..12.
+#include "dense_kernel.cuh"
+
+namespace hc {
+
+KernelRef dense_ref_d2_64(int n) {
+  switch (n) {
+    case 1: return dense_ref<2, false, 1>();
+    case 2: return dense_ref<2, false, 2>();
+    case 3: return dense_ref<2, false, 3>();
+    case 4: return dense_ref<2, false, 4>();
+    case 5: return dense_ref<2, false, 5>();
+    case 6: return dense_ref<2, false, 6>();
+    case 7: return dense_ref<2, false, 7>();
+    case 8: return dense_ref<2, false, 8>();
+    case 9: return dense_ref<2, false, 9>();
+    case 10: return dense_ref<2, false, 10>();
+    case 11: return dense_ref<2, false, 11>();
+    case 12: return dense_ref<2, false, 12>();
+    default: return KernelRef{nullptr, 0};
+  }
+}
+
+}  // namespace hc

@@ -1,0 +1,178 @@
+// Total-degree homotopy for dense systems of degree 2 or 3 (every monomial of
+// degree <= d present in every equation):
+//   H(x,t) = (1-t) gamma G(x) + t F(x),  G_i = x_i^d - 1        (paper Eq. 1)
+// with the random unit gamma.  Start point k: x_i = exp(2 pi i k_i / d),
+// k_i the i-th base-d digit of k (variable 1 least significant).
+//
+// Evaluation (paper Sec. 6: one Jacobian row per lane, coefficients shared
+// by the paths of a system).  For a dense system the homogenised term tuples
+// of Sec. 6 have a fixed pattern, so they are not stored: row i of dF/dx is
+//   dF_i/dx_j = sum_m D[j][m][i] mu_m(x),   mu = monomials of degree <= d-1,
+// with D the coefficient of mu_m in dF_i/dx_j (exponent multiplicity folded
+// in), and F_i follows from the same partial sums by Euler's identity on each
+// homogeneous part:  F_i = c_i0 + sum_j x_j (a0_j + a1_j / 2 + a2_j / 3),
+// where a_e is the part of dF_i/dx_j built from degree-e monomials.
+//
+// FP64 residuals use the monomial coefficients in nested Horner order
+//   F_i = c0 + sum_j x_j (b_j + sum_{k<=j} x_k (q_jk + sum_{l<=k} r_jkl x_l)),
+// one complex FMA per monomial.
+//
+// Data layout (per instance, lane stride L so that lane i reads D[..][i] and
+// the L lanes of a path read L consecutive complex numbers):
+//   D: [(N+1) slices][MP][L]; slice N entry 0 holds the constant c_i0.
+//   E: [M][L] complex double, nested Horner order.
+#pragma once
+
+#include <type_traits>
+
+#include "hc_device.cuh"
+
+namespace hc {
+
+template <int N, int DEG>
+struct DenseShape {
+  static_assert(DEG == 2 || DEG == 3, "dense evaluator: degree 2 or 3");
+  static constexpr int MP = (DEG == 2) ? (N + 1) : (1 + N + N * (N + 1) / 2);
+  static constexpr int M = (DEG == 2) ? ((N + 1) * (N + 2) / 2) : ((N + 1) * (N + 2) * (N + 3) / 6);
+  // graded-lex index of x_k x_l (k <= l) among the monomials of degree <= 2
+  static constexpr __host__ __device__ int idx2(int k, int l) {
+    return 1 + N + k * N - k * (k - 1) / 2 + (l - k);
+  }
+};
+
+template <int N, int DEG, int L>
+struct DenseTD {
+  using S = DenseShape<N, DEG>;
+  const cx<float>* D32;
+  const cx<double>* D64;
+  const cx<double>* E;
+  cx<double> gamma;
+
+  template <class R>
+  __device__ __forceinline__ const cx<R>* dptr() const;
+
+  template <class R>
+  __device__ __forceinline__ void eval(const cx<R> (&x)[N], int i, R t, R omt, cx<R> (&row)[N + 1],
+                                       cx<R>& H, cx<R>& Ht) const {
+    const cx<R>* D = dptr<R>() + i;
+    cx<R> F = D[(N * S::MP) * L];
+    cx<R> xi = x[0];
+#pragma unroll
+    for (int k = 1; k < N; ++k)
+      if (k == i) xi = x[k];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      const cx<R>* Dj = D + (j * S::MP) * L;
+      const cx<R> a0 = Dj[0];
+      cx<R> a1 = czero<R>();
+#pragma unroll
+      for (int k = 0; k < N; ++k) a1 = cfma(Dj[(1 + k) * L], x[k], a1);
+      if constexpr (DEG == 2) {
+        row[j] = a0 + a1;
+        F = cfma(x[j], a0 + R(0.5) * a1, F);
+      } else {
+        cx<R> a2 = czero<R>();
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+          cx<R> in = czero<R>();
+#pragma unroll
+          for (int l = k; l < N; ++l) in = cfma(Dj[S::idx2(k, l) * L], x[l], in);
+          a2 = cfma(x[k], in, a2);
+        }
+        row[j] = a0 + a1 + a2;
+        F = cfma(x[j], a0 + R(0.5) * a1 + R(1.0 / 3.0) * a2, F);
+      }
+    }
+    // G_i = xi^d - 1, dG_i/dx_i = d xi^(d-1)
+    const cx<R> xi2 = xi * xi;
+    const cx<R> G = (DEG == 2 ? xi2 : xi2 * xi) - mk<R>(R(1), R(0));
+    const cx<R> Gd = R(DEG) * (DEG == 2 ? xi : xi2);
+    const cx<R> gm = cvt<R>(gamma);
+    const cx<R> gG = gm * G;
+    H = t * F + omt * gG;
+    Ht = F - gG;
+    const cx<R> gd = omt * (gm * Gd);
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      row[j] = t * row[j];
+      if (j == i) row[j] = row[j] + gd;
+    }
+  }
+
+  template <bool SCALE>
+  __device__ __forceinline__ void residual64(const cx<double> (&x)[N], int i, double t, double omt,
+                                             cx<double>& H, double& sc) const {
+    const cx<double>* e = E + i;
+    int m = 0;
+    cx<double> F = e[0];
+    double Ssum = SCALE ? cabs2(e[0]) : 0.0;
+    m = 1;
+    cx<double> xi = x[0];
+#pragma unroll
+    for (int k = 1; k < N; ++k)
+      if (k == i) xi = x[k];
+    double ax[N];
+    if (SCALE) {
+#pragma unroll
+      for (int k = 0; k < N; ++k) ax[k] = cabs2(x[k]);
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      cx<double> in = e[m * L];
+      double ins = SCALE ? cabs2(e[m * L]) : 0.0;
+      ++m;
+#pragma unroll
+      for (int k = 0; k <= j; ++k) {
+        if constexpr (DEG == 2) {
+          in = cfma(e[m * L], x[k], in);
+          if (SCALE) ins += cabs2(e[m * L]) * ax[k];
+          ++m;
+        } else {
+          cx<double> in2 = e[m * L];
+          double in2s = SCALE ? cabs2(e[m * L]) : 0.0;
+          ++m;
+#pragma unroll
+          for (int l = 0; l <= k; ++l) {
+            in2 = cfma(e[m * L], x[l], in2);
+            if (SCALE) in2s += cabs2(e[m * L]) * ax[l];
+            ++m;
+          }
+          in = cfma(x[k], in2, in);
+          if (SCALE) ins += ax[k] * in2s;
+        }
+      }
+      F = cfma(x[j], in, F);
+      if (SCALE) Ssum += ax[j] * ins;
+    }
+    const cx<double> xi2 = xi * xi;
+    const cx<double> G = (DEG == 2 ? xi2 : xi2 * xi) - mk<double>(1.0, 0.0);
+    H = t * F + omt * (gamma * G);
+    if (SCALE) {
+      const double axi = cabs2(xi);
+      sc = t * Ssum + omt * (1.0 + (DEG == 2 ? axi * axi : axi * axi * axi));
+    } else {
+      sc = 0.0;
+    }
+  }
+
+  __device__ __forceinline__ cx<double> start(int64_t path, int i) const {
+    int64_t k = path;
+#pragma unroll 1
+    for (int v = 0; v < i; ++v) k /= DEG;
+    const int ki = (int)(k % DEG);
+    double s, c;
+    sincospi(2.0 * (double)ki / (double)DEG, &s, &c);
+    return mk<double>(c, s);
+  }
+};
+
+template <int N, int DEG, int L>
+template <class R>
+__device__ __forceinline__ const cx<R>* DenseTD<N, DEG, L>::dptr() const {
+  if constexpr (std::is_same<R, float>::value)
+    return D32;
+  else
+    return D64;
+}
+
+}  // namespace hc

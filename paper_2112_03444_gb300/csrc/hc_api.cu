@@ -1,0 +1,820 @@
+// Host runtime behind the C-ABI of include/hc.h: problem validation and
+// encoding, device staging, persistent tracking launches, FP64 escalation of
+// failed mixed-precision paths, result summary and the asynchronous poll.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "hc.h"
+#include "kernels.cuh"
+
+namespace hc {
+KernelRef dense_ref_d2_64(int n);
+KernelRef dense_ref_d2_32(int n);
+KernelRef dense_ref_d3_64(int n);
+KernelRef dense_ref_d3_32(int n);
+
+KernelRef dense_kernel(int deg, int n, bool mixed) {
+  if (deg == 2) return mixed ? dense_ref_d2_32(n) : dense_ref_d2_64(n);
+  if (deg == 3) return mixed ? dense_ref_d3_32(n) : dense_ref_d3_64(n);
+  return KernelRef{nullptr, 0};
+}
+}  // namespace hc
+
+using hc::cx;
+
+namespace {
+
+constexpr uint32_t kProblemMagic = 0x48435042u;  // "HCPB"
+constexpr uint32_t kBatchMagic = 0x48434254u;    // "HCBT"
+
+thread_local std::string g_err;
+
+void set_err(const std::string& s) { g_err = s; }
+
+#define HC_CUDA(call)                                                              \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      set_err(std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+      return e_ == cudaErrorMemoryAllocation ? HC_ERR_OOM : HC_ERR_CUDA;           \
+    }                                                                              \
+  } while (0)
+
+// ------------------------------------------------------------------ kernels
+__global__ void stage_dense_kernel(int64_t n_inst, int T, const double2* __restrict__ coef,
+                                   int64_t coef_stride, const int* __restrict__ emap, int ndc,
+                                   const int* __restrict__ dterm, const int* __restrict__ dslot,
+                                   const float* __restrict__ dmult, double2* E, int64_t Es,
+                                   float2* D32, double2* D64, int64_t Ds) {
+  const int64_t per = (int64_t)T + ndc;
+  const int64_t total = n_inst * per;
+  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < total;
+       w += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t inst = w / per;
+    int64_t r = w - inst * per;
+    const double2* c = coef + inst * coef_stride;
+    if (r < T) {
+      E[inst * Es + emap[r]] = c[r];
+    } else {
+      r -= T;
+      const double2 v = c[dterm[r]];
+      const double m = (double)dmult[r];
+      const double2 dv = make_double2(m * v.x, m * v.y);
+      if (D64) D64[inst * Ds + dslot[r]] = dv;
+      if (D32) D32[inst * Ds + dslot[r]] = make_float2((float)dv.x, (float)dv.y);
+    }
+  }
+}
+
+// Batch summary: [0] finite [1] real [2] diverged [3] singular [4] failed
+// [5] accepted steps [6] rejected steps [7] Newton iterations
+__global__ void summarize_kernel(int64_t items, const uint8_t* __restrict__ st,
+                                 const int32_t* __restrict__ steps, unsigned long long* out) {
+  unsigned long long c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < items;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int s = st[i];
+    const int b = s & 0x7f;
+    c[0] += (b == hc::ST_FINITE);
+    c[1] += (b == hc::ST_FINITE) && (s & hc::ST_REAL);
+    c[2] += (b == hc::ST_DIVERGED);
+    c[3] += (b == hc::ST_SINGULAR);
+    c[4] += (b != hc::ST_FINITE && b != hc::ST_DIVERGED && b != hc::ST_SINGULAR);
+    c[5] += (unsigned)steps[i * 3 + 0];
+    c[6] += (unsigned)steps[i * 3 + 1];
+    c[7] += (unsigned)steps[i * 3 + 2];
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    unsigned long long v = c[k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(out + k, v);
+  }
+}
+
+// ------------------------------------------------------------------ helpers
+int binom(int n, int k) {
+  if (k < 0 || k > n) return 0;
+  long long r = 1;
+  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+  return (int)r;
+}
+
+// Graded-lex index of an exponent vector among the monomials of degree <= dmax
+// in n variables (degree 0 first; inside a degree, the sorted variable tuple
+// in lexicographic order).
+int graded_index(int n, const std::vector<int>& vars /* sorted ascending */) {
+  const int deg = (int)vars.size();
+  int idx = 0;
+  for (int e = 0; e < deg; ++e) idx += binom(n + e - 1, e);  // monomials of lower degree
+  // rank of the multiset among combinations_with_replacement(range(n), deg)
+  int prev = 0;
+  for (int p = 0; p < deg; ++p) {
+    for (int v = prev; v < vars[p]; ++v) idx += binom((n - v) + (deg - p - 1) - 1, deg - p - 1);
+    prev = vars[p];
+  }
+  return idx;
+}
+
+struct DeviceBuf {
+  void* p = nullptr;
+};
+
+}  // namespace
+
+// ------------------------------------------------------------------ problem
+struct hc_problem {
+  uint32_t magic = kProblemMagic;
+  int n = 0, T = 0, kind = 0, maxpf = 0, P = 0, device = 0;
+  hc_settings s{};
+  double gamma[2] = {1.0, 0.0};
+  std::vector<int> eq;
+  std::vector<double> coef;  // [T][2]
+  std::vector<uint8_t> exps;
+  std::vector<int> par;
+  std::vector<double> p0, start;
+  int64_t n_start = 0;
+  int64_t paths = 0;
+  // dense total-degree encoding
+  bool dense = false;
+  int deg = 0, MP = 0, M = 0, L = 0;
+  int64_t Dstride = 0, Estride = 0;
+  int* d_emap = nullptr;
+  int ndc = 0;
+  int* d_dterm = nullptr;
+  int* d_dslot = nullptr;
+  float* d_dmult = nullptr;
+  double* d_coef = nullptr;  // default coefficients [T][2]
+};
+
+struct hc_batch {
+  uint32_t magic = kBatchMagic;
+  hc_problem* p = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t evk0 = nullptr, evk1 = nullptr, evk2 = nullptr;  // around the tracking launches
+  int64_t n_inst = 0, items = 0;
+  bool done = false;
+  std::vector<void*> dev;  // device allocations (stream-ordered)
+  unsigned long long* d_ctl = nullptr;
+  unsigned long long* h_ctl = nullptr;  // pinned: [0..7] summary, [8] escalated
+  // host outputs needing a copy at poll time (pageable destinations)
+  struct HostCopy {
+    void* dst;
+    void* pinned;
+    size_t bytes;
+  };
+  std::vector<HostCopy> copies;
+  std::vector<void*> pinned;
+};
+
+namespace {
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+bool is_pinned_host(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
+hc::DevSettings dev_settings(const hc_settings& s) {
+  hc::DevSettings d;
+  d.dt_min = s.dt_min;
+  d.dt_max = s.dt_max;
+  d.dt_init = s.dt_init;
+  d.newton_tol = s.newton_tol;
+  d.newton_tol_fp32 = s.newton_tol_fp32;
+  d.max_first_corr = s.max_first_corr;
+  d.refine_tol = s.refine_tol;
+  d.r_inf = s.r_inf;
+  d.finite_tol = s.finite_tol;
+  d.real_tol = s.real_tol;
+  d.singular_cond = s.singular_cond;
+  d.t_endgame = s.t_endgame;
+  d.max_newton = s.max_newton;
+  d.max_steps = s.max_steps;
+  d.grow_after = s.grow_after;
+  d.refine_iters = s.refine_iters;
+  return d;
+}
+
+hc_status validate_settings(const hc_settings& s) {
+  if (!(s.dt_min > 0) || !(s.dt_max >= s.dt_min) || !(s.dt_init >= s.dt_min) ||
+      !(s.dt_init <= s.dt_max) || s.max_newton < 1 || s.max_newton > 16 || s.max_steps < 1 ||
+      s.grow_after < 1 || s.refine_iters < 0 || s.refine_iters > 64 || !(s.newton_tol > 0) ||
+      !(s.newton_tol_fp32 > 0) || !(s.max_first_corr > 0) || !(s.r_inf > 0) ||
+      (s.precision != HC_PREC_FP64 && s.precision != HC_PREC_MIXED) ||
+      (s.lanes != 0 && s.lanes != 4 && s.lanes != 8 && s.lanes != 16 && s.lanes != 32)) {
+    set_err("invalid settings");
+    return HC_ERR_INVALID;
+  }
+  return HC_OK;
+}
+
+// Dense degree-d detection and encoding maps.
+bool encode_dense(hc_problem* p, std::vector<int>& emap, std::vector<int>& dterm,
+                  std::vector<int>& dslot, std::vector<float>& dmult) {
+  const int n = p->n;
+  if (p->kind != HC_TOTAL_DEGREE || p->maxpf != 0) return false;
+  // degrees
+  std::vector<int> deg(n, 0);
+  for (int k = 0; k < p->T; ++k) {
+    int d = 0;
+    for (int j = 0; j < n; ++j) d += p->exps[(size_t)k * n + j];
+    deg[p->eq[k]] = std::max(deg[p->eq[k]], d);
+  }
+  const int d = deg[0];
+  for (int i = 0; i < n; ++i)
+    if (deg[i] != d) return false;
+  if (d != 2 && d != 3) return false;
+  if ((d == 2 && n > 12) || (d == 3 && n > 8)) return false;
+  const int M = binom(n + d, d);
+  if (p->T != n * M) return false;
+  const int L = hc::lanes_for(n);
+  const int MP = binom(n + d - 1, d - 1);
+  // nested Horner order of F_i's monomials
+  std::map<std::vector<int>, int> nested;  // sorted var tuple (ascending) -> index
+  {
+    int m = 0;
+    nested[{}] = m++;
+    for (int j = 0; j < n; ++j) {
+      nested[{j}] = m++;
+      for (int k = 0; k <= j; ++k) {
+        nested[{k, j}] = m++;
+        if (d == 3)
+          for (int l = 0; l <= k; ++l) nested[{l, k, j}] = m++;
+      }
+    }
+    if (m != M) return false;
+  }
+  std::vector<int> seen((size_t)n * M, 0);
+  emap.assign(p->T, 0);
+  dterm.clear();
+  dslot.clear();
+  dmult.clear();
+  for (int k = 0; k < p->T; ++k) {
+    const int i = p->eq[k];
+    std::vector<int> vars;
+    for (int j = 0; j < n; ++j)
+      for (int e = 0; e < p->exps[(size_t)k * n + j]; ++e) vars.push_back(j);
+    auto it = nested.find(vars);
+    if (it == nested.end()) return false;
+    if (seen[(size_t)i * M + it->second]++) return false;  // duplicate monomial
+    emap[k] = it->second * L + i;
+    if (vars.empty()) {
+      dterm.push_back(k);
+      dslot.push_back((n * MP + 0) * L + i);
+      dmult.push_back(1.0f);
+      continue;
+    }
+    for (int j = 0; j < n; ++j) {
+      const int a = p->exps[(size_t)k * n + j];
+      if (a == 0) continue;
+      std::vector<int> rest;
+      bool dropped = false;
+      for (int v : vars) {
+        if (v == j && !dropped) {
+          dropped = true;
+          continue;
+        }
+        rest.push_back(v);
+      }
+      const int mp = graded_index(n, rest);
+      dterm.push_back(k);
+      dslot.push_back((j * MP + mp) * L + i);
+      dmult.push_back((float)a);
+    }
+  }
+  p->dense = true;
+  p->deg = d;
+  p->M = M;
+  p->MP = MP;
+  p->L = L;
+  p->Dstride = (int64_t)(n + 1) * MP * L;
+  p->Estride = (int64_t)M * L;
+  int64_t paths = 1;
+  for (int i = 0; i < n; ++i) paths *= d;
+  p->paths = paths;
+  return true;
+}
+
+template <class T>
+hc_status upload(const std::vector<T>& v, T** out) {
+  *out = nullptr;
+  if (v.empty()) return HC_OK;
+  HC_CUDA(cudaMalloc((void**)out, v.size() * sizeof(T)));
+  HC_CUDA(cudaMemcpy(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return HC_OK;
+}
+
+void free_problem(hc_problem* p) {
+  if (!p) return;
+  cudaFree(p->d_emap);
+  cudaFree(p->d_dterm);
+  cudaFree(p->d_dslot);
+  cudaFree(p->d_dmult);
+  cudaFree(p->d_coef);
+  p->magic = 0;
+  delete p;
+}
+
+struct Occ {
+  int blocks = 0;
+  int sms = 0;
+};
+
+Occ occupancy(const void* fn, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, size_t>, Occ> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  auto key = std::make_pair(fn, smem);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  Occ o;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&o.sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.blocks, fn, hc::kBlock, smem);
+  if (o.blocks < 1) o.blocks = 1;
+  cache[key] = o;
+  return o;
+}
+
+hc_status launch_tracker(const hc::KernelRef& k, const hc::DenseArgs& a, int64_t max_items,
+                         cudaStream_t st) {
+  const size_t smem = (size_t)(hc::kBlock / k.lanes) * 2 * k.lanes * sizeof(cx<double>);
+  const Occ o = occupancy(k.fn, smem);
+  const int64_t groups_per_block = hc::kBlock / k.lanes;
+  int64_t want = (max_items + groups_per_block - 1) / groups_per_block;
+  int64_t grid = std::min<int64_t>((int64_t)o.blocks * o.sms, std::max<int64_t>(want, 1));
+  void* args[] = {(void*)&a};
+  HC_CUDA(cudaLaunchKernel(k.fn, dim3((unsigned)grid), dim3(hc::kBlock), args, smem, st));
+  return HC_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C-ABI
+extern "C" {
+
+const char* hc_status_string(int32_t s) {
+  switch (s) {
+    case HC_OK: return "ok";
+    case HC_PENDING: return "pending";
+    case HC_ERR_INVALID: return "invalid argument";
+    case HC_ERR_OOM: return "out of memory";
+    case HC_ERR_CUDA: return "CUDA error";
+    case HC_ERR_TIMEOUT: return "device step budget exhausted";
+    case HC_ERR_NUMERIC: return "non-finite input";
+    case HC_ERR_BUSY: return "admission refused";
+    case HC_ERR_UNSUPPORTED: return "unsupported problem shape";
+    default: return "unknown status";
+  }
+}
+
+const char* hc_last_error(void) { return g_err.c_str(); }
+
+hc_settings hc_default_settings(void) {
+  hc_settings s;
+  std::memset(&s, 0, sizeof(s));
+  s.dt_min = 1e-6;
+  s.dt_max = 0.05;
+  s.dt_init = 0.01;
+  s.newton_tol = 1e-8;
+  s.newton_tol_fp32 = 1e-5;
+  s.max_first_corr = 0.1;
+  s.refine_tol = 1e-13;
+  s.r_inf = 1e8;
+  s.finite_tol = 1e-10;
+  s.real_tol = 1e-8;
+  s.singular_cond = 1e12;
+  s.t_endgame = 0.95;
+  s.max_newton = 3;
+  s.max_steps = 100000;
+  s.grow_after = 3;
+  s.refine_iters = 8;
+  s.precision = HC_PREC_MIXED;
+  s.escalate = 1;
+  s.lanes = 0;
+  return s;
+}
+
+hc_status hc_create_problem(const hc_problem_desc* d, hc_problem** out) {
+  g_err.clear();
+  if (!d || !out) {
+    set_err("null descriptor or output");
+    return HC_ERR_INVALID;
+  }
+  const int n = d->n, T = d->n_terms;
+  if (n < 1 || n > 32 || T < 1 || !d->term_eq || !d->term_coef || !d->term_exp ||
+      d->max_pfac < 0 || d->max_pfac > 8 || (d->max_pfac > 0 && !d->term_param) ||
+      (d->kind != HC_TOTAL_DEGREE && d->kind != HC_PARAMETER) || d->n_params < 0) {
+    set_err("invalid problem descriptor");
+    return HC_ERR_INVALID;
+  }
+  hc_status vs = validate_settings(d->settings);
+  if (vs != HC_OK) return vs;
+  std::vector<int> eqcount(n, 0);
+  for (int k = 0; k < T; ++k) {
+    if (d->term_eq[k] < 0 || d->term_eq[k] >= n) {
+      set_err("term_eq out of range");
+      return HC_ERR_INVALID;
+    }
+    ++eqcount[d->term_eq[k]];
+    int tot = 0;
+    for (int j = 0; j < n; ++j) tot += d->term_exp[(size_t)k * n + j];
+    if (tot > 15) {
+      set_err("term degree above 15");
+      return HC_ERR_INVALID;
+    }
+    for (int f = 0; f < d->max_pfac; ++f) {
+      const int l = d->term_param[(size_t)k * d->max_pfac + f];
+      if (l < -1 || l >= d->n_params) {
+        set_err("term_param out of range");
+        return HC_ERR_INVALID;
+      }
+    }
+    if (!std::isfinite(d->term_coef[2 * k]) || !std::isfinite(d->term_coef[2 * k + 1])) {
+      set_err("non-finite coefficient");
+      return HC_ERR_NUMERIC;
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    if (eqcount[i] == 0) {
+      set_err("an equation has no terms");
+      return HC_ERR_INVALID;
+    }
+  if (d->kind == HC_TOTAL_DEGREE &&
+      !(std::fabs(std::hypot(d->gamma[0], d->gamma[1]) - 1.0) < 1e-6)) {
+    set_err("gamma must have unit modulus");
+    return HC_ERR_INVALID;
+  }
+  if (d->kind == HC_PARAMETER && (d->n_params < 1 || !d->p0 || d->n_start < 1 || !d->start)) {
+    set_err("parameter homotopy needs p0 and start solutions");
+    return HC_ERR_INVALID;
+  }
+
+  hc_problem* p = new hc_problem;
+  p->n = n;
+  p->T = T;
+  p->kind = d->kind;
+  p->maxpf = d->max_pfac;
+  p->P = d->n_params;
+  p->s = d->settings;
+  p->gamma[0] = d->gamma[0];
+  p->gamma[1] = d->gamma[1];
+  p->eq.assign(d->term_eq, d->term_eq + T);
+  p->coef.assign(d->term_coef, d->term_coef + 2 * (size_t)T);
+  p->exps.assign(d->term_exp, d->term_exp + (size_t)T * n);
+  if (p->maxpf) p->par.assign(d->term_param, d->term_param + (size_t)T * p->maxpf);
+  cudaGetDevice(&p->device);
+
+  std::vector<int> emap, dterm, dslot;
+  std::vector<float> dmult;
+  if (!encode_dense(p, emap, dterm, dslot, dmult)) {
+    delete p;
+    set_err("this build tracks dense total-degree systems of degree 2 (n <= 12) or 3 (n <= 8)");
+    return HC_ERR_UNSUPPORTED;
+  }
+  p->ndc = (int)dterm.size();
+  hc_status st;
+  if ((st = upload(emap, &p->d_emap)) != HC_OK || (st = upload(dterm, &p->d_dterm)) != HC_OK ||
+      (st = upload(dslot, &p->d_dslot)) != HC_OK || (st = upload(dmult, &p->d_dmult)) != HC_OK ||
+      (st = upload(p->coef, &p->d_coef)) != HC_OK) {
+    free_problem(p);
+    return st;
+  }
+  *out = p;
+  return HC_OK;
+}
+
+int64_t hc_problem_paths(const hc_problem* p) {
+  if (!p || p->magic != kProblemMagic) return -1;
+  return p->paths;
+}
+
+hc_status hc_track_batch(hc_problem* p, const hc_batch_desc* b, hc_batch** out) {
+  g_err.clear();
+  if (!p || p->magic != kProblemMagic || !b || !out || b->n_instances < 1 || !b->x_out ||
+      !b->status_out) {
+    set_err("invalid batch descriptor");
+    return HC_ERR_INVALID;
+  }
+  if (p->kind == HC_PARAMETER && !b->p1) {
+    set_err("parameter homotopy batch needs p1");
+    return HC_ERR_INVALID;
+  }
+  int cur = 0;
+  HC_CUDA(cudaGetDevice(&cur));
+  if (cur != p->device) HC_CUDA(cudaSetDevice(p->device));
+  const bool devptrs = (b->flags & HC_DEVICE_PTRS) != 0;
+  const bool mixed = p->s.precision == HC_PREC_MIXED;
+  const bool escalate = mixed && p->s.escalate;
+
+  hc_batch* bt = new hc_batch;
+  bt->p = p;
+  bt->stream = (cudaStream_t)b->stream;
+  bt->n_inst = b->n_instances;
+  bt->items = bt->n_inst * p->paths;
+  const int64_t items = bt->items;
+  const int n = p->n;
+  cudaStream_t st = bt->stream;
+
+  auto fail = [&](hc_status s) {
+    cudaStreamSynchronize(st);
+    for (void* q : bt->dev) cudaFree(q);
+    for (void* q : bt->pinned) cudaFreeHost(q);
+    for (cudaEvent_t e : {bt->ev0, bt->ev1, bt->evk0, bt->evk1, bt->evk2})
+      if (e) cudaEventDestroy(e);
+    delete bt;
+    return s;
+  };
+  auto dalloc = [&](void** q, size_t bytes) -> hc_status {
+    cudaError_t e = cudaMallocAsync(q, std::max<size_t>(bytes, 16), st);
+    if (e != cudaSuccess) {
+      set_err(std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+      return e == cudaErrorMemoryAllocation ? HC_ERR_OOM : HC_ERR_CUDA;
+    }
+    bt->dev.push_back(*q);
+    return HC_OK;
+  };
+#define HC_TRY(x)                        \
+  do {                                   \
+    hc_status s_ = (x);                  \
+    if (s_ != HC_OK) return fail(s_);    \
+  } while (0)
+#define HC_TRYCUDA(call)                                                     \
+  do {                                                                       \
+    cudaError_t e_ = (call);                                                 \
+    if (e_ != cudaSuccess) {                                                 \
+      set_err(std::string(#call) + ": " + cudaGetErrorString(e_));           \
+      return fail(HC_ERR_CUDA);                                              \
+    }                                                                        \
+  } while (0)
+
+  HC_TRYCUDA(cudaEventCreate(&bt->ev0));
+  HC_TRYCUDA(cudaEventCreate(&bt->ev1));
+  HC_TRYCUDA(cudaEventCreate(&bt->evk0));
+  HC_TRYCUDA(cudaEventCreate(&bt->evk1));
+  HC_TRYCUDA(cudaEventCreate(&bt->evk2));
+  HC_TRYCUDA(cudaEventRecord(bt->ev0, st));
+
+  // ---- coefficients on the device
+  const double* d_coef = p->d_coef;
+  int64_t coef_stride = 0;
+  if (b->coef) {
+    coef_stride = (int64_t)p->T;
+    if (devptrs || is_device_ptr(b->coef)) {
+      d_coef = b->coef;
+    } else {
+      void* q;
+      HC_TRY(dalloc(&q, sizeof(double) * 2 * p->T * bt->n_inst));
+      HC_TRYCUDA(cudaMemcpyAsync(q, b->coef, sizeof(double) * 2 * p->T * bt->n_inst,
+                                 cudaMemcpyHostToDevice, st));
+      d_coef = (const double*)q;
+    }
+  }
+
+  // ---- encoded coefficients
+  void *E = nullptr, *D64 = nullptr, *D32 = nullptr;
+  const size_t eb = sizeof(cx<double>) * p->Estride * bt->n_inst;
+  const size_t db64 = sizeof(cx<double>) * p->Dstride * bt->n_inst;
+  const size_t db32 = sizeof(cx<float>) * p->Dstride * bt->n_inst;
+  HC_TRY(dalloc(&E, eb));
+  HC_TRYCUDA(cudaMemsetAsync(E, 0, eb, st));
+  if (!mixed || escalate) {
+    HC_TRY(dalloc(&D64, db64));
+    HC_TRYCUDA(cudaMemsetAsync(D64, 0, db64, st));
+  }
+  if (mixed) {
+    HC_TRY(dalloc(&D32, db32));
+    HC_TRYCUDA(cudaMemsetAsync(D32, 0, db32, st));
+  }
+  {
+    const int64_t work = bt->n_inst * (p->T + p->ndc);
+    const int grid = (int)std::min<int64_t>((work + 255) / 256, 4096);
+    stage_dense_kernel<<<grid, 256, 0, st>>>(bt->n_inst, p->T, (const double2*)d_coef, coef_stride,
+                                            p->d_emap, p->ndc, p->d_dterm, p->d_dslot,
+                                            p->d_dmult, (double2*)E, p->Estride, (float2*)D32,
+                                            (double2*)D64, p->Dstride);
+    HC_TRYCUDA(cudaGetLastError());
+  }
+
+  // ---- outputs (device side)
+  double* d_x = b->x_out;
+  uint8_t* d_status = b->status_out;
+  int32_t* d_steps = b->steps_out;
+  double* d_be = b->be_out;
+  auto out_buffer = [&](void* user, size_t bytes, void** dptr) -> hc_status {
+    void* q;
+    hc_status s = dalloc(&q, bytes);
+    if (s != HC_OK) return s;
+    *dptr = q;
+    if (user) {
+      if (is_pinned_host(user)) {
+        bt->copies.push_back({user, nullptr, bytes});
+      } else {
+        void* pin;
+        if (cudaMallocHost(&pin, bytes) != cudaSuccess) {
+          set_err("cudaMallocHost failed");
+          return HC_ERR_OOM;
+        }
+        bt->pinned.push_back(pin);
+        bt->copies.push_back({user, pin, bytes});
+      }
+    }
+    return HC_OK;
+  };
+  std::vector<std::pair<void*, size_t>> d2h;  // device source per copy
+  if (!devptrs) {
+    void* q;
+    HC_TRY(out_buffer(b->x_out, sizeof(double) * 2 * n * items, &q));
+    d_x = (double*)q;
+    d2h.push_back({q, 0});
+    HC_TRY(out_buffer(b->status_out, items, &q));
+    d_status = (uint8_t*)q;
+    d2h.push_back({q, 0});
+    HC_TRY(out_buffer(b->steps_out, sizeof(int32_t) * 3 * items, &q));
+    d_steps = (int32_t*)q;
+    if (b->steps_out) d2h.push_back({q, 0});
+    if (b->be_out) {
+      HC_TRY(out_buffer(b->be_out, sizeof(double) * items, &q));
+      d_be = (double*)q;
+      d2h.push_back({q, 0});
+    } else {
+      d_be = nullptr;
+    }
+  } else if (!d_steps) {
+    void* q;
+    HC_TRY(dalloc(&q, sizeof(int32_t) * 3 * items));
+    d_steps = (int32_t*)q;
+  }
+
+  // ---- control words: [0] queue [1] escalation queue [2] escalation count
+  //      [8..15] summary
+  {
+    void* q;
+    HC_TRY(dalloc(&q, sizeof(unsigned long long) * 16));
+    bt->d_ctl = (unsigned long long*)q;
+    HC_TRYCUDA(cudaMemsetAsync(q, 0, sizeof(unsigned long long) * 16, st));
+    void* pin;
+    if (cudaMallocHost(&pin, sizeof(unsigned long long) * 16) != cudaSuccess) {
+      set_err("cudaMallocHost failed");
+      return fail(HC_ERR_OOM);
+    }
+    bt->pinned.push_back(pin);
+    bt->h_ctl = (unsigned long long*)pin;
+    std::memset(pin, 0, sizeof(unsigned long long) * 16);
+  }
+  int64_t* esc_list = nullptr;
+  if (escalate) {
+    void* q;
+    HC_TRY(dalloc(&q, sizeof(int64_t) * items));
+    esc_list = (int64_t*)q;
+  }
+
+  // ---- tracking launch
+  hc::DenseArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.c.s = dev_settings(p->s);
+  a.c.n_items = items;
+  a.c.count_dev = nullptr;
+  a.c.items = nullptr;
+  a.c.queue = bt->d_ctl + 0;
+  a.c.paths = p->paths;
+  a.c.x_out = d_x;
+  a.c.status_out = d_status;
+  a.c.steps_out = d_steps;
+  a.c.be_out = d_be;
+  a.c.esc_list = esc_list;
+  a.c.esc_count = bt->d_ctl + 2;
+  a.D32 = (const cx<float>*)D32;
+  a.D64 = (const cx<double>*)D64;
+  a.E = (const cx<double>*)E;
+  a.Dstride = p->Dstride;
+  a.Estride = p->Estride;
+  a.gamma = cx<double>{p->gamma[0], p->gamma[1]};
+  const hc::KernelRef k = hc::dense_kernel(p->deg, n, mixed);
+  if (!k.fn) {
+    set_err("no kernel for this problem shape");
+    return fail(HC_ERR_UNSUPPORTED);
+  }
+  HC_TRYCUDA(cudaEventRecord(bt->evk0, st));
+  HC_TRY(launch_tracker(k, a, items, st));
+  HC_TRYCUDA(cudaEventRecord(bt->evk1, st));
+  if (escalate) {
+    hc::DenseArgs e = a;
+    e.c.count_dev = bt->d_ctl + 2;
+    e.c.items = esc_list;
+    e.c.queue = bt->d_ctl + 1;
+    e.c.esc_list = nullptr;
+    const hc::KernelRef k64 = hc::dense_kernel(p->deg, n, false);
+    // one block per SM is plenty for the (rare) escalated paths
+    HC_TRY(launch_tracker(k64, e, std::min<int64_t>(items, 4 * 152), st));
+  }
+  HC_TRYCUDA(cudaEventRecord(bt->evk2, st));
+  {
+    const int grid = (int)std::min<int64_t>((items + 255) / 256, 1024);
+    summarize_kernel<<<std::max(grid, 1), 256, 0, st>>>(items, d_status, d_steps, bt->d_ctl + 8);
+    HC_TRYCUDA(cudaGetLastError());
+  }
+  HC_TRYCUDA(cudaMemcpyAsync(bt->h_ctl, bt->d_ctl, sizeof(unsigned long long) * 16,
+                             cudaMemcpyDeviceToHost, st));
+  for (size_t i = 0; i < bt->copies.size(); ++i) {
+    void* dst = bt->copies[i].pinned ? bt->copies[i].pinned : bt->copies[i].dst;
+    HC_TRYCUDA(cudaMemcpyAsync(dst, d2h[i].first, bt->copies[i].bytes, cudaMemcpyDeviceToHost, st));
+  }
+  HC_TRYCUDA(cudaEventRecord(bt->ev1, st));
+  if (cur != p->device) cudaSetDevice(cur);
+  *out = bt;
+  return HC_OK;
+#undef HC_TRY
+#undef HC_TRYCUDA
+}
+
+hc_status hc_poll(hc_batch* b, int64_t timeout_us, hc_batch_result* r) {
+  g_err.clear();
+  if (!b || b->magic != kBatchMagic) {
+    set_err("invalid batch");
+    return HC_ERR_INVALID;
+  }
+  if (!b->done) {
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+      cudaError_t e = cudaEventQuery(b->ev1);
+      if (e == cudaSuccess) break;
+      if (e != cudaErrorNotReady) {
+        set_err(std::string("cudaEventQuery: ") + cudaGetErrorString(e));
+        return HC_ERR_CUDA;
+      }
+      if (timeout_us == 0) return HC_PENDING;
+      const auto el = std::chrono::duration_cast<std::chrono::microseconds>(
+                          std::chrono::steady_clock::now() - t0)
+                          .count();
+      if (timeout_us > 0 && el >= timeout_us) return HC_PENDING;
+      std::this_thread::sleep_for(std::chrono::microseconds(el < 200 ? 2 : 50));
+    }
+    for (auto& c : b->copies)
+      if (c.pinned) std::memcpy(c.dst, c.pinned, c.bytes);
+    b->done = true;
+  }
+  if (r) {
+    std::memset(r, 0, sizeof(*r));
+    r->paths = b->items;
+    const unsigned long long* s = b->h_ctl + 8;
+    r->finite = (int64_t)s[0];
+    r->real = (int64_t)s[1];
+    r->diverged = (int64_t)s[2];
+    r->singular = (int64_t)s[3];
+    r->failed = (int64_t)s[4];
+    r->steps_accepted = (int64_t)s[5];
+    r->steps_rejected = (int64_t)s[6];
+    r->newton_iters = (int64_t)s[7];
+    r->escalated = (int64_t)b->h_ctl[2];
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, b->ev0, b->ev1) == cudaSuccess) r->device_ms = ms;
+    if (cudaEventElapsedTime(&ms, b->evk0, b->evk1) == cudaSuccess) r->track_ms = ms;
+    if (cudaEventElapsedTime(&ms, b->evk1, b->evk2) == cudaSuccess) r->escalate_ms = ms;
+  }
+  return HC_OK;
+}
+
+void hc_destroy(void* handle) {
+  if (!handle) return;
+  const uint32_t magic = *static_cast<uint32_t*>(handle);
+  if (magic == kProblemMagic) {
+    free_problem(static_cast<hc_problem*>(handle));
+  } else if (magic == kBatchMagic) {
+    hc_batch* b = static_cast<hc_batch*>(handle);
+    if (!b->done) cudaEventSynchronize(b->ev1);
+    for (void* q : b->dev) cudaFreeAsync(q, b->stream);
+    cudaStreamSynchronize(b->stream);
+    for (void* q : b->pinned) cudaFreeHost(q);
+    for (cudaEvent_t e : {b->ev0, b->ev1, b->evk0, b->evk1, b->evk2}) cudaEventDestroy(e);
+    b->magic = 0;
+    delete b;
+  }
+}
+
+}  // extern "C"

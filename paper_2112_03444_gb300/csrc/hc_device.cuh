@@ -1,0 +1,176 @@
+// Device building blocks of the tracker: complex arithmetic, lane-group
+// primitives and the register-resident dense solve (Sec. 6 of the paper).
+//
+// Layout: one path is owned by a group of L lanes of a warp (L = 4, 8, 16 or
+// 32); lane i of the group holds row i of the augmented matrix [A | b] in
+// registers.  Pivot search is one warp-reduction instruction over the group,
+// and the pivot row reaches the other lanes through shuffles.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hc {
+
+template <class R>
+struct cx {
+  R re, im;
+};
+
+template <class R>
+__device__ __forceinline__ cx<R> mk(R re, R im) { return cx<R>{re, im}; }
+template <class R>
+__device__ __forceinline__ cx<R> czero() { return cx<R>{R(0), R(0)}; }
+
+template <class R>
+__device__ __forceinline__ cx<R> operator+(cx<R> a, cx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <class R>
+__device__ __forceinline__ cx<R> operator-(cx<R> a, cx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <class R>
+__device__ __forceinline__ cx<R> operator-(cx<R> a) { return {-a.re, -a.im}; }
+template <class R>
+__device__ __forceinline__ cx<R> operator*(cx<R> a, cx<R> b) {
+  return {fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re)};
+}
+template <class R>
+__device__ __forceinline__ cx<R> operator*(R s, cx<R> a) { return {s * a.re, s * a.im}; }
+
+// acc + a*b (four FMAs)
+template <class R>
+__device__ __forceinline__ cx<R> cfma(cx<R> a, cx<R> b, cx<R> acc) {
+  return {fma(a.re, b.re, fma(-a.im, b.im, acc.re)), fma(a.re, b.im, fma(a.im, b.re, acc.im))};
+}
+// acc - a*b
+template <class R>
+__device__ __forceinline__ cx<R> cfms(cx<R> a, cx<R> b, cx<R> acc) {
+  return {fma(-a.re, b.re, fma(a.im, b.im, acc.re)), fma(-a.re, b.im, fma(-a.im, b.re, acc.im))};
+}
+
+// 1/z with scaling by max(|re|, |im|) so that |z|^2 cannot overflow for
+// |z| up to the format's range.
+template <class R>
+__device__ __forceinline__ cx<R> crecip(cx<R> z) {
+  const R s = fmax(fabs(z.re), fabs(z.im));
+  const R inv_s = R(1) / s;
+  const R zr = z.re * inv_s, zi = z.im * inv_s;
+  const R d = R(1) / (s * fma(zr, zr, zi * zi));
+  return {zr * d, -zi * d};
+}
+
+template <class R>
+__device__ __forceinline__ R cabs1(cx<R> z) { return fabs(z.re) + fabs(z.im); }
+template <class R>
+__device__ __forceinline__ R cabs2(cx<R> z) { return sqrt(fma(z.re, z.re, z.im * z.im)); }
+
+template <class D, class S>
+__device__ __forceinline__ cx<D> cvt(cx<S> z) { return {(D)z.re, (D)z.im}; }
+
+template <class R>
+__device__ __forceinline__ bool cfinite(cx<R> z) { return isfinite(z.re) && isfinite(z.im); }
+
+// ---------------------------------------------------------------- lane groups
+struct Group {
+  int gl;          // lane index inside the group (row index)
+  int wl;          // lane index inside the warp
+  unsigned mask;   // lanes of this group
+};
+
+template <int L>
+__device__ __forceinline__ Group make_group() {
+  Group g;
+  g.wl = threadIdx.x & 31;
+  g.gl = g.wl & (L - 1);
+  g.mask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << (g.wl & ~(L - 1)));
+  return g;
+}
+
+template <class R>
+__device__ __forceinline__ cx<R> shfl(unsigned mask, cx<R> v, int src) {
+  return {__shfl_sync(mask, v.re, src), __shfl_sync(mask, v.im, src)};
+}
+
+// max over the group of a non-negative float (NaN compares above everything)
+__device__ __forceinline__ float gmaxf(const Group& g, float v) {
+  unsigned b = __reduce_max_sync(g.mask, __float_as_uint(fmaxf(v, 0.0f)) | (isnan(v) ? 0x7fc00000u : 0u));
+  return __uint_as_float(b);
+}
+__device__ __forceinline__ bool gany(const Group& g, bool v) {
+  return __reduce_or_sync(g.mask, v ? 1u : 0u) != 0u;
+}
+// sum over the group (butterfly)
+template <int L, class R>
+__device__ __forceinline__ R gsum(const Group& g, R v) {
+#pragma unroll
+  for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(g.mask, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------- dense solve
+//
+// Gauss-Jordan elimination with partial pivoting on the augmented matrix
+// [A | B] (N rows, N + NR columns), row i in lane i.  The paper (Sec. 6)
+// factors [A b] by LU, which carries the L-solve inside the factorisation,
+// and finishes with a back substitution on the cached U.  With one row per
+// lane the back substitution would be N serial broadcast steps; eliminating
+// above the pivot as well (Gauss-Jordan) costs no extra latency because those
+// rows sit in otherwise idle lanes, and it removes the back substitution.
+//
+// Pivot: the largest |Re| + |Im| among rows not yet used, lowest lane on
+// ties, found with one __reduce_max_sync on a key whose high bits are the
+// magnitude's float bits and whose low 5 bits encode the lane.
+//
+// On return lane i with i < N holds in col the column it pivoted on and in
+// sol[r] the solution component x[col] of right-hand side r.  Returns false
+// if a pivot was zero or non-finite (the caller rejects the step).
+template <int N, int NR, class R>
+__device__ __forceinline__ bool gj_solve(const Group& g, cx<R> (&a)[N + NR], cx<R> (&sol)[NR],
+                                         int& col) {
+  bool used = g.gl >= N;
+  cx<R> diag = mk<R>(R(1), R(0));
+  col = -1;
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const float m = (float)cabs1(a[k]);
+    const unsigned key = used ? 0u : ((__float_as_uint(m) & ~31u) | (unsigned)(31 - g.wl));
+    const unsigned kmax = __reduce_max_sync(g.mask, key);
+    const unsigned mbits = kmax & ~31u;
+    ok = ok && (mbits != 0u) && (mbits < 0x7f800000u);
+    const int p = 31 - (int)(kmax & 31u);
+    const cx<R> pk = shfl(g.mask, a[k], p);
+    const bool me = (g.wl == p);
+    const cx<R> l = me ? czero<R>() : a[k] * crecip(pk);
+    if (me) {
+      used = true;
+      diag = a[k];
+      col = k;
+    }
+#pragma unroll
+    for (int j = k + 1; j < N + NR; ++j) {
+      const cx<R> pj = shfl(g.mask, a[j], p);
+      a[j] = cfms(l, pj, a[j]);
+    }
+  }
+  const cx<R> id = crecip(diag);
+#pragma unroll
+  for (int r = 0; r < NR; ++r) sol[r] = a[N + r] * id;
+  return ok;
+}
+
+// ---------------------------------------------------------------- settings
+struct DevSettings {
+  double dt_min, dt_max, dt_init, newton_tol, newton_tol_fp32, max_first_corr;
+  double refine_tol, r_inf, finite_tol, real_tol, singular_cond, t_endgame;
+  int max_newton, max_steps, grow_after, refine_iters;
+};
+
+enum : int {
+  ST_FINITE = 1, ST_DIVERGED = 2, ST_FAIL_STEP = 3, ST_FAIL_MAXSTEPS = 4,
+  ST_FAIL_NAN = 5, ST_SINGULAR = 6, ST_FAIL_REFINE = 7, ST_REAL = 0x80
+};
+
+// Largest FP32 condition estimate that still certifies cond_1 < 1e12 with
+// room to spare; above it a mixed-precision path is re-tracked in FP64.
+constexpr double kFp32CondTrust = 1.0e5;
+
+}  // namespace hc

@@ -1,0 +1,52 @@
+// Kernel entry points and their host-visible launch descriptors.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hc_device.cuh"
+
+namespace hc {
+
+constexpr int kBlock = 128;  // threads per block of the tracking kernels
+
+// Work distribution of a tracking launch: work item = (instance, path),
+// item = instance * paths + path; a lane group takes the next item with one
+// atomicAdd on *queue (retire/refill: a group that finishes a path pulls the
+// next one), until the items are exhausted.
+struct LaunchCommon {
+  DevSettings s;
+  int64_t n_items;                      // used when count_dev == nullptr
+  const unsigned long long* count_dev;  // number of items, read on the device
+  const int64_t* items;                 // optional explicit item list
+  unsigned long long* queue;            // next item counter (zeroed before launch)
+  int64_t paths;                        // paths per instance
+  double* x_out;                        // [items][n] complex
+  uint8_t* status_out;                  // [items]
+  int32_t* steps_out;                   // [items][3]
+  double* be_out;                       // [items] (optional)
+  int64_t* esc_list;                    // mixed precision: items to re-track in FP64
+  unsigned long long* esc_count;
+};
+
+struct DenseArgs {
+  LaunchCommon c;
+  const cx<float>* D32;
+  const cx<double>* D64;
+  const cx<double>* E;
+  int64_t Dstride, Estride;  // complex elements per instance
+  cx<double> gamma;
+};
+
+struct KernelRef {
+  const void* fn;   // __global__ function
+  int lanes;        // lanes per path (L)
+};
+
+// Lanes per path chosen for n unknowns (one row per lane, groups are powers
+// of two so that a warp holds 32 / L paths).
+inline int lanes_for(int n) { return n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : 32; }
+
+KernelRef dense_kernel(int deg, int n, bool mixed);  // fn == nullptr if absent
+
+}  // namespace hc

@@ -1,0 +1,284 @@
+"""Thin ctypes binding of the C-ABI in include/hc.h (libhc.so).
+
+Argument marshalling only: every step of the tracking path runs in the CUDA
+kernels behind the C-ABI.  The library must have been built (``build.py``);
+importing this module without it raises, there is no CPU fallback.
+
+Same names as the C calls: ``create_problem``, ``track_batch``, ``poll``,
+``destroy``, ``default_settings``; plus ``Problem`` / ``Batch`` wrappers that
+accept numpy arrays (host) or torch CUDA tensors (device-resident).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhc.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with paper_2112_03444_gb300/build.py "
+                      "(the tracker has no CPU fallback)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+# ---------------------------------------------------------------- constants
+HC_OK, HC_PENDING = 0, 1
+HC_ERR_INVALID, HC_ERR_OOM, HC_ERR_CUDA, HC_ERR_TIMEOUT = -1, -2, -3, -4
+HC_ERR_NUMERIC, HC_ERR_BUSY, HC_ERR_UNSUPPORTED = -5, -6, -7
+HC_TOTAL_DEGREE, HC_PARAMETER = 0, 1
+HC_PREC_FP64, HC_PREC_MIXED = 0, 1
+HC_DEVICE_PTRS, HC_BLOCKING_ADMIT = 1, 2
+PATH_FINITE, PATH_DIVERGED, PATH_FAIL_STEP, PATH_FAIL_MAXSTEPS = 1, 2, 3, 4
+PATH_FAIL_NAN, PATH_SINGULAR, PATH_FAIL_REFINE, PATH_REAL = 5, 6, 7, 0x80
+
+
+class hc_settings(ctypes.Structure):
+    _fields_ = [("dt_min", ctypes.c_double), ("dt_max", ctypes.c_double),
+                ("dt_init", ctypes.c_double), ("newton_tol", ctypes.c_double),
+                ("newton_tol_fp32", ctypes.c_double), ("max_first_corr", ctypes.c_double),
+                ("refine_tol", ctypes.c_double), ("r_inf", ctypes.c_double),
+                ("finite_tol", ctypes.c_double), ("real_tol", ctypes.c_double),
+                ("singular_cond", ctypes.c_double), ("t_endgame", ctypes.c_double),
+                ("max_newton", ctypes.c_int32), ("max_steps", ctypes.c_int32),
+                ("grow_after", ctypes.c_int32), ("refine_iters", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("escalate", ctypes.c_int32),
+                ("lanes", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class hc_problem_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("n_terms", ctypes.c_int32),
+                ("term_eq", ctypes.c_void_p), ("term_coef", ctypes.c_void_p),
+                ("term_exp", ctypes.c_void_p), ("max_pfac", ctypes.c_int32),
+                ("term_param", ctypes.c_void_p), ("n_params", ctypes.c_int32),
+                ("kind", ctypes.c_int32), ("gamma", ctypes.c_double * 2),
+                ("p0", ctypes.c_void_p), ("n_start", ctypes.c_int64),
+                ("start", ctypes.c_void_p), ("settings", hc_settings)]
+
+
+class hc_batch_desc(ctypes.Structure):
+    _fields_ = [("n_instances", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("coef", ctypes.c_void_p), ("p1", ctypes.c_void_p),
+                ("stream", ctypes.c_void_p), ("x_out", ctypes.c_void_p),
+                ("status_out", ctypes.c_void_p), ("steps_out", ctypes.c_void_p),
+                ("be_out", ctypes.c_void_p)]
+
+
+class hc_batch_result(ctypes.Structure):
+    _fields_ = [("paths", ctypes.c_int64), ("finite", ctypes.c_int64),
+                ("real", ctypes.c_int64), ("diverged", ctypes.c_int64),
+                ("singular", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("escalated", ctypes.c_int64), ("steps_accepted", ctypes.c_int64),
+                ("steps_rejected", ctypes.c_int64), ("newton_iters", ctypes.c_int64),
+                ("device_ms", ctypes.c_double), ("track_ms", ctypes.c_double),
+                ("escalate_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_lib.hc_status_string.restype = ctypes.c_char_p
+_lib.hc_status_string.argtypes = [ctypes.c_int32]
+_lib.hc_last_error.restype = ctypes.c_char_p
+_lib.hc_default_settings.restype = hc_settings
+_lib.hc_create_problem.restype = ctypes.c_int32
+_lib.hc_create_problem.argtypes = [ctypes.POINTER(hc_problem_desc), ctypes.POINTER(_P)]
+_lib.hc_problem_paths.restype = ctypes.c_int64
+_lib.hc_problem_paths.argtypes = [_P]
+_lib.hc_track_batch.restype = ctypes.c_int32
+_lib.hc_track_batch.argtypes = [_P, ctypes.POINTER(hc_batch_desc), ctypes.POINTER(_P)]
+_lib.hc_poll.restype = ctypes.c_int32
+_lib.hc_poll.argtypes = [_P, ctypes.c_int64, ctypes.POINTER(hc_batch_result)]
+_lib.hc_destroy.restype = None
+_lib.hc_destroy.argtypes = [_P]
+
+EXPORTED = ("hc_status_string", "hc_last_error", "hc_default_settings", "hc_create_problem",
+            "hc_problem_paths", "hc_track_batch", "hc_poll", "hc_destroy")
+
+
+class HCError(RuntimeError):
+    def __init__(self, code, where):
+        msg = _lib.hc_last_error().decode()
+        super().__init__(f"{where}: {_lib.hc_status_string(code).decode()} ({code}) {msg}")
+        self.code = code
+
+
+def _check(code, where):
+    if code not in (HC_OK, HC_PENDING):
+        raise HCError(code, where)
+    return code
+
+
+def default_settings(**over) -> hc_settings:
+    s = _lib.hc_default_settings()
+    for k, v in over.items():
+        setattr(s, k, v)
+    return s
+
+
+# ---------------------------------------------------------------- raw calls
+def create_problem(desc: hc_problem_desc) -> int:
+    h = _P()
+    _check(_lib.hc_create_problem(ctypes.byref(desc), ctypes.byref(h)), "hc_create_problem")
+    return h.value
+
+
+def track_batch(problem: int, desc: hc_batch_desc) -> int:
+    h = _P()
+    _check(_lib.hc_track_batch(problem, ctypes.byref(desc), ctypes.byref(h)), "hc_track_batch")
+    return h.value
+
+
+def poll(batch: int, timeout_us: int = -1):
+    r = hc_batch_result()
+    code = _check(_lib.hc_poll(batch, int(timeout_us), ctypes.byref(r)), "hc_poll")
+    return code, r
+
+
+def destroy(handle: int) -> None:
+    if handle:
+        _lib.hc_destroy(handle)
+
+
+def problem_paths(problem: int) -> int:
+    return int(_lib.hc_problem_paths(problem))
+
+
+# ---------------------------------------------------------------- wrappers
+def _host(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _addr(a):
+    """Address of a numpy array or a torch tensor (host or device)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+class Problem:
+    """A polynomial system and its homotopy, encoded on the current device.
+
+    system: an ``inputs.TermSystem``.  kind: HC_TOTAL_DEGREE (gamma) or
+    HC_PARAMETER (p0, start).  settings: hc_settings or dict of overrides.
+    """
+
+    def __init__(self, system, kind=HC_TOTAL_DEGREE, gamma=1 + 0j, p0=None, start=None,
+                 settings=None):
+        if isinstance(settings, dict) or settings is None:
+            settings = default_settings(**(settings or {}))
+        self.system = system
+        self.n = int(system.n)
+        self.kind = kind
+        self._keep = [
+            _host(system.term_eq, np.int32), _host(system.term_coef, np.complex128),
+            _host(system.term_exp, np.uint8), _host(system.term_param, np.int32),
+            None if p0 is None else _host(p0, np.complex128),
+            None if start is None else _host(start, np.complex128),
+        ]
+        eq, cf, ex, pa, p0a, sa = self._keep
+        d = hc_problem_desc()
+        d.n = self.n
+        d.n_terms = int(system.n_terms)
+        d.term_eq = eq.ctypes.data
+        d.term_coef = cf.ctypes.data
+        d.term_exp = ex.ctypes.data
+        d.max_pfac = int(system.max_pfac)
+        d.term_param = pa.ctypes.data if pa.size else None
+        d.n_params = int(system.n_params)
+        d.kind = kind
+        g = complex(gamma)
+        d.gamma[0], d.gamma[1] = g.real, g.imag
+        d.p0 = None if p0a is None else p0a.ctypes.data
+        d.n_start = 0 if sa is None else int(sa.shape[0])
+        d.start = None if sa is None else sa.ctypes.data
+        d.settings = settings
+        self.settings = settings
+        self.h = create_problem(d)
+        self.paths = problem_paths(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def track(self, n_instances=1, coef=None, p1=None, stream=None, device_out=None,
+              x_out=None, status_out=None, steps_out=None, be_out=None, device=False):
+        """Enqueue a batch; returns a Batch.  Host mode (default) allocates numpy
+        outputs; with device=True pass torch CUDA tensors (inputs and outputs)."""
+        I, P, n = int(n_instances), self.paths, self.n
+        if not device:
+            x_out = np.zeros((I, P, n), np.complex128) if x_out is None else x_out
+            status_out = np.zeros((I, P), np.uint8) if status_out is None else status_out
+            steps_out = np.zeros((I, P, 3), np.int32) if steps_out is None else steps_out
+            be_out = np.zeros((I, P), np.float64) if be_out is None else be_out
+            if coef is not None and not hasattr(coef, "data_ptr"):
+                coef = _host(coef, np.complex128)
+            if p1 is not None and not hasattr(p1, "data_ptr"):
+                p1 = _host(p1, np.complex128)
+        b = hc_batch_desc()
+        b.n_instances = I
+        b.flags = HC_DEVICE_PTRS if device else 0
+        b.coef = _addr(coef)
+        b.p1 = _addr(p1)
+        b.stream = stream
+        b.x_out = _addr(x_out)
+        b.status_out = _addr(status_out)
+        b.steps_out = _addr(steps_out)
+        b.be_out = _addr(be_out)
+        h = track_batch(self.h, b)
+        return Batch(h, self, dict(x=x_out, status=status_out, steps=steps_out, be=be_out,
+                                   coef=coef, p1=p1))
+
+
+class Batch:
+    def __init__(self, h, problem, bufs):
+        self.h = h
+        self.problem = problem
+        self.bufs = bufs
+        self.result = None
+
+    def poll(self, timeout_us=-1):
+        code, r = poll(self.h, timeout_us)
+        if code == HC_OK:
+            self.result = r.as_dict()
+        return code
+
+    def wait(self):
+        self.poll(-1)
+        return self
+
+    @property
+    def x(self):
+        return self.bufs["x"]
+
+    @property
+    def status(self):
+        return self.bufs["status"]
+
+    @property
+    def steps(self):
+        return self.bufs["steps"]
+
+    @property
+    def be(self):
+        return self.bufs["be"]
+
+    def close(self):
+        if getattr(self, "h", None):
+            destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()

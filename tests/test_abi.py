@@ -1,0 +1,109 @@
+"""The C-ABI library loads, exports every declared symbol and validates its
+inputs on the host (CPU only: no call here reaches the GPU)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def hc():
+    from paper_2112_03444_gb300 import build
+    build.build()
+    from paper_2112_03444_gb300 import hc as mod
+    return mod
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "hc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hc_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(hc):
+    lib = ctypes.CDLL(hc.LIB_PATH)
+    names = declared_functions()
+    assert "hc_create_problem" in names and "hc_track_batch" in names
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) <= set(hc.EXPORTED) | set(names)
+
+
+def test_struct_layouts_match_header_sizes(hc):
+    # hc_settings: 12 doubles + 8 int32 = 128 bytes
+    assert ctypes.sizeof(hc.hc_settings) == 128
+    assert ctypes.sizeof(hc.hc_batch_result) == 13 * 8
+
+
+def test_default_settings_and_strings(hc):
+    s = hc.default_settings()
+    assert s.dt_min == 1e-6 and s.dt_max == 0.05 and s.max_newton == 3
+    assert s.precision == hc.HC_PREC_MIXED and s.newton_tol == 1e-8
+    assert hc._lib.hc_status_string(hc.HC_ERR_INVALID) == b"invalid argument"
+    assert hc._lib.hc_status_string(12345) == b"unknown status"
+
+
+def _desc(hc, system, **kw):
+    keep = [np.ascontiguousarray(system.term_eq, np.int32),
+            np.ascontiguousarray(system.term_coef, np.complex128),
+            np.ascontiguousarray(system.term_exp, np.uint8)]
+    d = hc.hc_problem_desc()
+    d.n = system.n
+    d.n_terms = system.n_terms
+    d.term_eq, d.term_coef, d.term_exp = (k.ctypes.data for k in keep)
+    d.kind = hc.HC_TOTAL_DEGREE
+    d.gamma[0], d.gamma[1] = 1.0, 0.0
+    d.settings = hc.default_settings()
+    for k, v in kw.items():
+        setattr(d, k, v)
+    return d, keep
+
+
+@pytest.mark.parametrize("field,value", [("n", 0), ("n", 33), ("n_terms", 0), ("kind", 7)])
+def test_create_problem_rejects_bad_descriptors(hc, field, value):
+    from paper_2112_03444_gb300 import inputs
+    d, keep = _desc(hc, inputs.dense_system(3, 2, 0), **{field: value})
+    h = ctypes.c_void_p(12345)
+    rc = hc._lib.hc_create_problem(ctypes.byref(d), ctypes.byref(h))
+    assert rc == hc.HC_ERR_INVALID
+    assert h.value == 12345  # untouched on error
+
+
+def test_create_problem_rejects_out_of_range_equation(hc):
+    from paper_2112_03444_gb300 import inputs
+    sys_ = inputs.dense_system(2, 2, 0)
+    sys_.term_eq[3] = 5
+    d, keep = _desc(hc, sys_)
+    h = ctypes.c_void_p()
+    assert hc._lib.hc_create_problem(ctypes.byref(d), ctypes.byref(h)) == hc.HC_ERR_INVALID
+
+
+def test_create_problem_rejects_non_unit_gamma_and_nan(hc):
+    from paper_2112_03444_gb300 import inputs
+    sys_ = inputs.dense_system(2, 2, 0)
+    d, keep = _desc(hc, sys_)
+    d.gamma[0] = 2.0
+    h = ctypes.c_void_p()
+    assert hc._lib.hc_create_problem(ctypes.byref(d), ctypes.byref(h)) == hc.HC_ERR_INVALID
+    sys_.term_coef[0] = complex(np.nan, 0)
+    d, keep = _desc(hc, sys_)
+    assert hc._lib.hc_create_problem(ctypes.byref(d), ctypes.byref(h)) == hc.HC_ERR_NUMERIC
+
+
+def test_create_problem_rejects_bad_settings(hc):
+    from paper_2112_03444_gb300 import inputs
+    d, keep = _desc(hc, inputs.dense_system(2, 2, 0))
+    d.settings.dt_min = -1.0
+    h = ctypes.c_void_p()
+    assert hc._lib.hc_create_problem(ctypes.byref(d), ctypes.byref(h)) == hc.HC_ERR_INVALID
+
+
+def test_null_handles_are_rejected(hc):
+    r = hc.hc_batch_result()
+    assert hc._lib.hc_poll(None, 0, ctypes.byref(r)) == hc.HC_ERR_INVALID
+    assert hc._lib.hc_problem_paths(None) == -1
+    hc._lib.hc_destroy(None)  # no-op
