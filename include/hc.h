@@ -99,7 +99,7 @@ typedef struct hc_settings {
   double dt_max;          /* 0.05 */
   double dt_init;         /* 0.01 */
   double newton_tol;      /* FP64 corrector tolerance, 1e-8 */
-  double newton_tol_fp32; /* FP32 corrector tolerance (mixed precision), 1e-5 */
+  double newton_tol_fp32; /* FP32 corrector tolerance (mixed precision), 1e-4 */
   double max_first_corr;  /* 0.1 */
   double refine_tol;      /* endpoint refinement target, 1e-13 */
   double r_inf;           /* divergence radius, 1e8 */
@@ -107,6 +107,10 @@ typedef struct hc_settings {
   double real_tol;        /* |Im x|_inf <= real_tol * max(1, |x|_inf), 1e-8 */
   double singular_cond;   /* cond_1 bound, 1e12 */
   double t_endgame;       /* mixed precision: FP64 residuals for t > t_endgame, 0.95 */
+  double dt_min_fp32;     /* mixed precision: a path whose FP32 step falls below this is
+                             handed to the FP64 tier instead of crawling, 1e-4 */
+  double max_first_corr_fp32; /* first-correction bound of the FP32 tier, 0.01 */
+  int32_t max_steps_fp32; /* mixed precision: FP32 step budget before the hand-off, 2000 */
   int32_t max_newton;     /* 3 */
   int32_t max_steps;      /* 100000 (also the device step budget of one path) */
   int32_t grow_after;     /* 3 */
@@ -114,7 +118,6 @@ typedef struct hc_settings {
   int32_t precision;      /* HC_PREC_MIXED */
   int32_t escalate;       /* 1: mixed-precision paths that fail are re-tracked in FP64 */
   int32_t lanes;          /* lanes per path: 0 = automatic, else 4, 8, 16 or 32 */
-  int32_t reserved;
 } hc_settings;
 
 /*
@@ -181,7 +184,8 @@ typedef struct hc_batch_result {
   int64_t paths;               /* n_instances * paths per instance            */
   int64_t finite, real, diverged, singular, failed;
   int64_t escalated;           /* mixed-precision paths re-tracked in FP64      */
-  int64_t steps_accepted, steps_rejected, newton_iters;
+  int64_t steps_accepted, steps_rejected, newton_iters;  /* all tiers        */
+  int64_t esc_accepted, esc_rejected, esc_newton;        /* FP64 tier part   */
   double device_ms;            /* stream time from first copy to last copy      */
   double track_ms;             /* stream time of the tracking launch             */
   double escalate_ms;          /* stream time of the FP64 re-tracking launch     */
@@ -224,6 +228,16 @@ hc_status hc_poll(hc_batch* b, int64_t timeout_us, hc_batch_result* r);
 /* Free a problem or a batch (waits for a running batch first).  NULL is a
  * no-op.  A problem must outlive its batches. */
 void hc_destroy(void* handle);
+
+/*
+ * Measurement utility (no counterpart in the paper): FMA throughput of the
+ * current device's CUDA cores, FP32 (fp64 = 0) or FP64 (fp64 = 1), from one
+ * timed launch of independent FMA chains on every SM; iters sets the length
+ * (each thread issues iters * 128 FMAs).  *flops_per_s = 2 * FMAs / time.
+ * Used for the roofline of the ALU-bound tracker.  Errors: HC_ERR_INVALID,
+ * HC_ERR_OOM, HC_ERR_CUDA.
+ */
+hc_status hc_measure_fma_peak(int32_t fp64, int32_t iters, double* flops_per_s, double* ms);
 
 #ifdef __cplusplus
 }

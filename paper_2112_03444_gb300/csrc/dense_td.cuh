@@ -99,57 +99,53 @@ struct DenseTD {
     }
   }
 
+  // FP64 residual of row i at (x, t); x is read from the group's shared copy
+  // (xs[k], k < N) so that no FP64 vector occupies registers.  With SCALE the
+  // backward-error denominator sum |c| |x^a| (FP32 accuracy is enough for a
+  // ratio test) is returned in sc.
   template <bool SCALE>
-  __device__ __forceinline__ void residual64(const cx<double> (&x)[N], int i, double t, double omt,
+  __device__ __forceinline__ void residual64(const cx<double>* xs, int i, double t, double omt,
                                              cx<double>& H, double& sc) const {
     const cx<double>* e = E + i;
     int m = 0;
     cx<double> F = e[0];
-    double Ssum = SCALE ? cabs2(e[0]) : 0.0;
+    float Ssum = SCALE ? cabs2(cvt<float>(e[0])) : 0.f;
     m = 1;
-    cx<double> xi = x[0];
-#pragma unroll
-    for (int k = 1; k < N; ++k)
-      if (k == i) xi = x[k];
-    double ax[N];
-    if (SCALE) {
-#pragma unroll
-      for (int k = 0; k < N; ++k) ax[k] = cabs2(x[k]);
-    }
 #pragma unroll
     for (int j = 0; j < N; ++j) {
       cx<double> in = e[m * L];
-      double ins = SCALE ? cabs2(e[m * L]) : 0.0;
+      float ins = SCALE ? cabs2(cvt<float>(e[m * L])) : 0.f;
       ++m;
 #pragma unroll
       for (int k = 0; k <= j; ++k) {
         if constexpr (DEG == 2) {
-          in = cfma(e[m * L], x[k], in);
-          if (SCALE) ins += cabs2(e[m * L]) * ax[k];
+          in = cfma(e[m * L], xs[k], in);
+          if (SCALE) ins += cabs2(cvt<float>(e[m * L])) * cabs2(cvt<float>(xs[k]));
           ++m;
         } else {
           cx<double> in2 = e[m * L];
-          double in2s = SCALE ? cabs2(e[m * L]) : 0.0;
+          float in2s = SCALE ? cabs2(cvt<float>(e[m * L])) : 0.f;
           ++m;
 #pragma unroll
           for (int l = 0; l <= k; ++l) {
-            in2 = cfma(e[m * L], x[l], in2);
-            if (SCALE) in2s += cabs2(e[m * L]) * ax[l];
+            in2 = cfma(e[m * L], xs[l], in2);
+            if (SCALE) in2s += cabs2(cvt<float>(e[m * L])) * cabs2(cvt<float>(xs[l]));
             ++m;
           }
-          in = cfma(x[k], in2, in);
-          if (SCALE) ins += ax[k] * in2s;
+          in = cfma(xs[k], in2, in);
+          if (SCALE) ins += cabs2(cvt<float>(xs[k])) * in2s;
         }
       }
-      F = cfma(x[j], in, F);
-      if (SCALE) Ssum += ax[j] * ins;
+      F = cfma(xs[j], in, F);
+      if (SCALE) Ssum += cabs2(cvt<float>(xs[j])) * ins;
     }
+    const cx<double> xi = xs[i < N ? i : 0];
     const cx<double> xi2 = xi * xi;
     const cx<double> G = (DEG == 2 ? xi2 : xi2 * xi) - mk<double>(1.0, 0.0);
     H = t * F + omt * (gamma * G);
     if (SCALE) {
-      const double axi = cabs2(xi);
-      sc = t * Ssum + omt * (1.0 + (DEG == 2 ? axi * axi : axi * axi * axi));
+      const float axi = cabs2(cvt<float>(xi));
+      sc = t * (double)Ssum + omt * (double)(1.0f + (DEG == 2 ? axi * axi : axi * axi * axi));
     } else {
       sc = 0.0;
     }

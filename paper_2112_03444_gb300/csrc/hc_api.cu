@@ -76,6 +76,45 @@ __global__ void stage_dense_kernel(int64_t n_inst, int T, const double2* __restr
   }
 }
 
+// Path-jump detection: two paths of one instance that end on the same root
+// (relative infinity distance <= tol) cannot both be right, so both go to
+// the FP64 tier, restarted at t = 0.  One thread per path scans the other
+// paths of its instance; the threads of a warp read the same endpoint at the
+// same time (a broadcast load).  x32 holds NaN for paths that did not end
+// finite, which then never match.
+__global__ void dedupe_kernel(int64_t items, int64_t paths, int n, const float2* __restrict__ x32,
+                              float tol, int64_t* esc_list, unsigned long long* esc_count,
+                              double* t_io) {
+  for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < items;
+       a += (int64_t)gridDim.x * blockDim.x) {
+    const float2* xa = x32 + a * n;
+    const float2 v0 = xa[0];
+    if (isnan(v0.x)) continue;
+    float sc = 1.f;
+    for (int k = 0; k < n; ++k) sc = fmaxf(sc, fmaxf(fabsf(xa[k].x), fabsf(xa[k].y)));
+    const float thr = tol * sc;
+    const int64_t b0 = (a / paths) * paths;
+    bool dup = false;
+    for (int64_t b = b0; b < b0 + paths && !dup; ++b) {
+      if (b == a) continue;
+      const float2* xb = x32 + b * n;
+      const float2 w = xb[0];
+      if (!(fabsf(w.x - v0.x) <= thr) || !(fabsf(w.y - v0.y) <= thr)) continue;
+      bool same = true;
+      for (int k = 1; k < n && same; ++k) {
+        const float2 p = xa[k], q = xb[k];
+        same = (fabsf(p.x - q.x) <= thr) && (fabsf(p.y - q.y) <= thr);
+      }
+      dup = same;
+    }
+    if (dup) {
+      const unsigned long long pos = atomicAdd(esc_count, 1ull);
+      esc_list[pos] = a;
+      t_io[a] = 0.0;
+    }
+  }
+}
+
 // Batch summary: [0] finite [1] real [2] diverged [3] singular [4] failed
 // [5] accepted steps [6] rejected steps [7] Newton iterations
 __global__ void summarize_kernel(int64_t items, const uint8_t* __restrict__ st,
@@ -212,6 +251,9 @@ hc::DevSettings dev_settings(const hc_settings& s) {
   d.real_tol = s.real_tol;
   d.singular_cond = s.singular_cond;
   d.t_endgame = s.t_endgame;
+  d.dt_min_fp32 = s.dt_min_fp32;
+  d.max_first_corr_fp32 = s.max_first_corr_fp32;
+  d.max_steps_fp32 = s.max_steps_fp32;
   d.max_newton = s.max_newton;
   d.max_steps = s.max_steps;
   d.grow_after = s.grow_after;
@@ -224,6 +266,7 @@ hc_status validate_settings(const hc_settings& s) {
       !(s.dt_init <= s.dt_max) || s.max_newton < 1 || s.max_newton > 16 || s.max_steps < 1 ||
       s.grow_after < 1 || s.refine_iters < 0 || s.refine_iters > 64 || !(s.newton_tol > 0) ||
       !(s.newton_tol_fp32 > 0) || !(s.max_first_corr > 0) || !(s.r_inf > 0) ||
+      !(s.dt_min_fp32 >= s.dt_min) || !(s.max_first_corr_fp32 > 0) || s.max_steps_fp32 < 1 ||
       (s.precision != HC_PREC_FP64 && s.precision != HC_PREC_MIXED) ||
       (s.lanes != 0 && s.lanes != 4 && s.lanes != 8 && s.lanes != 16 && s.lanes != 32)) {
     set_err("invalid settings");
@@ -363,7 +406,7 @@ Occ occupancy(const void* fn, size_t smem) {
 
 hc_status launch_tracker(const hc::KernelRef& k, const hc::DenseArgs& a, int64_t max_items,
                          cudaStream_t st) {
-  const size_t smem = (size_t)(hc::kBlock / k.lanes) * 2 * k.lanes * sizeof(cx<double>);
+  const size_t smem = (size_t)hc::kBlock * hc::kGroupSmemBytesPerLane;
   const Occ o = occupancy(k.fn, smem);
   const int64_t groups_per_block = hc::kBlock / k.lanes;
   int64_t want = (max_items + groups_per_block - 1) / groups_per_block;
@@ -402,7 +445,7 @@ hc_settings hc_default_settings(void) {
   s.dt_max = 0.05;
   s.dt_init = 0.01;
   s.newton_tol = 1e-8;
-  s.newton_tol_fp32 = 1e-5;
+  s.newton_tol_fp32 = 1e-4;
   s.max_first_corr = 0.1;
   s.refine_tol = 1e-13;
   s.r_inf = 1e8;
@@ -410,6 +453,9 @@ hc_settings hc_default_settings(void) {
   s.real_tol = 1e-8;
   s.singular_cond = 1e12;
   s.t_endgame = 0.95;
+  s.dt_min_fp32 = 1e-4;
+  s.max_first_corr_fp32 = 0.01;
+  s.max_steps_fp32 = 2000;
   s.max_newton = 3;
   s.max_steps = 100000;
   s.grow_after = 3;
@@ -688,11 +734,18 @@ hc_status hc_track_batch(hc_problem* p, const hc_batch_desc* b, hc_batch** out) 
     std::memset(pin, 0, sizeof(unsigned long long) * 16);
   }
   int64_t* esc_list = nullptr;
+  double* t_io = nullptr;
+  float2* x32 = nullptr;
   if (escalate) {
     void* q;
     HC_TRY(dalloc(&q, sizeof(int64_t) * items));
     esc_list = (int64_t*)q;
+    HC_TRY(dalloc(&q, sizeof(double) * items));
+    t_io = (double*)q;
+    HC_TRY(dalloc(&q, sizeof(float2) * n * items));
+    x32 = (float2*)q;
   }
+  HC_TRYCUDA(cudaMemsetAsync(d_steps, 0, sizeof(int32_t) * 3 * items, st));
 
   // ---- tracking launch
   hc::DenseArgs a;
@@ -709,6 +762,9 @@ hc_status hc_track_batch(hc_problem* p, const hc_batch_desc* b, hc_batch** out) 
   a.c.be_out = d_be;
   a.c.esc_list = esc_list;
   a.c.esc_count = bt->d_ctl + 2;
+  a.c.t_io = t_io;
+  a.c.x32_out = x32;
+  a.c.esc_steps = nullptr;
   a.D32 = (const cx<float>*)D32;
   a.D64 = (const cx<double>*)D64;
   a.E = (const cx<double>*)E;
@@ -724,11 +780,19 @@ hc_status hc_track_batch(hc_problem* p, const hc_batch_desc* b, hc_batch** out) 
   HC_TRY(launch_tracker(k, a, items, st));
   HC_TRYCUDA(cudaEventRecord(bt->evk1, st));
   if (escalate) {
+    {
+      const int grid = (int)std::min<int64_t>((items + 255) / 256, 65535);
+      dedupe_kernel<<<std::max(grid, 1), 256, 0, st>>>(items, p->paths, n, x32, 1e-6f, esc_list,
+                                                      bt->d_ctl + 2, t_io);
+      HC_TRYCUDA(cudaGetLastError());
+    }
     hc::DenseArgs e = a;
     e.c.count_dev = bt->d_ctl + 2;
     e.c.items = esc_list;
     e.c.queue = bt->d_ctl + 1;
     e.c.esc_list = nullptr;
+    e.c.x32_out = nullptr;
+    e.c.esc_steps = bt->d_ctl + 3;
     const hc::KernelRef k64 = hc::dense_kernel(p->deg, n, false);
     // one block per SM is plenty for the (rare) escalated paths
     HC_TRY(launch_tracker(k64, e, std::min<int64_t>(items, 4 * 152), st));
@@ -792,6 +856,9 @@ hc_status hc_poll(hc_batch* b, int64_t timeout_us, hc_batch_result* r) {
     r->steps_rejected = (int64_t)s[6];
     r->newton_iters = (int64_t)s[7];
     r->escalated = (int64_t)b->h_ctl[2];
+    r->esc_accepted = (int64_t)b->h_ctl[3];
+    r->esc_rejected = (int64_t)b->h_ctl[4];
+    r->esc_newton = (int64_t)b->h_ctl[5];
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, b->ev0, b->ev1) == cudaSuccess) r->device_ms = ms;
     if (cudaEventElapsedTime(&ms, b->evk0, b->evk1) == cudaSuccess) r->track_ms = ms;

@@ -46,16 +46,26 @@ __device__ __forceinline__ cx<R> cfms(cx<R> a, cx<R> b, cx<R> acc) {
   return {fma(-a.re, b.re, fma(a.im, b.im, acc.re)), fma(-a.re, b.im, fma(-a.im, b.re, acc.im))};
 }
 
+// Correctly rounded reciprocal without the IEEE-division slow path.
+__device__ __forceinline__ float rcp(float v) { return __frcp_rn(v); }
+__device__ __forceinline__ double rcp(double v) { return __drcp_rn(v); }
+
 // 1/z with scaling by max(|re|, |im|) so that |z|^2 cannot overflow for
 // |z| up to the format's range.
 template <class R>
 __device__ __forceinline__ cx<R> crecip(cx<R> z) {
   const R s = fmax(fabs(z.re), fabs(z.im));
-  const R inv_s = R(1) / s;
+  const R inv_s = rcp(s);
   const R zr = z.re * inv_s, zi = z.im * inv_s;
-  const R d = R(1) / (s * fma(zr, zr, zi * zi));
+  const R d = rcp(s * fma(zr, zr, zi * zi));
   return {zr * d, -zi * d};
 }
+
+template <class R>
+__device__ __forceinline__ R cnorm2(cx<R> z) { return fma(z.re, z.re, z.im * z.im); }
+
+// sqrt of a non-negative float for threshold tests (approximate, 0 -> 0)
+__device__ __forceinline__ float sqrt_approx(float v) { return v > 0.f ? v * rsqrtf(v) : 0.f; }
 
 template <class R>
 __device__ __forceinline__ R cabs1(cx<R> z) { return fabs(z.re) + fabs(z.im); }
@@ -161,7 +171,8 @@ __device__ __forceinline__ bool gj_solve(const Group& g, cx<R> (&a)[N + NR], cx<
 struct DevSettings {
   double dt_min, dt_max, dt_init, newton_tol, newton_tol_fp32, max_first_corr;
   double refine_tol, r_inf, finite_tol, real_tol, singular_cond, t_endgame;
-  int max_newton, max_steps, grow_after, refine_iters;
+  double dt_min_fp32, max_first_corr_fp32;
+  int max_newton, max_steps, grow_after, refine_iters, max_steps_fp32;
 };
 
 enum : int {

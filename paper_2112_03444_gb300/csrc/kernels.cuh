@@ -9,6 +9,7 @@
 namespace hc {
 
 constexpr int kBlock = 128;  // threads per block of the tracking kernels
+constexpr int kGroupSmemBytesPerLane = 40;  // shared bytes per lane (see tracker.cuh)
 
 // Work distribution of a tracking launch: work item = (instance, path),
 // item = instance * paths + path; a lane group takes the next item with one
@@ -27,6 +28,10 @@ struct LaunchCommon {
   double* be_out;                       // [items] (optional)
   int64_t* esc_list;                    // mixed precision: items to re-track in FP64
   unsigned long long* esc_count;
+  // Hand-over between the FP32 and FP64 tiers:
+  double* t_io;                 // per item: t to resume from in FP64 (0 = restart at t = 0)
+  float2* x32_out;              // per item endpoint copy for duplicate detection (NaN if not finite)
+  unsigned long long* esc_steps;  // FP64 tier: accepted, rejected, Newton totals (atomic)
 };
 
 struct DenseArgs {

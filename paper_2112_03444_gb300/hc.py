@@ -42,10 +42,11 @@ class hc_settings(ctypes.Structure):
                 ("refine_tol", ctypes.c_double), ("r_inf", ctypes.c_double),
                 ("finite_tol", ctypes.c_double), ("real_tol", ctypes.c_double),
                 ("singular_cond", ctypes.c_double), ("t_endgame", ctypes.c_double),
-                ("max_newton", ctypes.c_int32), ("max_steps", ctypes.c_int32),
+                ("dt_min_fp32", ctypes.c_double), ("max_first_corr_fp32", ctypes.c_double),
+                ("max_steps_fp32", ctypes.c_int32), ("max_newton", ctypes.c_int32), ("max_steps", ctypes.c_int32),
                 ("grow_after", ctypes.c_int32), ("refine_iters", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("escalate", ctypes.c_int32),
-                ("lanes", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("lanes", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -75,6 +76,8 @@ class hc_batch_result(ctypes.Structure):
                 ("singular", ctypes.c_int64), ("failed", ctypes.c_int64),
                 ("escalated", ctypes.c_int64), ("steps_accepted", ctypes.c_int64),
                 ("steps_rejected", ctypes.c_int64), ("newton_iters", ctypes.c_int64),
+                ("esc_accepted", ctypes.c_int64), ("esc_rejected", ctypes.c_int64),
+                ("esc_newton", ctypes.c_int64),
                 ("device_ms", ctypes.c_double), ("track_ms", ctypes.c_double),
                 ("escalate_ms", ctypes.c_double)]
 
@@ -98,8 +101,21 @@ _lib.hc_poll.argtypes = [_P, ctypes.c_int64, ctypes.POINTER(hc_batch_result)]
 _lib.hc_destroy.restype = None
 _lib.hc_destroy.argtypes = [_P]
 
+_lib.hc_measure_fma_peak.restype = ctypes.c_int32
+_lib.hc_measure_fma_peak.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double)]
+
 EXPORTED = ("hc_status_string", "hc_last_error", "hc_default_settings", "hc_create_problem",
-            "hc_problem_paths", "hc_track_batch", "hc_poll", "hc_destroy")
+            "hc_problem_paths", "hc_track_batch", "hc_poll", "hc_destroy", "hc_measure_fma_peak")
+
+
+def measure_fma_peak(fp64: bool, iters: int = 20000):
+    """(FLOP/s, ms) of the device's FP32 or FP64 FMA pipe (own microbenchmark)."""
+    f = ctypes.c_double()
+    ms = ctypes.c_double()
+    _check(_lib.hc_measure_fma_peak(int(bool(fp64)), int(iters), ctypes.byref(f), ctypes.byref(ms)),
+           "hc_measure_fma_peak")
+    return f.value, ms.value
 
 
 class HCError(RuntimeError):

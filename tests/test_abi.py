@@ -34,9 +34,9 @@ def test_every_declared_symbol_is_exported(hc):
 
 
 def test_struct_layouts_match_header_sizes(hc):
-    # hc_settings: 12 doubles + 8 int32 = 128 bytes
-    assert ctypes.sizeof(hc.hc_settings) == 128
-    assert ctypes.sizeof(hc.hc_batch_result) == 13 * 8
+    # hc_settings: 14 doubles + 8 int32 = 144 bytes
+    assert ctypes.sizeof(hc.hc_settings) == 144
+    assert ctypes.sizeof(hc.hc_batch_result) == 16 * 8
 
 
 def test_default_settings_and_strings(hc):
