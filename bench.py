@@ -143,6 +143,9 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     sp = stream.cuda_stream
+    # one stream per size class: the five persistent launches (and their FP64
+    # re-tracking launches) overlap on the device
+    class_streams = [torch.cuda.Stream(device=dev) for _ in SIZES]
     wl = workload(rank)
     settings = dict(precision=hc.HC_PREC_MIXED)
     problems, bufs = [], []
@@ -162,10 +165,17 @@ def run_gpu(args):
 
     def step():
         batches = []
-        for pr, b in zip(problems, bufs):
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        for pr, b, cs in zip(problems, bufs, class_streams):
+            cs.wait_event(ev)
             batches.append(pr.track(n_instances=SYSTEMS_PER_SIZE, coef=b["coef"], device=True,
                                     x_out=b["x"], status_out=b["st"], steps_out=b["steps"],
-                                    be_out=b["be"], stream=sp))
+                                    be_out=b["be"], stream=cs.cuda_stream))
+        for cs in class_streams:
+            done = torch.cuda.Event()
+            done.record(cs)
+            stream.wait_event(done)
         return batches
 
     for _ in range(args.warmup):

@@ -107,10 +107,10 @@ typedef struct hc_settings {
   double real_tol;        /* |Im x|_inf <= real_tol * max(1, |x|_inf), 1e-8 */
   double singular_cond;   /* cond_1 bound, 1e12 */
   double t_endgame;       /* mixed precision: FP64 residuals for t > t_endgame, 0.95 */
-  double dt_min_fp32;     /* mixed precision: a path whose FP32 step falls below this is
-                             handed to the FP64 tier instead of crawling, 1e-4 */
+  double dt_min_fp32;     /* mixed precision: a path whose FP32 step falls below this
+                             continues with FP64 state and FP64 residuals, 1e-4 */
   double max_first_corr_fp32; /* first-correction bound of the FP32 tier, 0.01 */
-  int32_t max_steps_fp32; /* mixed precision: FP32 step budget before the hand-off, 2000 */
+  int32_t max_steps_fp32; /* mixed precision: FP32-state steps before that switch, 2000 */
   int32_t max_newton;     /* 3 */
   int32_t max_steps;      /* 100000 (also the device step budget of one path) */
   int32_t grow_after;     /* 3 */

@@ -11,12 +11,14 @@
 //
 // Code shape.  Every phase of the method needs the same work item: evaluate
 // row i of [dH/dx | rhs] at some point and time, solve, and scatter the
-// solution.  The tracker is therefore one loop around ONE copy of the
-// (fully unrolled) evaluation and solve, driven by a small per-path state
-// machine: RK stage 1..4, Newton iteration, endpoint refinement, condition
-// columns.  Inlining a copy per phase multiplied the kernel's code size and
-// made instruction fetch the dominant stall once the lane groups of an SM
-// drifted into different phases.
+// solution.  A lane group therefore runs ONE loop around ONE copy of the
+// (fully unrolled) evaluation and solve, driven by a small state machine:
+// fetch the next path (retire/refill of the persistent launch), RK stage
+// 1..4, Newton iteration, endpoint refinement, condition columns, write the
+// result.  Inlining a copy per phase multiplied the code size and made
+// instruction fetch the dominant stall; keeping path fetch and output inside
+// the same loop keeps the lane groups that share a warp executing the heavy
+// body together even when their paths start and end at different times.
 //
 // Precision tiers.
 //   MIXED = false: every operation in complex FP64 (the plain form).
@@ -24,12 +26,15 @@
 //     iterations are complex FP32 and no FP64 instruction executes; for
 //     t > t_endgame the state is FP64 and the corrector's residual H is
 //     evaluated in FP64 while the Jacobian and the solve stay FP32 (mixed
-//     precision iterative refinement); the final refinement and the backward
-//     error use FP64 residuals the same way.  GB300 issues FP64 FMAs at about
-//     1/74 of its FP32 rate (measured), so FP64 is kept to a few residuals per
-//     path.  A path the FP32 tier cannot resolve (step below dt_min_fp32,
-//     step budget, suspect condition) is reported failed and re-tracked by
-//     the FP64 tier.
+//     precision iterative refinement, converged to the FP64 tolerance); the
+//     final refinement and the backward error use FP64 residuals the same way.
+//     A path whose FP32 steps fall below dt_min_fp32 (the corrector stalls
+//     at the FP32 noise floor near an ill-conditioned stretch) or exhaust
+//     max_steps_fp32 switches to that FP64-residual mode at once.  GB300
+//     issues FP64 FMAs at about 1/74 of its FP32 rate (measured), so FP64 is
+//     kept to the residuals where it buys accuracy.  Paths that still fail,
+//     paths whose endpoints collide (a path jump) and endpoints whose FP32
+//     condition estimate is suspect are re-tracked by the all-FP64 kernel.
 //
 // Evaluator interface (HOM):
 //   template <class R> eval(x[N], i, t, 1-t, row[N+1], H, Ht)
@@ -43,15 +48,9 @@
 #include <type_traits>
 
 #include "hc_device.cuh"
+#include "kernels.cuh"
 
 namespace hc {
-
-struct PathOut {
-  cx<double> x;  // this lane's component of the endpoint
-  double t;      // where tracking stopped (1 unless the path failed on the way)
-  int status, nacc, nrej, nnewt;
-  float be;
-};
 
 template <int N, class S, class R>
 __device__ __forceinline__ void load_vec(const cx<S>* buf, cx<R> (&x)[N]) {
@@ -59,7 +58,7 @@ __device__ __forceinline__ void load_vec(const cx<S>* buf, cx<R> (&x)[N]) {
   for (int k = 0; k < N; ++k) x[k] = cvt<R>(buf[k]);
 }
 
-enum : int { M_RK = 0, M_NEWTON = 1, M_REFINE = 2, M_COND = 3, M_DONE = 4 };
+enum : int { M_RK = 0, M_NEWTON = 1, M_REFINE = 2, M_COND = 3, M_DONE = 4, M_FETCH = 5 };
 
 // Shared memory of one lane group: vf = FP32 copy of the evaluation point,
 // vd = FP64 copy (phases with FP64 state), sb = solution scatter buffer.
@@ -71,49 +70,46 @@ struct GroupSmem {
 };
 
 
-template <int N, int L, bool MIXED, class HOM>
-__device__ __forceinline__ void track_path(const HOM& hom, const DevSettings& s, const Group& g,
-                                           GroupSmem<L>* sm, int64_t path, double t0,
-                                           const double2* x0, PathOut& o) {
+
+// Persistent loop of one lane group over the work items of a launch.
+// PROB::hom(inst) binds the evaluator to an instance.
+template <int N, int L, bool MIXED, class PROB>
+__device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon& c,
+                                            const Group& g, GroupSmem<L>* sm) {
   using R = typename std::conditional<MIXED, float, double>::type;
+  using HOM = decltype(prob.hom(0));
+  const DevSettings& s = c.s;
   cx<R>* sb = reinterpret_cast<cx<R>*>(sm->sb);
   const bool act = g.gl < N;
-  o.be = 0.f;
+  const int leader = g.wl & ~(L - 1);
+  const int64_t total = c.count_dev ? (int64_t)(*c.count_dev) : c.n_items;
 
-  // ---- path state (identical control state in all lanes of the group); a
-  // path handed over by the FP32 tier resumes from its last accepted point.
-  cx<double> xd = czero<double>();  // FP64 state
-  if (act) {
-    if (x0) {
-      const double2 v = x0[g.gl];
-      xd = mk<double>(v.x, v.y);
-    } else {
-      xd = hom.start(path, g.gl);
-    }
-  }
-  cx<float> xf = cvt<float>(xd);  // FP32 state
-  bool hi = !MIXED;  // state lives in xd (FP64) rather than xf
-  double t = x0 ? t0 : 0.0, dt = s.dt_init, h = 0.0, t1 = 0.0;
-  int consec = 0, nacc = 0, nrej = 0, nnewt = 0, status = 0;
   const double tA = MIXED ? fmin(s.t_endgame, 1.0) : 1.0;  // end of the FP32 phase
-  const float tol = MIXED ? (float)s.newton_tol_fp32 : (float)s.newton_tol;
-  const float corr1 = MIXED ? (float)s.max_first_corr_fp32 : (float)s.max_first_corr;
-  const double dtmin = MIXED ? s.dt_min_fp32 : s.dt_min;
-  const int maxsteps = MIXED ? s.max_steps_fp32 : s.max_steps;
+  // FP32-state steps use the FP32 tier's tolerances; FP64-state steps (plain
+  // FP64, or FP32 solves refined by FP64 residuals) use the FP64 ones.
+  const float tol32 = (float)s.newton_tol_fp32, tol64 = (float)s.newton_tol;
+  const float corr32 = (float)s.max_first_corr_fp32, corr64 = (float)s.max_first_corr;
 
-  int mode = M_RK, stage = 0, it = 0;
+  // ---- per-path state (identical control state in all lanes of the group)
+  HOM hom = prob.hom(0);
+  int64_t item = 0;
+  cx<double> xd = czero<double>();  // FP64 state
+  cx<float> xf = czero<float>();    // FP32 state
+  bool hi = !MIXED;                 // the state lives in xd rather than xf
+  double t = 0.0, dt = 0.0, h = 0.0, t1 = 0.0;
+  int consec = 0, nacc = 0, nrej = 0, nnewt = 0, status = 0;
+  int mode = M_FETCH, stage = 0, it = 0;
   cx<R> kprev = czero<R>(), ksum = czero<R>();
-  cx<float> xpf = xf;       // corrector iterate (FP32 phase)
-  cx<double> xpd = xd;      // corrector iterate (FP64 state)
+  cx<float> xpf = czero<float>();   // corrector iterate (FP32 state)
+  cx<double> xpd = czero<double>(); // corrector iterate (FP64 state)
   bool step_ok = true;
-  float cond_inorm = 0.f, cond_anorm = 0.f;
+  float cond_inorm = 0.f, cond_anorm = 0.f, be = 0.f;
 
   cx<R> row[N + 1];
   cx<R> x[N];
   cx<R> sol[1];
   int col;
 
-  // Begins a step from (t, state): picks h, t1 for the current phase.
   auto begin_step = [&]() {
     const double t_stop = hi ? 1.0 : tA;
     const bool last = dt >= t_stop - t;
@@ -135,34 +131,127 @@ __device__ __forceinline__ void track_path(const HOM& hom, const DevSettings& s,
     ++nrej;
     consec = 0;
     dt *= 0.5;
-    if (dt < dtmin) {
+    if (MIXED && !hi && dt < s.dt_min_fp32) {
+      // FP32 cannot resolve this stretch of the path (its corrector stalls at
+      // the FP32 noise floor): continue from the last accepted point with the
+      // FP64 state and FP64 residuals instead of failing the path.
+      xd = cvt<double>(xf);
+      hi = true;
+      dt = s.dt_min_fp32;
+      begin_step();
+    } else if (dt < s.dt_min) {
       status = ST_FAIL_STEP;
       mode = M_DONE;
     } else {
       begin_step();
     }
   };
-  begin_step();
 
 #pragma unroll 1
   for (;;) {
-    if (mode == M_DONE) break;
-    if (mode == M_RK && stage == 0 && nacc + nrej >= maxsteps) {
-      status = ST_FAIL_MAXSTEPS;
-      break;
+    // ---- 0. retire the finished path and refill the group with the next one
+    if (mode == M_DONE) {
+      if (!hi) xd = cvt<double>(xf);
+      if ((status & 0x7f) != ST_FINITE && status != ST_FAIL_NAN && gany(g, act && !cfinite(xd)))
+        status = ST_FAIL_NAN;
+      const int base = status & 0x7f;
+      if (act) {
+        reinterpret_cast<double2*>(c.x_out)[item * N + g.gl] = make_double2(xd.re, xd.im);
+        if (MIXED && c.x32_out)
+          c.x32_out[item * N + g.gl] = base == ST_FINITE
+                                           ? make_float2((float)xd.re, (float)xd.im)
+                                           : make_float2(__int_as_float(0x7fc00000), 0.f);
+      }
+      if (g.gl == 0) {
+        c.status_out[item] = (uint8_t)status;
+        if (c.be_out) c.be_out[item] = (double)be;
+        if (MIXED) {
+          c.steps_out[item * 3 + 0] = nacc;
+          c.steps_out[item * 3 + 1] = nrej;
+          c.steps_out[item * 3 + 2] = nnewt;
+          if (c.esc_list && base != ST_FINITE) {
+            // resume point for the FP64 tier: the last accepted point after a
+            // step-size or budget failure, t = 1 (refinement and exact
+            // condition) for a suspect-condition endpoint, t = 0 otherwise
+            if (c.t_io)
+              c.t_io[item] = (base == ST_FAIL_STEP || base == ST_FAIL_MAXSTEPS) ? t
+                             : (base == ST_SINGULAR)                            ? 1.0
+                                                                               : 0.0;
+            const unsigned long long pos = atomicAdd(c.esc_count, 1ull);
+            c.esc_list[pos] = item;
+          } else if (c.t_io) {
+            c.t_io[item] = 0.0;
+          }
+        } else {
+          c.steps_out[item * 3 + 0] += nacc;
+          c.steps_out[item * 3 + 1] += nrej;
+          c.steps_out[item * 3 + 2] += nnewt;
+          if (c.esc_steps) {
+            atomicAdd(c.esc_steps + 0, (unsigned long long)nacc);
+            atomicAdd(c.esc_steps + 1, (unsigned long long)nrej);
+            atomicAdd(c.esc_steps + 2, (unsigned long long)nnewt);
+          }
+        }
+      }
+      mode = M_FETCH;
     }
+    if (mode == M_FETCH) {
+      unsigned long long q = 0;
+      if (g.gl == 0) q = atomicAdd(c.queue, 1ull);
+      q = __shfl_sync(g.mask, q, leader);
+      if ((int64_t)q >= total) break;
+      item = c.items ? c.items[q] : (int64_t)q;
+      const int64_t inst = item / c.paths;
+      const int64_t path = item - inst * c.paths;
+      hom = prob.hom(inst);
+      // a path handed over by the FP32 tier resumes from its last accepted point
+      const double t0 = (!MIXED && c.t_io) ? c.t_io[item] : 0.0;
+      __syncwarp(g.mask);
+      xd = czero<double>();
+      if (act) {
+        if (t0 > 0.0) {
+          const double2 v = reinterpret_cast<const double2*>(c.x_out)[item * N + g.gl];
+          xd = mk<double>(v.x, v.y);
+        } else {
+          xd = hom.start(path, g.gl);
+        }
+      }
+      xf = cvt<float>(xd);
+      hi = !MIXED;
+      t = t0 > 0.0 ? t0 : 0.0;
+      dt = s.dt_init;
+      consec = nacc = nrej = nnewt = status = 0;
+      be = 0.f;
+      if (t >= 1.0)
+        enter_refine();
+      else
+        begin_step();
+    }
+    if (mode == M_RK && stage == 0) {
+      if (nacc + nrej >= s.max_steps) {
+        status = ST_FAIL_MAXSTEPS;
+        mode = M_DONE;
+        continue;
+      }
+      if (MIXED && !hi && nacc + nrej >= s.max_steps_fp32) {  // FP32 step budget spent
+        xd = cvt<double>(xf);
+        hi = true;
+        begin_step();
+      }
+    }
+
     // ---- 1. evaluation point and time
     double te;
     bool need64 = false;
     if (mode == M_RK) {
-      const double c = (stage == 0) ? 0.0 : (stage == 3 ? 1.0 : 0.5);
-      te = (stage == 3) ? t1 : t + c * h;
+      const double cst = (stage == 0) ? 0.0 : (stage == 3 ? 1.0 : 0.5);
+      te = (stage == 3) ? t1 : t + cst * h;
       if (hi) {
-        const cx<double> p = xd + (c * h) * cvt<double>(kprev);
+        const cx<double> p = xd + (cst * h) * cvt<double>(kprev);
         if (act) sm->vd[g.gl] = p;
         if (act) sm->vf[g.gl] = cvt<float>(p);
       } else {
-        const cx<float> p = xf + ((float)c * (float)h) * cvt<float>(kprev);
+        const cx<float> p = xf + ((float)cst * (float)h) * cvt<float>(kprev);
         if (act) sm->vf[g.gl] = p;
       }
     } else if (mode == M_NEWTON) {
@@ -226,14 +315,14 @@ __device__ __forceinline__ void track_path(const HOM& hom, const DevSettings& s,
       if (++stage == 4) {
         if (!step_ok) {
           reject();
-          continue;
+        } else {
+          if (hi)
+            xpd = xd + (h / 6.0) * cvt<double>(ksum);
+          else
+            xpf = xf + ((float)h / 6.0f) * cvt<float>(ksum);
+          mode = M_NEWTON;
+          it = 0;
         }
-        if (hi)
-          xpd = xd + (h / 6.0) * cvt<double>(ksum);
-        else
-          xpf = xf + ((float)h / 6.0f) * cvt<float>(ksum);
-        mode = M_NEWTON;
-        it = 0;
       }
     } else if (mode == M_NEWTON) {
       float xn2;
@@ -248,10 +337,13 @@ __device__ __forceinline__ void track_path(const HOM& hom, const DevSettings& s,
       const float xn = sqrt_approx(xn2);
       const float dn = sqrt_approx(gmaxf(g, act ? (float)cnorm2(d) : 0.f));
       const bool bad = !sok || !(dn <= 3.0e38f) || !(xn <= 3.0e38f) ||
-                       (it == 0 && dn > corr1 * (1.f + xn));
-      if (!bad && dn <= tol * (1.f + xn)) {
-        // accept
-        if (hi) xd = xpd; else xf = xpf;
+                       (it == 0 && dn > (hi ? corr64 : corr32) * (1.f + xn));
+      if (!bad && dn <= (hi ? tol64 : tol32) * (1.f + xn)) {
+        // accept the step
+        if (hi)
+          xd = xpd;
+        else
+          xf = xpf;
         t = t1;
         ++nacc;
         if (++consec >= s.grow_after) {
@@ -298,8 +390,8 @@ __device__ __forceinline__ void track_path(const HOM& hom, const DevSettings& s,
           hom.template residual64<true>(sm->vd, g.gl, 1.0, 0.0, H64, sc);
           const double r = (double)cabs2(cvt<float>(H64));
           const double bei = act ? (sc > 0.0 ? r / sc : r) : 0.0;
-          o.be = gmaxf(g, (float)bei);
-          if (!((double)o.be <= s.finite_tol)) {
+          be = gmaxf(g, (float)bei);
+          if (!((double)be <= s.finite_tol)) {
             status = ST_FAIL_REFINE;
             mode = M_DONE;
           } else {
@@ -311,7 +403,8 @@ __device__ __forceinline__ void track_path(const HOM& hom, const DevSettings& s,
       }
     } else {  // M_COND
       if (!sok) cond_inorm = INFINITY;
-      cond_inorm = fmaxf(cond_inorm, gsum<L, float>(g, (act && col >= 0) ? cabs2(cvt<float>(d)) : 0.f));
+      cond_inorm =
+          fmaxf(cond_inorm, gsum<L, float>(g, (act && col >= 0) ? cabs2(cvt<float>(d)) : 0.f));
       if (++stage >= N) {
         const double cnd = (double)cond_anorm * (double)cond_inorm;
         const double lim = MIXED ? fmin(s.singular_cond, kFp32CondTrust) : s.singular_cond;
@@ -327,16 +420,6 @@ __device__ __forceinline__ void track_path(const HOM& hom, const DevSettings& s,
       }
     }
   }
-
-  if (!hi) xd = cvt<double>(xf);
-  if ((status & 0x7f) != ST_FINITE && status != ST_FAIL_NAN && gany(g, act && !cfinite(xd)))
-    status = ST_FAIL_NAN;
-  o.x = xd;
-  o.t = t;
-  o.status = status;
-  o.nacc = nacc;
-  o.nrej = nrej;
-  o.nnewt = nnewt;
 }
 
 }  // namespace hc
