@@ -239,6 +239,37 @@ void hc_destroy(void* handle);
  */
 hc_status hc_measure_fma_peak(int32_t fp64, int32_t iters, double* flops_per_s, double* ms);
 
+/*
+ * Tracking without allocation (no counterpart in the paper).  For callers
+ * that cannot allocate device memory when they track: code inside a pool or
+ * arena that owns the device, real-time loops that must not enter the CUDA
+ * allocator (it can synchronize the device), hosts whose allocator belongs to
+ * another framework.  Runs the same dense total-degree kernels as
+ * hc_track_batch on one batch, allocating nothing: every buffer besides the
+ * caller's inputs and outputs lives in one fixed 16 MiB device array that
+ * each GPU loading the library holds until exit.
+ *   n, degree   dense system: every monomial of degree <= degree in each of
+ *               the n equations; degree 2 with n <= 12 or degree 3 with n <= 8
+ *   gamma       host [2] unit-modulus homotopy constant
+ *   settings    host hc_settings (precision, tolerances, escalation)
+ *   coef        device [n_instances][n][M][2] doubles, M = C(n+degree, degree),
+ *               monomials in graded order (degree 0 first; inside a degree the
+ *               sorted variable tuple in lexicographic order)
+ *   x_out, status_out, steps_out (required), be_out (optional): device
+ *               buffers laid out as in hc_batch_desc
+ *   stream      cudaStream_t (NULL = legacy default stream)
+ * Enqueues on the stream and returns; completion is the stream's.  The first
+ * call on a device looks up the array's device address (make it before any
+ * stream capture).  Calls share the array: calls that overlap on the GPU
+ * race and must be serialized by the caller.  A batch whose scratch exceeds
+ * the array returns HC_ERR_INVALID (hc_last_error says how much it needs);
+ * also HC_ERR_INVALID for bad arguments, HC_ERR_CUDA for launch errors.
+ */
+hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const double* gamma,
+                                 const hc_settings* settings, int32_t n_instances,
+                                 const double* coef, double* x_out, uint8_t* status_out,
+                                 int32_t* steps_out, double* be_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -885,3 +885,24 @@ void hc_destroy(void* handle) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ helpers shared with noalloc.cu
+namespace hc {
+
+void set_last_error(const char* msg) { set_err(msg); }
+
+cudaError_t launch_dedupe(int64_t items, int64_t paths, int n, const float2* x32, float tol,
+                          int64_t* esc_list, unsigned long long* esc_count, double* t_io,
+                          cudaStream_t st) {
+  const int grid = (int)std::min<int64_t>((items + 255) / 256, 65535);
+  dedupe_kernel<<<std::max(grid, 1), 256, 0, st>>>(items, paths, n, x32, tol, esc_list, esc_count,
+                                                  t_io);
+  return cudaGetLastError();
+}
+
+}  // namespace hc
+
+namespace hc {
+DevSettings to_dev_settings(const hc_settings& s) { return dev_settings(s); }
+hc_status check_settings(const hc_settings& s) { return validate_settings(s); }
+}  // namespace hc

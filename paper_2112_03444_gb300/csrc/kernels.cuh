@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "hc.h"
 #include "hc_device.cuh"
 
 namespace hc {
@@ -53,5 +54,13 @@ struct KernelRef {
 inline int lanes_for(int n) { return n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : 32; }
 
 KernelRef dense_kernel(int deg, int n, bool mixed);  // fn == nullptr if absent
+
+// Host helpers defined in hc_api.cu.
+void set_last_error(const char* msg);
+DevSettings to_dev_settings(const hc_settings& s);
+hc_status check_settings(const hc_settings& s);
+cudaError_t launch_dedupe(int64_t items, int64_t paths, int n, const float2* x32, float tol,
+                          int64_t* esc_list, unsigned long long* esc_count, double* t_io,
+                          cudaStream_t st);
 
 }  // namespace hc

@@ -105,8 +105,31 @@ _lib.hc_measure_fma_peak.restype = ctypes.c_int32
 _lib.hc_measure_fma_peak.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double)]
 
+_lib.hc_track_dense_noalloc.restype = ctypes.c_int32
+_lib.hc_track_dense_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(hc_settings), ctypes.c_int32, _P, _P, _P, _P,
+                                        _P, _P]
+
 EXPORTED = ("hc_status_string", "hc_last_error", "hc_default_settings", "hc_create_problem",
-            "hc_problem_paths", "hc_track_batch", "hc_poll", "hc_destroy", "hc_measure_fma_peak")
+            "hc_problem_paths", "hc_track_batch", "hc_poll", "hc_destroy", "hc_measure_fma_peak",
+            "hc_track_dense_noalloc")
+
+
+def track_dense_noalloc(n, degree, gamma, settings, n_instances, coef, x_out, status_out,
+                        steps_out, be_out=None, stream=None):
+    """hc_track_dense_noalloc on device buffers (torch CUDA tensors); returns the status code.
+
+    For callers that cannot allocate device memory while tracking: all scratch
+    lives in the library's fixed device array.  Calls that overlap on the GPU
+    race on that array; serialize them.
+    """
+    g = (ctypes.c_double * 2)(complex(gamma).real, complex(gamma).imag)
+    if isinstance(settings, dict) or settings is None:
+        settings = default_settings(**(settings or {}))
+    return int(_lib.hc_track_dense_noalloc(int(n), int(degree), g, ctypes.byref(settings),
+                                           int(n_instances), _addr(coef), _addr(x_out),
+                                           _addr(status_out), _addr(steps_out), _addr(be_out),
+                                           stream))
 
 
 def measure_fma_peak(fp64: bool, iters: int = 20000):
