@@ -24,10 +24,10 @@ struct DenseProblem {
 template <int N, int DEG, bool MIXED>
 __global__ void __launch_bounds__(kBlock) dense_td_kernel(const DenseArgs a) {
   constexpr int L = (N <= 4) ? 4 : (N <= 8) ? 8 : (N <= 16) ? 16 : 32;
-  static_assert(sizeof(GroupSmem<L>) == kGroupSmemBytesPerLane * L, "group smem layout");
+  static_assert(group_smem_bytes(L, 0) == kGroupSmemBytesPerLane * L, "group smem layout");
   extern __shared__ __align__(16) unsigned char smem[];
   const Group g = make_group<L>();
-  GroupSmem<L>* sm = reinterpret_cast<GroupSmem<L>*>(smem) + threadIdx.x / L;
+  const GroupMem sm = make_group_mem<L>(smem, 0);
   DenseProblem<N, DEG, L> prob{&a};
   run_tracker<N, L, MIXED>(prob, a.c, g, sm);
 }

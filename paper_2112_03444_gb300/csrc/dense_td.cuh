@@ -151,6 +151,8 @@ struct DenseTD {
     }
   }
 
+  __device__ __forceinline__ void init(const Group&) const {}
+
   __device__ __forceinline__ cx<double> start(int64_t path, int i) const {
     int64_t k = path;
 #pragma unroll 1

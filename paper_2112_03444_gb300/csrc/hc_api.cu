@@ -23,6 +23,11 @@ KernelRef dense_ref_d2_32(int n);
 KernelRef dense_ref_d3_64(int n);
 KernelRef dense_ref_d3_32(int n);
 
+KernelRef term_ref_64(int n);
+KernelRef term_ref_32(int n);
+
+KernelRef term_kernel(int n, bool mixed) { return mixed ? term_ref_32(n) : term_ref_64(n); }
+
 KernelRef dense_kernel(int deg, int n, bool mixed) {
   if (deg == 2) return mixed ? dense_ref_d2_32(n) : dense_ref_d2_64(n);
   if (deg == 3) return mixed ? dense_ref_d3_32(n) : dense_ref_d3_64(n);
@@ -194,6 +199,14 @@ struct hc_problem {
   int* d_dslot = nullptr;
   float* d_dmult = nullptr;
   double* d_coef = nullptr;  // default coefficients [T][2]
+  // parameter homotopy (homogenised term tuples)
+  bool terms = false;
+  int kcnt[hc::kMaxTermEntries] = {}, koff[hc::kMaxTermEntries] = {}, kdeg[hc::kMaxTermEntries] = {};
+  int extra = 0;
+  hc::TermRec* d_rec = nullptr;
+  double2* d_s64 = nullptr;
+  double2* d_p0 = nullptr;
+  double2* d_start = nullptr;
 };
 
 struct hc_batch {
@@ -362,6 +375,96 @@ bool encode_dense(hc_problem* p, std::vector<int>& emap, std::vector<int>& dterm
   return true;
 }
 
+
+// Homogenised term tuples of a parameter homotopy (paper Sec. 6): for every
+// row i and entry e (dH_i/dx_j for e = j < n, dH_i/dt for e = n, H_i for
+// e = n + 1) a list of tuples (s, factor indices into V), V = [x | pad to L |
+// 1 | p(t) | dp].  x-derivatives by the power rule, the t-derivative by the
+// product rule over the parameter factors (dp/dt = p1 - p0).  Entries are
+// padded to a common tuple count per entry and a common factor count.
+bool encode_terms(hc_problem* p, std::vector<hc::TermRec>& rec, std::vector<double2>& s64) {
+  const int n = p->n, P = p->P, L = hc::lanes_for(n);
+  const int one = L, pbase = L + 1, dbase = L + 1 + P;
+  if (p->kind != HC_PARAMETER || n + 2 > hc::kMaxTermEntries || dbase + P > 255) return false;
+  struct Tup {
+    double re, im;
+    std::vector<int> f;
+  };
+  std::vector<std::vector<std::vector<Tup>>> tab(n + 2, std::vector<std::vector<Tup>>(n));
+  for (int k = 0; k < p->T; ++k) {
+    const int i = p->eq[k];
+    const double sr = p->coef[2 * k], si = p->coef[2 * k + 1];
+    std::vector<int> xf, pf;
+    for (int j = 0; j < n; ++j)
+      for (int a = 0; a < p->exps[(size_t)k * n + j]; ++a) xf.push_back(j);
+    for (int f = 0; f < p->maxpf; ++f) {
+      const int l = p->par[(size_t)k * p->maxpf + f];
+      if (l >= 0) pf.push_back(l);
+    }
+    auto add = [&](int e, double mult, std::vector<int> f) {
+      if (f.empty()) f.push_back(one);
+      tab[e][i].push_back(Tup{sr * mult, si * mult, std::move(f)});
+    };
+    {  // H
+      std::vector<int> f = xf;
+      for (int l : pf) f.push_back(pbase + l);
+      add(n + 1, 1.0, f);
+    }
+    for (int j = 0; j < n; ++j) {  // dH/dx_j
+      const int a = p->exps[(size_t)k * n + j];
+      if (a == 0) continue;
+      std::vector<int> f;
+      bool dropped = false;
+      for (int v : xf) {
+        if (v == j && !dropped) {
+          dropped = true;
+          continue;
+        }
+        f.push_back(v);
+      }
+      for (int l : pf) f.push_back(pbase + l);
+      add(j, (double)a, f);
+    }
+    for (size_t q = 0; q < pf.size(); ++q) {  // dH/dt
+      std::vector<int> f = xf;
+      for (size_t r = 0; r < pf.size(); ++r) f.push_back((r == q ? dbase : pbase) + pf[r]);
+      add(n, 1.0, f);
+    }
+  }
+  int off = 0;
+  for (int e = 0; e < n + 2; ++e) {
+    int K = 0, D = 1;
+    for (int i = 0; i < n; ++i) {
+      K = std::max(K, (int)tab[e][i].size());
+      for (auto& t : tab[e][i]) D = std::max(D, (int)t.f.size());
+    }
+    if (D > hc::kMaxTermFactors) return false;
+    p->kcnt[e] = K;
+    p->koff[e] = off;
+    p->kdeg[e] = D;
+    off += K;
+  }
+  rec.assign((size_t)off * L, hc::TermRec{});
+  s64.assign((size_t)off * L, make_double2(0.0, 0.0));
+  for (auto& r : rec)
+    for (int f = 0; f < hc::kMaxTermFactors; ++f) r.idx[f] = (uint8_t)one;
+  for (int e = 0; e < n + 2; ++e)
+    for (int i = 0; i < n; ++i)
+      for (size_t k = 0; k < tab[e][i].size(); ++k) {
+        const Tup& t = tab[e][i][k];
+        const size_t r = ((size_t)p->koff[e] + k) * L + i;
+        rec[r].s = make_float2((float)t.re, (float)t.im);
+        for (size_t f = 0; f < t.f.size() && f < (size_t)hc::kMaxTermFactors; ++f)
+          rec[r].idx[f] = (uint8_t)t.f[f];
+        s64[r] = make_double2(t.re, t.im);
+      }
+  p->terms = true;
+  p->L = L;
+  p->extra = 1 + 2 * P;
+  p->paths = p->n_start;
+  return true;
+}
+
 template <class T>
 hc_status upload(const std::vector<T>& v, T** out) {
   *out = nullptr;
@@ -378,6 +481,10 @@ void free_problem(hc_problem* p) {
   cudaFree(p->d_dslot);
   cudaFree(p->d_dmult);
   cudaFree(p->d_coef);
+  cudaFree(p->d_rec);
+  cudaFree(p->d_s64);
+  cudaFree(p->d_p0);
+  cudaFree(p->d_start);
   p->magic = 0;
   delete p;
 }
@@ -402,6 +509,19 @@ Occ occupancy(const void* fn, size_t smem) {
   if (o.blocks < 1) o.blocks = 1;
   cache[key] = o;
   return o;
+}
+
+hc_status launch_generic(const hc::KernelRef& k, void* args, size_t smem, int64_t max_items,
+                         cudaStream_t st) {
+  if (smem > 48 * 1024)
+    HC_CUDA(cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const Occ o = occupancy(k.fn, smem);
+  const int64_t groups_per_block = hc::kBlock / k.lanes;
+  int64_t want = (max_items + groups_per_block - 1) / groups_per_block;
+  int64_t grid = std::min<int64_t>((int64_t)o.blocks * o.sms, std::max<int64_t>(want, 1));
+  void* argv[] = {args};
+  HC_CUDA(cudaLaunchKernel(k.fn, dim3((unsigned)grid), dim3(hc::kBlock), argv, smem, st));
+  return HC_OK;
 }
 
 hc_status launch_tracker(const hc::KernelRef& k, const hc::DenseArgs& a, int64_t max_items,
@@ -536,11 +656,44 @@ hc_status hc_create_problem(const hc_problem_desc* d, hc_problem** out) {
   if (p->maxpf) p->par.assign(d->term_param, d->term_param + (size_t)T * p->maxpf);
   cudaGetDevice(&p->device);
 
+  if (d->kind == HC_PARAMETER) {
+    p->n_start = d->n_start;
+    for (int64_t k = 0; k < (int64_t)d->n_params * 2; ++k)
+      if (!std::isfinite(d->p0[k])) {
+        delete p;
+        set_err("non-finite p0");
+        return HC_ERR_NUMERIC;
+      }
+    std::vector<hc::TermRec> rec;
+    std::vector<double2> s64;
+    if (!encode_terms(p, rec, s64)) {
+      delete p;
+      set_err("parameter homotopy: n <= 32, at most 8 factors per term, L + 1 + 2 n_params <= 255");
+      return HC_ERR_UNSUPPORTED;
+    }
+    if (!hc::term_kernel(n, true).fn) {
+      delete p;
+      set_err("this build has parameter-homotopy kernels for n <= 24");
+      return HC_ERR_UNSUPPORTED;
+    }
+    std::vector<double2> p0v(d->n_params), sv((size_t)d->n_start * n);
+    for (int l = 0; l < d->n_params; ++l) p0v[l] = make_double2(d->p0[2 * l], d->p0[2 * l + 1]);
+    for (size_t k = 0; k < sv.size(); ++k) sv[k] = make_double2(d->start[2 * k], d->start[2 * k + 1]);
+    hc_status st;
+    if ((st = upload(rec, &p->d_rec)) != HC_OK || (st = upload(s64, &p->d_s64)) != HC_OK ||
+        (st = upload(p0v, &p->d_p0)) != HC_OK || (st = upload(sv, &p->d_start)) != HC_OK) {
+      free_problem(p);
+      return st;
+    }
+    *out = p;
+    return HC_OK;
+  }
   std::vector<int> emap, dterm, dslot;
   std::vector<float> dmult;
   if (!encode_dense(p, emap, dterm, dslot, dmult)) {
     delete p;
-    set_err("this build tracks dense total-degree systems of degree 2 (n <= 12) or 3 (n <= 8)");
+    set_err("this build tracks total-degree homotopies of dense systems of degree 2 (n <= 12) "
+            "or 3 (n <= 8)");
     return HC_ERR_UNSUPPORTED;
   }
   p->ndc = (int)dterm.size();
@@ -626,45 +779,60 @@ hc_status hc_track_batch(hc_problem* p, const hc_batch_desc* b, hc_batch** out) 
   HC_TRYCUDA(cudaEventCreate(&bt->evk2));
   HC_TRYCUDA(cudaEventRecord(bt->ev0, st));
 
-  // ---- coefficients on the device
-  const double* d_coef = p->d_coef;
-  int64_t coef_stride = 0;
-  if (b->coef) {
-    coef_stride = (int64_t)p->T;
-    if (devptrs || is_device_ptr(b->coef)) {
-      d_coef = b->coef;
+  void *E = nullptr, *D64 = nullptr, *D32 = nullptr;
+  const double2* d_p1 = nullptr;
+  if (p->terms) {
+    // ---- target parameters on the device
+    if (devptrs || is_device_ptr(b->p1)) {
+      d_p1 = (const double2*)b->p1;
     } else {
       void* q;
-      HC_TRY(dalloc(&q, sizeof(double) * 2 * p->T * bt->n_inst));
-      HC_TRYCUDA(cudaMemcpyAsync(q, b->coef, sizeof(double) * 2 * p->T * bt->n_inst,
+      HC_TRY(dalloc(&q, sizeof(double2) * p->P * bt->n_inst));
+      HC_TRYCUDA(cudaMemcpyAsync(q, b->p1, sizeof(double2) * p->P * bt->n_inst,
                                  cudaMemcpyHostToDevice, st));
-      d_coef = (const double*)q;
+      d_p1 = (const double2*)q;
     }
-  }
+  } else {
+    // ---- coefficients on the device
+    const double* d_coef = p->d_coef;
+    int64_t coef_stride = 0;
+    if (b->coef) {
+      coef_stride = (int64_t)p->T;
+      if (devptrs || is_device_ptr(b->coef)) {
+        d_coef = b->coef;
+      } else {
+        void* q;
+        HC_TRY(dalloc(&q, sizeof(double) * 2 * p->T * bt->n_inst));
+        HC_TRYCUDA(cudaMemcpyAsync(q, b->coef, sizeof(double) * 2 * p->T * bt->n_inst,
+                                   cudaMemcpyHostToDevice, st));
+        d_coef = (const double*)q;
+      }
+    }
 
-  // ---- encoded coefficients
-  void *E = nullptr, *D64 = nullptr, *D32 = nullptr;
-  const size_t eb = sizeof(cx<double>) * p->Estride * bt->n_inst;
-  const size_t db64 = sizeof(cx<double>) * p->Dstride * bt->n_inst;
-  const size_t db32 = sizeof(cx<float>) * p->Dstride * bt->n_inst;
-  HC_TRY(dalloc(&E, eb));
-  HC_TRYCUDA(cudaMemsetAsync(E, 0, eb, st));
-  if (!mixed || escalate) {
-    HC_TRY(dalloc(&D64, db64));
-    HC_TRYCUDA(cudaMemsetAsync(D64, 0, db64, st));
-  }
-  if (mixed) {
-    HC_TRY(dalloc(&D32, db32));
-    HC_TRYCUDA(cudaMemsetAsync(D32, 0, db32, st));
-  }
-  {
-    const int64_t work = bt->n_inst * (p->T + p->ndc);
-    const int grid = (int)std::min<int64_t>((work + 255) / 256, 4096);
-    stage_dense_kernel<<<grid, 256, 0, st>>>(bt->n_inst, p->T, (const double2*)d_coef, coef_stride,
-                                            p->d_emap, p->ndc, p->d_dterm, p->d_dslot,
-                                            p->d_dmult, (double2*)E, p->Estride, (float2*)D32,
-                                            (double2*)D64, p->Dstride);
-    HC_TRYCUDA(cudaGetLastError());
+    // ---- encoded coefficients
+    const size_t eb = sizeof(cx<double>) * p->Estride * bt->n_inst;
+    const size_t db64 = sizeof(cx<double>) * p->Dstride * bt->n_inst;
+    const size_t db32 = sizeof(cx<float>) * p->Dstride * bt->n_inst;
+    HC_TRY(dalloc(&E, eb));
+    HC_TRYCUDA(cudaMemsetAsync(E, 0, eb, st));
+    if (!mixed || escalate) {
+      HC_TRY(dalloc(&D64, db64));
+      HC_TRYCUDA(cudaMemsetAsync(D64, 0, db64, st));
+    }
+    if (mixed) {
+      HC_TRY(dalloc(&D32, db32));
+      HC_TRYCUDA(cudaMemsetAsync(D32, 0, db32, st));
+    }
+    {
+      const int64_t work = bt->n_inst * (p->T + p->ndc);
+      const int grid = (int)std::min<int64_t>((work + 255) / 256, 4096);
+      stage_dense_kernel<<<grid, 256, 0, st>>>(bt->n_inst, p->T, (const double2*)d_coef, coef_stride,
+                                              p->d_emap, p->ndc, p->d_dterm, p->d_dslot,
+                                              p->d_dmult, (double2*)E, p->Estride, (float2*)D32,
+                                              (double2*)D64, p->Dstride);
+      HC_TRYCUDA(cudaGetLastError());
+    }
+
   }
 
   // ---- outputs (device side)
@@ -748,56 +916,97 @@ hc_status hc_track_batch(hc_problem* p, const hc_batch_desc* b, hc_batch** out) 
   HC_TRYCUDA(cudaMemsetAsync(d_steps, 0, sizeof(int32_t) * 3 * items, st));
 
   // ---- tracking launch
-  hc::DenseArgs a;
-  std::memset(&a, 0, sizeof(a));
-  a.c.s = dev_settings(p->s);
-  a.c.n_items = items;
-  a.c.count_dev = nullptr;
-  a.c.items = nullptr;
-  a.c.queue = bt->d_ctl + 0;
-  a.c.paths = p->paths;
-  a.c.x_out = d_x;
-  a.c.status_out = d_status;
-  a.c.steps_out = d_steps;
-  a.c.be_out = d_be;
-  a.c.esc_list = esc_list;
-  a.c.esc_count = bt->d_ctl + 2;
-  a.c.t_io = t_io;
-  a.c.x32_out = x32;
-  a.c.esc_steps = nullptr;
-  a.D32 = (const cx<float>*)D32;
-  a.D64 = (const cx<double>*)D64;
-  a.E = (const cx<double>*)E;
-  a.Dstride = p->Dstride;
-  a.Estride = p->Estride;
-  a.gamma = cx<double>{p->gamma[0], p->gamma[1]};
-  const hc::KernelRef k = hc::dense_kernel(p->deg, n, mixed);
-  if (!k.fn) {
-    set_err("no kernel for this problem shape");
-    return fail(HC_ERR_UNSUPPORTED);
-  }
-  HC_TRYCUDA(cudaEventRecord(bt->evk0, st));
-  HC_TRY(launch_tracker(k, a, items, st));
-  HC_TRYCUDA(cudaEventRecord(bt->evk1, st));
-  if (escalate) {
-    {
-      const int grid = (int)std::min<int64_t>((items + 255) / 256, 65535);
-      dedupe_kernel<<<std::max(grid, 1), 256, 0, st>>>(items, p->paths, n, x32, 1e-6f, esc_list,
-                                                      bt->d_ctl + 2, t_io);
-      HC_TRYCUDA(cudaGetLastError());
+  hc::LaunchCommon cm;
+  std::memset(&cm, 0, sizeof(cm));
+  cm.s = dev_settings(p->s);
+  cm.n_items = items;
+  cm.count_dev = nullptr;
+  cm.items = nullptr;
+  cm.queue = bt->d_ctl + 0;
+  cm.paths = p->paths;
+  cm.x_out = d_x;
+  cm.status_out = d_status;
+  cm.steps_out = d_steps;
+  cm.be_out = d_be;
+  cm.esc_list = esc_list;
+  cm.esc_count = bt->d_ctl + 2;
+  cm.t_io = t_io;
+  cm.x32_out = x32;
+  cm.esc_steps = nullptr;
+  // the FP64 re-tracking launch: items from the escalation list
+  hc::LaunchCommon ce = cm;
+  ce.count_dev = bt->d_ctl + 2;
+  ce.items = esc_list;
+  ce.queue = bt->d_ctl + 1;
+  ce.esc_list = nullptr;
+  ce.x32_out = nullptr;
+  ce.esc_steps = bt->d_ctl + 3;
+  int sms = 0;
+  HC_TRYCUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
+  const int64_t esc_groups = std::min<int64_t>(items, 4 * (int64_t)sms);
+  auto dedupe = [&]() -> hc_status {
+    const int grid = (int)std::min<int64_t>((items + 255) / 256, 65535);
+    dedupe_kernel<<<std::max(grid, 1), 256, 0, st>>>(items, p->paths, n, x32, 1e-6f, esc_list,
+                                                    bt->d_ctl + 2, t_io);
+    HC_CUDA(cudaGetLastError());
+    return HC_OK;
+  };
+  if (p->terms) {
+    hc::TermArgs ta;
+    std::memset(&ta, 0, sizeof(ta));
+    ta.c = cm;
+    ta.rec = p->d_rec;
+    ta.s64 = p->d_s64;
+    for (int e = 0; e < hc::kMaxTermEntries; ++e) {
+      ta.kcnt[e] = p->kcnt[e];
+      ta.koff[e] = p->koff[e];
+      ta.kdeg[e] = p->kdeg[e];
     }
-    hc::DenseArgs e = a;
-    e.c.count_dev = bt->d_ctl + 2;
-    e.c.items = esc_list;
-    e.c.queue = bt->d_ctl + 1;
-    e.c.esc_list = nullptr;
-    e.c.x32_out = nullptr;
-    e.c.esc_steps = bt->d_ctl + 3;
-    const hc::KernelRef k64 = hc::dense_kernel(p->deg, n, false);
-    // one block per SM is plenty for the (rare) escalated paths
-    HC_TRY(launch_tracker(k64, e, std::min<int64_t>(items, 4 * 152), st));
+    ta.P = p->P;
+    ta.extra = p->extra;
+    ta.p0 = p->d_p0;
+    ta.p1 = d_p1;
+    ta.start = p->d_start;
+    const hc::KernelRef k = hc::term_kernel(n, mixed);
+    const int L = k.lanes;
+    const size_t smem = (size_t)(hc::kBlock / L) *
+                        ((L + p->extra) * 16 + L * 16 + (L + p->extra) * 8);
+    HC_TRYCUDA(cudaEventRecord(bt->evk0, st));
+    HC_TRY(launch_generic(k, &ta, smem, items, st));
+    HC_TRYCUDA(cudaEventRecord(bt->evk1, st));
+    if (escalate) {
+      HC_TRY(dedupe());
+      hc::TermArgs te = ta;
+      te.c = ce;
+      HC_TRY(launch_generic(hc::term_kernel(n, false), &te, smem, esc_groups, st));
+    }
+    HC_TRYCUDA(cudaEventRecord(bt->evk2, st));
+  } else {
+    hc::DenseArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.c = cm;
+    a.D32 = (const cx<float>*)D32;
+    a.D64 = (const cx<double>*)D64;
+    a.E = (const cx<double>*)E;
+    a.Dstride = p->Dstride;
+    a.Estride = p->Estride;
+    a.gamma = cx<double>{p->gamma[0], p->gamma[1]};
+    const hc::KernelRef k = hc::dense_kernel(p->deg, n, mixed);
+    if (!k.fn) {
+      set_err("no kernel for this problem shape");
+      return fail(HC_ERR_UNSUPPORTED);
+    }
+    HC_TRYCUDA(cudaEventRecord(bt->evk0, st));
+    HC_TRY(launch_tracker(k, a, items, st));
+    HC_TRYCUDA(cudaEventRecord(bt->evk1, st));
+    if (escalate) {
+      HC_TRY(dedupe());
+      hc::DenseArgs e = a;
+      e.c = ce;
+      HC_TRY(launch_tracker(hc::dense_kernel(p->deg, n, false), e, esc_groups, st));
+    }
+    HC_TRYCUDA(cudaEventRecord(bt->evk2, st));
   }
-  HC_TRYCUDA(cudaEventRecord(bt->evk2, st));
   {
     const int grid = (int)std::min<int64_t>((items + 255) / 256, 1024);
     summarize_kernel<<<std::max(grid, 1), 256, 0, st>>>(items, d_status, d_steps, bt->d_ctl + 8);

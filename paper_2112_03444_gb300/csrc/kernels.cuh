@@ -44,6 +44,27 @@ struct DenseArgs {
   cx<double> gamma;
 };
 
+// One homogenised term tuple: scalar (FP32 copy) and up to 8 factor indices
+// into the per-path vector V (see term_param.cuh).
+struct TermRec {
+  float2 s;
+  uint8_t idx[8];
+};
+constexpr int kMaxTermEntries = 34;  // N + 2 entries per row, N <= 32
+constexpr int kMaxTermFactors = 8;
+
+struct TermArgs {
+  LaunchCommon c;
+  const TermRec* rec;    // [sum_e K_e][L]
+  const double2* s64;    // FP64 scalars, same layout
+  int kcnt[kMaxTermEntries], koff[kMaxTermEntries], kdeg[kMaxTermEntries];
+  int P;                 // number of parameters
+  int extra;             // shared-memory entries behind the point: 1 + 2P
+  const double2* p0;     // [P]
+  const double2* p1;     // [instances][P]
+  const double2* start;  // [paths][n]
+};
+
 struct KernelRef {
   const void* fn;   // __global__ function
   int lanes;        // lanes per path (L)
@@ -54,6 +75,7 @@ struct KernelRef {
 inline int lanes_for(int n) { return n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : 32; }
 
 KernelRef dense_kernel(int deg, int n, bool mixed);  // fn == nullptr if absent
+KernelRef term_kernel(int n, bool mixed);            // fn == nullptr if absent
 
 // Host helpers defined in hc_api.cu.
 void set_last_error(const char* msg);

@@ -43,6 +43,9 @@
 //       xs[0..N) (shared memory), and with SCALE the backward-error
 //       denominator sum |c| |x^a| of row i
 //   start(path, i)                                 start component x_i(0)
+//   init(g)                                        per-path set-up (once per path)
+// Evaluators read the point from the group's shared copy written by the
+// tracker before every evaluation (vf for FP32, vd for FP64) or from x[].
 #pragma once
 
 #include <type_traits>
@@ -62,12 +65,27 @@ enum : int { M_RK = 0, M_NEWTON = 1, M_REFINE = 2, M_COND = 3, M_DONE = 4, M_FET
 
 // Shared memory of one lane group: vf = FP32 copy of the evaluation point,
 // vd = FP64 copy (phases with FP64 state), sb = solution scatter buffer.
-template <int L>
-struct GroupSmem {
-  cx<double> vd[L];
-  cx<double> sb[L];  // holds L values of cx<R>
-  cx<float> vf[L];
+// vf and vd hold L + extra entries: the point occupies [0, N) and an
+// evaluator may keep its own per-path values behind index L.
+struct GroupMem {
+  cx<double>* vd;
+  cx<double>* sb;  // holds L values of cx<R>
+  cx<float>* vf;
 };
+
+__host__ __device__ constexpr int group_smem_bytes(int L, int extra) {
+  return (L + extra) * 16 + L * 16 + (L + extra) * 8;
+}
+
+template <int L>
+__device__ __forceinline__ GroupMem make_group_mem(unsigned char* smem, int extra) {
+  unsigned char* b = smem + (threadIdx.x / L) * group_smem_bytes(L, extra);
+  GroupMem m;
+  m.vd = reinterpret_cast<cx<double>*>(b);
+  m.sb = reinterpret_cast<cx<double>*>(b + (L + extra) * 16);
+  m.vf = reinterpret_cast<cx<float>*>(b + (L + extra) * 16 + L * 16);
+  return m;
+}
 
 
 
@@ -75,11 +93,11 @@ struct GroupSmem {
 // PROB::hom(inst) binds the evaluator to an instance.
 template <int N, int L, bool MIXED, class PROB>
 __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon& c,
-                                            const Group& g, GroupSmem<L>* sm) {
+                                            const Group& g, const GroupMem& sm) {
   using R = typename std::conditional<MIXED, float, double>::type;
   using HOM = decltype(prob.hom(0));
   const DevSettings& s = c.s;
-  cx<R>* sb = reinterpret_cast<cx<R>*>(sm->sb);
+  cx<R>* sb = reinterpret_cast<cx<R>*>(sm.sb);
   const bool act = g.gl < N;
   const int leader = g.wl & ~(L - 1);
   const int64_t total = c.count_dev ? (int64_t)(*c.count_dev) : c.n_items;
@@ -204,6 +222,7 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
       const int64_t inst = item / c.paths;
       const int64_t path = item - inst * c.paths;
       hom = prob.hom(inst);
+      hom.init(g);  // per-path constants of the evaluator (shared memory)
       // a path handed over by the FP32 tier resumes from its last accepted point
       const double t0 = (!MIXED && c.t_io) ? c.t_io[item] : 0.0;
       __syncwarp(g.mask);
@@ -248,32 +267,32 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
       te = (stage == 3) ? t1 : t + cst * h;
       if (hi) {
         const cx<double> p = xd + (cst * h) * cvt<double>(kprev);
-        if (act) sm->vd[g.gl] = p;
-        if (act) sm->vf[g.gl] = cvt<float>(p);
+        if (act) sm.vd[g.gl] = p;
+        if (act) sm.vf[g.gl] = cvt<float>(p);
       } else {
         const cx<float> p = xf + ((float)cst * (float)h) * cvt<float>(kprev);
-        if (act) sm->vf[g.gl] = p;
+        if (act) sm.vf[g.gl] = p;
       }
     } else if (mode == M_NEWTON) {
       te = t1;
       need64 = MIXED && hi;
       if (hi) {
-        if (act) sm->vd[g.gl] = xpd;
-        if (act) sm->vf[g.gl] = cvt<float>(xpd);
+        if (act) sm.vd[g.gl] = xpd;
+        if (act) sm.vf[g.gl] = cvt<float>(xpd);
       } else {
-        if (act) sm->vf[g.gl] = xpf;
+        if (act) sm.vf[g.gl] = xpf;
       }
     } else {  // M_REFINE, M_COND: at the endpoint, t = 1
       te = 1.0;
       need64 = (mode == M_REFINE);
-      if (act) sm->vd[g.gl] = xd;
-      if (act) sm->vf[g.gl] = cvt<float>(xd);
+      if (act) sm.vd[g.gl] = xd;
+      if (act) sm.vf[g.gl] = cvt<float>(xd);
     }
     __syncwarp(g.mask);
     if constexpr (MIXED) {
-      load_vec<N, float, float>(sm->vf, x);
+      load_vec<N, float, float>(sm.vf, x);
     } else {
-      load_vec<N, double, double>(sm->vd, x);
+      load_vec<N, double, double>(sm.vd, x);
     }
 
     // ---- 2. row i of [dH/dx | rhs] and the solve
@@ -296,7 +315,7 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
       } else if (need64) {
         cx<double> H64;
         double sc;
-        hom.template residual64<false>(sm->vd, g.gl, te, 1.0 - te, H64, sc);
+        hom.template residual64<false>(sm.vd, g.gl, te, 1.0 - te, H64, sc);
         row[N] = cvt<R>(-H64);
       } else {
         row[N] = -H;
@@ -383,11 +402,11 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
           mode = M_DONE;
         } else {
           __syncwarp(g.mask);
-          if (act) sm->vd[g.gl] = xd;
+          if (act) sm.vd[g.gl] = xd;
           __syncwarp(g.mask);
           cx<double> H64;
           double sc;
-          hom.template residual64<true>(sm->vd, g.gl, 1.0, 0.0, H64, sc);
+          hom.template residual64<true>(sm.vd, g.gl, 1.0, 0.0, H64, sc);
           const double r = (double)cabs2(cvt<float>(H64));
           const double bei = act ? (sc > 0.0 ? r / sc : r) : 0.0;
           be = gmaxf(g, (float)bei);

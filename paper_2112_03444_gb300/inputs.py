@@ -129,3 +129,398 @@ def system_from_polys(n: int, polys) -> TermSystem:
 def random_complex(shape, seed) -> np.ndarray:
     rng = np.random.default_rng(seed)
     return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+# ---------------------------------------------------------------------------
+# Parameter-homotopy problem families (paper Sec. 4, configs with synthetic
+# scenes).  Polynomials are built as dicts {(x-exponent tuple, sorted param
+# index tuple): coefficient}; this is the problem statement written out as
+# data, not part of the method.
+# ---------------------------------------------------------------------------
+
+class _Poly:
+    """Polynomial in unknowns x (n) whose coefficients are monomials in params."""
+
+    __slots__ = ("n", "t")
+
+    def __init__(self, n, terms=None):
+        self.n = n
+        self.t = dict(terms or {})
+
+    @staticmethod
+    def const(n, c):
+        return _Poly(n, {((0,) * n, ()): complex(c)})
+
+    @staticmethod
+    def var(n, j, c=1.0):
+        e = [0] * n
+        e[j] = 1
+        return _Poly(n, {(tuple(e), ()): complex(c)})
+
+    @staticmethod
+    def param(n, l, c=1.0):
+        return _Poly(n, {((0,) * n, (l,)): complex(c)})
+
+    def __add__(self, o):
+        if not isinstance(o, _Poly):
+            o = _Poly.const(self.n, o)
+        t = dict(self.t)
+        for k, v in o.t.items():
+            t[k] = t.get(k, 0) + v
+        return _Poly(self.n, {k: v for k, v in t.items() if v != 0})
+
+    __radd__ = __add__
+
+    def __neg__(self):
+        return _Poly(self.n, {k: -v for k, v in self.t.items()})
+
+    def __sub__(self, o):
+        return self + (-o if isinstance(o, _Poly) else -complex(o))
+
+    def __rsub__(self, o):
+        return (-self) + o
+
+    def __mul__(self, o):
+        if not isinstance(o, _Poly):
+            return _Poly(self.n, {k: v * o for k, v in self.t.items() if v * o != 0})
+        t = {}
+        for (e1, p1), c1 in self.t.items():
+            for (e2, p2), c2 in o.t.items():
+                k = (tuple(a + b for a, b in zip(e1, e2)), tuple(sorted(p1 + p2)))
+                t[k] = t.get(k, 0) + c1 * c2
+        return _Poly(self.n, {k: v for k, v in t.items() if v != 0})
+
+    __rmul__ = __mul__
+
+
+def _system_from(n, n_params, polys, name):
+    eqs, cf, ex, pa = [], [], [], []
+    maxpf = max((len(p) for poly in polys for (_, p) in poly.t), default=0)
+    for i, poly in enumerate(polys):
+        for (e, p), c in sorted(poly.t.items()):
+            eqs.append(i)
+            cf.append(c)
+            ex.append(e)
+            pa.append(list(p) + [-1] * (maxpf - len(p)))
+    return TermSystem(n=n, term_eq=np.array(eqs), term_coef=np.array(cf),
+                      term_exp=np.array(ex, dtype=np.uint8).reshape(-1, n),
+                      term_param=np.array(pa, dtype=np.int32).reshape(-1, maxpf),
+                      n_params=n_params, name=name)
+
+
+@dataclass
+class ParamFamily:
+    """A parameter-homotopy problem family F(x; p)."""
+
+    system: TermSystem
+    unknowns: list            # names of the unknowns, in order
+    params: list              # names of the parameters, in order
+    linear_params: list       # indices of params in which F is affine (for seeding)
+    unit_groups: list         # unknown-index groups constrained by q.q = 1
+    name: str
+
+
+def triangulation_family(views: int = 4) -> ParamFamily:
+    """N-view optimal triangulation by Lagrange multipliers (paper Sec. 4).
+
+    Unknowns: image corrections (u_k, v_k), k = 1..N, and one multiplier
+    lambda_ij per view pair i < j: 2N + N(N-1)/2 unknowns (14 for N = 4).
+    Parameters: normalised image points (xi_k, eta_k) and the nine entries of
+    each pairwise essential matrix E_ij (row-major): 2N + 9 N(N-1)/2 (62).
+    With g_k = (xi_k - u_k, eta_k - v_k, 1) the Lagrangian is
+      sum_k (u_k^2 + v_k^2) + sum_{i<j} lambda_ij g_j^T E_ij g_i
+    and the equations are its derivatives (all quadratic):
+      2 u_k - sum_{i<k} l_ik e1^T E_ik g_i - sum_{j>k} l_kj g_j^T E_kj e1 = 0
+      2 v_k - (same with e2) = 0
+      g_j^T E_ij g_i = 0.
+    """
+    N = views
+    pairs = [(i, j) for i in range(N) for j in range(i + 1, N)]
+    n = 2 * N + len(pairs)
+    P = 2 * N + 9 * len(pairs)
+    U = lambda k: 2 * k
+    V = lambda k: 2 * k + 1
+    LAM = {pr: 2 * N + a for a, pr in enumerate(pairs)}
+    XI = lambda k: 2 * k
+    ETA = lambda k: 2 * k + 1
+    EP = {pr: 2 * N + 9 * a for a, pr in enumerate(pairs)}
+
+    def g(k):
+        return [_Poly.param(n, XI(k)) - _Poly.var(n, U(k)),
+                _Poly.param(n, ETA(k)) - _Poly.var(n, V(k)),
+                _Poly.const(n, 1.0)]
+
+    def E(pr, a, b):
+        return _Poly.param(n, EP[pr] + 3 * a + b)
+
+    def bil(pr, left, right):  # left^T E_pr right
+        out = _Poly(n)
+        for a in range(3):
+            for b in range(3):
+                out = out + left[a] * E(pr, a, b) * right[b]
+        return out
+
+    unit = [[_Poly.const(n, 1.0), _Poly(n), _Poly(n)], [_Poly(n), _Poly.const(n, 1.0), _Poly(n)]]
+    polys = []
+    for k in range(N):
+        for c, var in ((0, U), (1, V)):
+            eq = _Poly.var(n, var(k), 2.0)
+            for (i, j) in pairs:
+                lam = _Poly.var(n, LAM[(i, j)])
+                if j == k:     # d/du_j of g_j^T E g_i = -e^T E g_i
+                    eq = eq - lam * bil((i, j), unit[c], g(i))
+                elif i == k:   # d/du_i of g_j^T E g_i = -g_j^T E e
+                    eq = eq - lam * bil((i, j), g(j), [unit[c][0], unit[c][1], unit[c][2]])
+            polys.append(eq)
+    for pr in pairs:
+        polys.append(bil(pr, g(pr[1]), g(pr[0])))
+    unknowns = [f"{s}{k + 1}" for k in range(N) for s in ("u", "v")] + \
+               [f"l{i + 1}{j + 1}" for (i, j) in pairs]
+    params = [f"{s}{k + 1}" for k in range(N) for s in ("xi", "eta")] + \
+             [f"E{i + 1}{j + 1}_{a}{b}" for (i, j) in pairs for a in range(3) for b in range(3)]
+    return ParamFamily(system=_system_from(n, P, polys, f"triangulation{N}"), unknowns=unknowns,
+                       params=params, linear_params=list(range(2 * N, P)), unit_groups=[],
+                       name=f"triangulation{N}")
+
+
+def _quat_rot(q):
+    """Rotation matrix (list of lists of _Poly) of an unnormalised quaternion (q0, q1, q2, q3)."""
+    q0, q1, q2, q3 = q
+    return [[q0 * q0 + q1 * q1 - q2 * q2 - q3 * q3, 2 * (q1 * q2 - q0 * q3), 2 * (q1 * q3 + q0 * q2)],
+            [2 * (q1 * q2 + q0 * q3), q0 * q0 - q1 * q1 + q2 * q2 - q3 * q3, 2 * (q2 * q3 - q0 * q1)],
+            [2 * (q1 * q3 - q0 * q2), 2 * (q2 * q3 + q0 * q1), q0 * q0 - q1 * q1 - q2 * q2 + q3 * q3]]
+
+
+def trifocal_family() -> ParamFamily:
+    """Trifocal relative pose with a shared unknown focal length (paper Sec. 4).
+
+    Unknowns (18): phi (= s/f, pixel coordinates pre-scaled by s), the
+    quaternions q12, q13 of R_12, R_13, T_12 = (a, b, 1) (affine chart fixing
+    the scale), T_13 (3), and the depths rho_p of the four points in view 1.
+    Parameters (24): image coordinates (xi_vp, eta_vp) of point p in view v,
+    principal point subtracted and divided by s.  With
+      w = rho_p R(q_1v) (phi xi_1p, phi eta_1p, 1)^T + T_1v
+    the depth in view v is w_3 and the equations are
+      phi xi_vp w_3 - w_1 = 0,  phi eta_vp w_3 - w_2 = 0   (v = 2, 3; 16 equations)
+      q12 . q12 - 1 = 0,  q13 . q13 - 1 = 0.
+    """
+    n, P = 18, 24
+    PHI, Q12, Q13, AB, T13, RHO = 0, 1, 5, 9, 11, 14
+    X = lambda j: _Poly.var(n, j)
+    PXI = lambda v, p: _Poly.param(n, 2 * (3 * p + v))       # view v = 0, 1, 2
+    PETA = lambda v, p: _Poly.param(n, 2 * (3 * p + v) + 1)
+    phi = X(PHI)
+    polys = []
+    for v, qb in ((1, Q12), (2, Q13)):
+        R = _quat_rot([X(qb + a) for a in range(4)])
+        T = [X(AB), X(AB + 1), _Poly.const(n, 1.0)] if v == 1 else [X(T13 + a) for a in range(3)]
+        for p in range(4):
+            g1 = [phi * PXI(0, p), phi * PETA(0, p), _Poly.const(n, 1.0)]
+            w = []
+            for a in range(3):
+                acc = T[a]
+                for b in range(3):
+                    acc = acc + X(RHO + p) * R[a][b] * g1[b]
+                w.append(acc)
+            polys.append(phi * PXI(v, p) * w[2] - w[0])
+            polys.append(phi * PETA(v, p) * w[2] - w[1])
+    for qb in (Q12, Q13):
+        polys.append(sum((X(qb + a) * X(qb + a) for a in range(4)), _Poly(n)) - 1.0)
+    unknowns = ["phi"] + [f"q12_{a}" for a in range(4)] + [f"q13_{a}" for a in range(4)] + \
+               ["a", "b"] + [f"T13_{a}" for a in range(3)] + [f"rho{p + 1}" for p in range(4)]
+    params = [f"{s}{v + 1}_{p + 1}" for p in range(4) for v in range(3) for s in ("xi", "eta")]
+    linear = [2 * (3 * p + v) + c for p in range(4) for v in (1, 2) for c in (0, 1)]
+    return ParamFamily(system=_system_from(n, P, polys, "trifocal_f"), unknowns=unknowns,
+                       params=params, linear_params=sorted(linear),
+                       unit_groups=[list(range(Q12, Q12 + 4)), list(range(Q13, Q13 + 4))],
+                       name="trifocal_f")
+
+
+# ---------------------------------------------------------------- scenes
+def _rot_axis_angle(axis, ang):
+    axis = np.asarray(axis, float)
+    axis = axis / np.linalg.norm(axis)
+    K = np.array([[0, -axis[2], axis[1]], [axis[2], 0, -axis[0]], [-axis[1], axis[0], 0]])
+    return np.eye(3) + np.sin(ang) * K + (1 - np.cos(ang)) * K @ K
+
+
+def _quat_of(R):
+    """A unit quaternion (q0, q1, q2, q3) with _quat_rot(q) = R (Shepperd's method)."""
+    tr = np.trace(R)
+    if tr > 0:
+        s = 2.0 * np.sqrt(tr + 1.0)
+        q = [0.25 * s, (R[2, 1] - R[1, 2]) / s, (R[0, 2] - R[2, 0]) / s, (R[1, 0] - R[0, 1]) / s]
+    else:
+        i = int(np.argmax(np.diag(R)))
+        j, k = (i + 1) % 3, (i + 2) % 3
+        s = 2.0 * np.sqrt(1.0 + R[i, i] - R[j, j] - R[k, k])
+        q = [0.0] * 4
+        q[0] = (R[k, j] - R[j, k]) / s
+        q[1 + i] = 0.25 * s
+        q[1 + j] = (R[j, i] + R[i, j]) / s
+        q[1 + k] = (R[k, i] + R[i, k]) / s
+    return np.array(q)
+
+
+def triangulation_scene(seed: int, views: int = 4, noise_px: float = 1.0, f: float = 1000.0,
+                        width: int = 1920, height: int = 1080, pose_noise_deg: float = 2.0,
+                        pose_noise_t: float = 0.03):
+    """Synthetic N-view scene: pinhole cameras (focal f px) on the radius-5
+    sphere looking at the origin, random roll, one 3D point uniform in the
+    centred unit cube, projections with N(0, noise_px) pixel noise.
+
+    Each essential matrix E_ij (g_j^T E_ij g_i = 0) comes from its own
+    perturbed relative pose: rotation by N(0, pose_noise_deg) degrees about a
+    random axis, translation direction perturbed by N(0, pose_noise_t).
+    Pairwise-estimated essential matrices are never exactly consistent; with
+    exactly consistent ones the pairwise constraints of three or more views
+    are redundant at the data and the Lagrange system's optimum is a singular
+    root (pose_noise_deg = pose_noise_t = 0 gives that degenerate case).
+
+    Returns (p1, truth): p1 = parameter vector (normalised image points and
+    the nine entries of each E_ij), truth = dict with the noise-free image
+    points packed with the same E's (p_clean), cameras and the 3D point.
+    """
+    rng = np.random.default_rng([seed, 0x7A1])
+    Kinv = np.linalg.inv(np.array([[f, 0, width / 2], [0, f, height / 2], [0, 0, 1.0]]))
+    for _attempt in range(1000):
+        X = rng.uniform(-0.5, 0.5, 3)
+        Rs, ts, pix = [], [], []
+        ok = True
+        for _ in range(views):
+            c = rng.standard_normal(3)
+            c = 5.0 * c / np.linalg.norm(c)
+            z = -c / np.linalg.norm(c)                       # optical axis towards the origin
+            tmp = np.array([0.0, 0.0, 1.0]) if abs(z[2]) < 0.9 else np.array([1.0, 0.0, 0.0])
+            x = np.cross(tmp, z); x /= np.linalg.norm(x)
+            y = np.cross(z, x)
+            R = np.stack([x, y, z])                          # world -> camera
+            roll = rng.uniform(0, 2 * np.pi)
+            R = _rot_axis_angle([0, 0, 1], roll) @ R
+            t = -R @ c
+            xc = R @ X + t
+            if xc[2] <= 0:
+                ok = False
+                break
+            u = f * xc[0] / xc[2] + width / 2
+            v = f * xc[1] / xc[2] + height / 2
+            if not (0 <= u < width and 0 <= v < height):
+                ok = False
+                break
+            Rs.append(R); ts.append(t); pix.append((u, v))
+        if ok:
+            break
+    pairs = [(i, j) for i in range(views) for j in range(i + 1, views)]
+    Es = []
+    for (i, j) in pairs:
+        Rij = Rs[j] @ Rs[i].T
+        tij = ts[j] - Rij @ ts[i]
+        if pose_noise_deg > 0:
+            Rij = _rot_axis_angle(rng.standard_normal(3),
+                                  np.deg2rad(rng.normal(0, pose_noise_deg))) @ Rij
+        if pose_noise_t > 0:
+            nrm = np.linalg.norm(tij)
+            tij = tij / nrm + rng.normal(0, pose_noise_t, 3)
+            tij = tij / np.linalg.norm(tij) * nrm
+        tx = np.array([[0, -tij[2], tij[1]], [tij[2], 0, -tij[0]], [-tij[1], tij[0], 0]])
+        Es.append(tx @ Rij)
+
+    def pack(pixels):
+        pts = []
+        for (u, v) in pixels:
+            g = Kinv @ np.array([u, v, 1.0])
+            pts += [g[0], g[1]]
+        return np.array(pts + [e for E in Es for e in E.reshape(-1)], dtype=np.complex128)
+
+    noisy = [(u + rng.normal(0, noise_px), v + rng.normal(0, noise_px)) for (u, v) in pix]
+    return pack(noisy), dict(p_clean=pack(pix), R=Rs, t=ts, X=X, pixels=pix, f=f)
+
+
+def trifocal_scene(seed: int, noise_px: float = 0.5, width: int = 1920, height: int = 1080,
+                   scale: float = 1000.0):
+    """Synthetic three-view scene for the trifocal family: f ~ U[500, 2000] px
+    shared by the three cameras, camera 1 at the identity, R_12, R_13 about a
+    random axis by U[0, 30] degrees, T_1v of random direction and length
+    U[0.5, 1.5], four points with pixel position uniform in image 1 and depth
+    U[2, 10], visible in all views; N(0, noise_px) pixel noise.
+
+    Returns (p1, truth): truth has p_clean and the ground-truth unknowns
+    x_true in the family's chart (T_12 scaled to (a, b, 1)).
+    """
+    rng = np.random.default_rng([seed, 0x7F1])
+    for _attempt in range(1000):
+        f = rng.uniform(500, 2000)
+        Rv, Tv = [np.eye(3)], [np.zeros(3)]
+        for _ in range(2):
+            ax = rng.standard_normal(3)
+            Rv.append(_rot_axis_angle(ax, np.deg2rad(rng.uniform(0, 30))))
+            d = rng.standard_normal(3)
+            Tv.append(d / np.linalg.norm(d) * rng.uniform(0.5, 1.5))
+        pts, ok = [], True
+        for _p in range(4):
+            for _try in range(100):
+                u, v = rng.uniform(0, width), rng.uniform(0, height)
+                z = rng.uniform(2, 10)
+                Xc = z * np.array([(u - width / 2) / f, (v - height / 2) / f, 1.0])
+                proj = []
+                good = True
+                for k in range(3):
+                    xk = Rv[k] @ Xc + Tv[k]
+                    if xk[2] <= 0:
+                        good = False
+                        break
+                    uk, vk = f * xk[0] / xk[2] + width / 2, f * xk[1] / xk[2] + height / 2
+                    if not (0 <= uk < width and 0 <= vk < height):
+                        good = False
+                        break
+                    proj.append((uk, vk))
+                if good:
+                    pts.append((Xc, proj))
+                    break
+            else:
+                ok = False
+                break
+        if ok and abs(Tv[1][2]) > 0.05:
+            break
+
+    def pack(pixlists):
+        out = []
+        for proj in pixlists:
+            for (uk, vk) in proj:
+                out += [(uk - width / 2) / scale, (vk - height / 2) / scale]
+        return np.array(out, dtype=np.complex128)
+
+    clean = [proj for (_, proj) in pts]
+    noisy = [[(uk + rng.normal(0, noise_px), vk + rng.normal(0, noise_px)) for (uk, vk) in proj]
+             for proj in clean]
+    sz = Tv[1][2]
+    x = [scale / f] + list(_quat_of(Rv[1])) + list(_quat_of(Rv[2])) + \
+        [Tv[1][0] / sz, Tv[1][1] / sz] + list(Tv[2] / sz) + [Xc[2] / sz for (Xc, _) in pts]
+    return pack(noisy), dict(p_clean=pack(clean), x_true=np.array(x, dtype=np.complex128), f=f,
+                             R=Rv, T=Tv)
+
+
+def dense_parameter_family(n: int, d: int, seed: int):
+    """A dense random system written as a parameter family whose parameters
+    are its coefficients: F(x; p) = sum_k p_k x^alpha_k (one parameter per
+    term).  Returns (system, p1, p0) with p1 = the random coefficients and
+    p0 = gamma * G embedded in the same support (coefficient gamma on
+    x_i^d, -gamma on the constant of equation i, 0 elsewhere), so that
+    F(x; (1-t) p0 + t p1) = (1-t) gamma G(x) + t F(x): the total-degree
+    homotopy written as a parameter homotopy.
+    """
+    base = dense_system(n, d, seed)
+    T = base.n_terms
+    sys_ = TermSystem(n=n, term_eq=base.term_eq, term_coef=np.ones(T, np.complex128),
+                      term_exp=base.term_exp, term_param=np.arange(T, dtype=np.int32)[:, None],
+                      n_params=T, name=f"dense_param_n{n}_d{d}_s{seed}")
+    g = unit_gamma(seed)
+    p0 = np.zeros(T, np.complex128)
+    for k in range(T):
+        i = int(base.term_eq[k])
+        e = base.term_exp[k]
+        if e.sum() == 0:
+            p0[k] = -g
+        elif e[i] == d and e.sum() == d:
+            p0[k] = g
+    return sys_, base.term_coef.copy(), p0
