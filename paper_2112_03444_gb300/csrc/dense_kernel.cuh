@@ -11,12 +11,15 @@ namespace hc {
 template <int N, int DEG, int L>
 struct DenseProblem {
   const DenseArgs* a;
+  GroupMem sm;
   __device__ __forceinline__ DenseTD<N, DEG, L> hom(int64_t inst) const {
     DenseTD<N, DEG, L> h;
     h.D32 = a->D32 ? a->D32 + inst * a->Dstride : nullptr;
     h.D64 = a->D64 ? a->D64 + inst * a->Dstride : nullptr;
     h.E = a->E + inst * a->Estride;
     h.gamma = a->gamma;
+    h.Vf = sm.vf;
+    h.Vd = sm.vd;
     return h;
   }
 };
@@ -28,7 +31,7 @@ __global__ void __launch_bounds__(kBlock) dense_td_kernel(const DenseArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Group g = make_group<L>();
   const GroupMem sm = make_group_mem<L>(smem, 0);
-  DenseProblem<N, DEG, L> prob{&a};
+  DenseProblem<N, DEG, L> prob{&a, sm};
   run_tracker<N, L, MIXED>(prob, a.c, g, sm);
 }
 

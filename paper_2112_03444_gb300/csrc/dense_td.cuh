@@ -47,42 +47,77 @@ struct DenseTD {
   const cx<double>* D64;
   const cx<double>* E;
   cx<double> gamma;
+  const cx<float>* Vf;   // the group's shared copies of the evaluation point
+  const cx<double>* Vd;
 
   template <class R>
   __device__ __forceinline__ const cx<R>* dptr() const;
+  template <class R>
+  __device__ __forceinline__ const cx<R>* vptr() const {
+    if constexpr (std::is_same<R, float>::value)
+      return Vf;
+    else
+      return Vd;
+  }
 
+  // The contraction index k runs in a loop that is not unrolled (x_k is read
+  // from the group's shared copy of the point); the rows j stay unrolled so
+  // that row[] lives in registers.  Code size O(N) instead of O(N^2) / O(N^3).
   template <class R>
   __device__ __forceinline__ void eval(const cx<R> (&x)[N], int i, R t, R omt, cx<R> (&row)[N + 1],
                                        cx<R>& H, cx<R>& Ht) const {
     const cx<R>* D = dptr<R>() + i;
+    const cx<R>* V = vptr<R>();
+    cx<R> a1[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) a1[j] = czero<R>();
+#pragma unroll 1
+    for (int k = 0; k < N; ++k) {
+      const cx<R> xk = V[k];
+      const cx<R>* Dk = D + (1 + k) * L;
+#pragma unroll
+      for (int j = 0; j < N; ++j) a1[j] = cfma(Dk[j * S::MP * L], xk, a1[j]);
+    }
     cx<R> F = D[(N * S::MP) * L];
+    if constexpr (DEG == 2) {
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        const cx<R> a0 = D[(j * S::MP) * L];
+        row[j] = a0 + a1[j];
+        F = cfma(x[j], a0 + R(0.5) * a1[j], F);
+      }
+    } else {
+      cx<R> a2[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) a2[j] = czero<R>();
+#pragma unroll 1
+      for (int k = 0; k < N; ++k) {
+        cx<R> in[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) in[j] = czero<R>();
+        const int base = S::idx2(k, k);
+#pragma unroll 1
+        for (int l = k; l < N; ++l) {
+          const cx<R> xl = V[l];
+          const cx<R>* Dl = D + (base + (l - k)) * L;
+#pragma unroll
+          for (int j = 0; j < N; ++j) in[j] = cfma(Dl[j * S::MP * L], xl, in[j]);
+        }
+        const cx<R> xk = V[k];
+#pragma unroll
+        for (int j = 0; j < N; ++j) a2[j] = cfma(xk, in[j], a2[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        const cx<R> a0 = D[(j * S::MP) * L];
+        row[j] = a0 + a1[j] + a2[j];
+        F = cfma(x[j], a0 + R(0.5) * a1[j] + R(1.0 / 3.0) * a2[j], F);
+      }
+    }
     cx<R> xi = x[0];
 #pragma unroll
     for (int k = 1; k < N; ++k)
       if (k == i) xi = x[k];
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-      const cx<R>* Dj = D + (j * S::MP) * L;
-      const cx<R> a0 = Dj[0];
-      cx<R> a1 = czero<R>();
-#pragma unroll
-      for (int k = 0; k < N; ++k) a1 = cfma(Dj[(1 + k) * L], x[k], a1);
-      if constexpr (DEG == 2) {
-        row[j] = a0 + a1;
-        F = cfma(x[j], a0 + R(0.5) * a1, F);
-      } else {
-        cx<R> a2 = czero<R>();
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-          cx<R> in = czero<R>();
-#pragma unroll
-          for (int l = k; l < N; ++l) in = cfma(Dj[S::idx2(k, l) * L], x[l], in);
-          a2 = cfma(x[k], in, a2);
-        }
-        row[j] = a0 + a1 + a2;
-        F = cfma(x[j], a0 + R(0.5) * a1 + R(1.0 / 3.0) * a2, F);
-      }
-    }
     // G_i = xi^d - 1, dG_i/dx_i = d xi^(d-1)
     const cx<R> xi2 = xi * xi;
     const cx<R> G = (DEG == 2 ? xi2 : xi2 * xi) - mk<R>(R(1), R(0));

@@ -115,6 +115,7 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
   cx<float> xf = czero<float>();    // FP32 state
   bool hi = !MIXED;                 // the state lives in xd rather than xf
   double t = 0.0, dt = 0.0, h = 0.0, t1 = 0.0;
+  float tf = 0.f, hf = 0.f, t1f = 0.f;  // FP32 copies for the FP32 phase
   int consec = 0, nacc = 0, nrej = 0, nnewt = 0, status = 0;
   int mode = M_FETCH, stage = 0, it = 0;
   cx<R> kprev = czero<R>(), ksum = czero<R>();
@@ -133,6 +134,9 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
     const bool last = dt >= t_stop - t;
     h = last ? t_stop - t : dt;
     t1 = last ? t_stop : t + h;
+    tf = (float)t;
+    hf = (float)h;
+    t1f = (float)t1;
     stage = 0;
     ksum = czero<R>();
     kprev = czero<R>();
@@ -259,22 +263,26 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
       }
     }
 
-    // ---- 1. evaluation point and time
-    double te;
+    // ---- 1. evaluation point and time (FP32 arithmetic in the FP32 phase)
+    double te = 1.0;
+    float tef = 1.f;
     bool need64 = false;
     if (mode == M_RK) {
-      const double cst = (stage == 0) ? 0.0 : (stage == 3 ? 1.0 : 0.5);
-      te = (stage == 3) ? t1 : t + cst * h;
       if (hi) {
+        const double cst = (stage == 0) ? 0.0 : (stage == 3 ? 1.0 : 0.5);
+        te = (stage == 3) ? t1 : t + cst * h;
         const cx<double> p = xd + (cst * h) * cvt<double>(kprev);
         if (act) sm.vd[g.gl] = p;
         if (act) sm.vf[g.gl] = cvt<float>(p);
       } else {
-        const cx<float> p = xf + ((float)cst * (float)h) * cvt<float>(kprev);
+        const float cst = (stage == 0) ? 0.f : (stage == 3 ? 1.f : 0.5f);
+        tef = (stage == 3) ? t1f : tf + cst * hf;
+        const cx<float> p = xf + (cst * hf) * cvt<float>(kprev);
         if (act) sm.vf[g.gl] = p;
       }
     } else if (mode == M_NEWTON) {
       te = t1;
+      tef = t1f;
       need64 = MIXED && hi;
       if (hi) {
         if (act) sm.vd[g.gl] = xpd;
@@ -283,7 +291,6 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
         if (act) sm.vf[g.gl] = xpf;
       }
     } else {  // M_REFINE, M_COND: at the endpoint, t = 1
-      te = 1.0;
       need64 = (mode == M_REFINE);
       if (act) sm.vd[g.gl] = xd;
       if (act) sm.vf[g.gl] = cvt<float>(xd);
@@ -298,7 +305,7 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
     // ---- 2. row i of [dH/dx | rhs] and the solve
     {
       cx<R> H, Ht;
-      const R ter = (R)te;
+      const R ter = hi ? (R)te : (R)tef;
       const R omt = hi ? (R)(1.0 - te) : R(1) - ter;
       hom.template eval<R>(x, g.gl, ter, omt, row, H, Ht);
       if (mode == M_RK) {
@@ -338,7 +345,7 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
           if (hi)
             xpd = xd + (h / 6.0) * cvt<double>(ksum);
           else
-            xpf = xf + ((float)h / 6.0f) * cvt<float>(ksum);
+            xpf = xf + (hf / 6.0f) * cvt<float>(ksum);
           mode = M_NEWTON;
           it = 0;
         }
