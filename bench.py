@@ -160,18 +160,22 @@ def run_gpu(args):
             be=torch.zeros((I, P), dtype=torch.float64, device=dev)))
         problems.append(pr)
     total_paths = sum(p.paths * SYSTEMS_PER_SIZE for p in problems)
+    order = sorted(range(len(wl)), key=lambda i: -problems[i].paths * wl[i]["n"] ** 2)
     total_systems = SYSTEMS_PER_SIZE * len(problems)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step():
-        batches = []
+        batches = [None] * len(problems)
         ev = torch.cuda.Event()
         ev.record(stream)
-        for pr, b, cs in zip(problems, bufs, class_streams):
+        # largest class first: later classes' launches fill the SMs while the
+        # earlier ones finish their re-tracking tails
+        for i in order:
+            pr, b, cs = problems[i], bufs[i], class_streams[i]
             cs.wait_event(ev)
-            batches.append(pr.track(n_instances=SYSTEMS_PER_SIZE, coef=b["coef"], device=True,
-                                    x_out=b["x"], status_out=b["st"], steps_out=b["steps"],
-                                    be_out=b["be"], stream=cs.cuda_stream))
+            batches[i] = pr.track(n_instances=SYSTEMS_PER_SIZE, coef=b["coef"], device=True,
+                                  x_out=b["x"], status_out=b["st"], steps_out=b["steps"],
+                                  be_out=b["be"], stream=cs.cuda_stream)
         for cs in class_streams:
             done = torch.cuda.Event()
             done.record(cs)
@@ -352,6 +356,20 @@ def run_reference(args):
                          d2h_bytes_per_step=0))
 
 
+def run_case(spec):
+    """One dense size class, tracked twice (for profilers): spec = "n,d,instances"."""
+    import torch
+    from paper_2112_03444_gb300 import hc, inputs
+    n, d, ni = (int(v) for v in spec.split(","))
+    torch.cuda.set_device(0)
+    seeds = [SEED0 + k for k in range(ni)]
+    base, coefs = inputs.dense_batch(n, d, seeds)
+    pr = hc.Problem(base, gamma=inputs.unit_gamma(seeds[0]), settings=dict(escalate=0))
+    for _ in range(2):
+        bt = pr.track(n_instances=ni, coef=coefs).wait()
+    print(json.dumps(dict(case=spec, **bt.result)))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -361,7 +379,12 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=160)
     ap.add_argument("--ref-sample", type=int, default=48)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--case", default=None,
+                    help="profiling helper: track one dense class 'n,d,instances' twice and exit")
     args = ap.parse_args()
+    if args.case:
+        run_case(args.case)
+        return
     if args.impl == "reference":
         line = run_reference(args)
     else:

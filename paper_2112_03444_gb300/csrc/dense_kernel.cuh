@@ -25,7 +25,7 @@ struct DenseProblem {
 };
 
 template <int N, int DEG, bool MIXED>
-__global__ void __launch_bounds__(kBlock) dense_td_kernel(const DenseArgs a) {
+__global__ void __launch_bounds__(kBlock, 4) dense_td_kernel(const DenseArgs a) {
   constexpr int L = (N <= 4) ? 4 : (N <= 8) ? 8 : (N <= 16) ? 16 : 32;
   static_assert(group_smem_bytes(L, 0) == kGroupSmemBytesPerLane * L, "group smem layout");
   extern __shared__ __align__(16) unsigned char smem[];

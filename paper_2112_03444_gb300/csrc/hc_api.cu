@@ -82,8 +82,8 @@ __global__ void stage_dense_kernel(int64_t n_inst, int T, const double2* __restr
 }
 
 // Path-jump detection: two paths of one instance that end on the same root
-// (relative infinity distance <= tol) cannot both be right, so both go to
-// the FP64 tier, restarted at t = 0.  One thread per path scans the other
+// (relative infinity distance <= tol) cannot both be right, so both are
+// re-tracked from t = 0 with FP64-quality step acceptance.  One thread per path scans the other
 // paths of its instance; the threads of a warp read the same endpoint at the
 // same time (a broadcast load).  x32 holds NaN for paths that did not end
 // finite, which then never match.
@@ -902,12 +902,15 @@ hc_status hc_track_batch(hc_problem* p, const hc_batch_desc* b, hc_batch** out) 
     std::memset(pin, 0, sizeof(unsigned long long) * 16);
   }
   int64_t* esc_list = nullptr;
+  int64_t* dup_list = nullptr;
   double* t_io = nullptr;
   float2* x32 = nullptr;
   if (escalate) {
     void* q;
     HC_TRY(dalloc(&q, sizeof(int64_t) * items));
     esc_list = (int64_t*)q;
+    HC_TRY(dalloc(&q, sizeof(int64_t) * items));
+    dup_list = (int64_t*)q;
     HC_TRY(dalloc(&q, sizeof(double) * items));
     t_io = (double*)q;
     HC_TRY(dalloc(&q, sizeof(float2) * n * items));
@@ -933,7 +936,16 @@ hc_status hc_track_batch(hc_problem* p, const hc_batch_desc* b, hc_batch** out) 
   cm.t_io = t_io;
   cm.x32_out = x32;
   cm.esc_steps = nullptr;
-  // the FP64 re-tracking launch: items from the escalation list
+  // Re-tracking tiers.  Colliding paths (dup_list, ctl[7]) run again from
+  // t = 0 in the mixed kernel with the FP64 state, FP64 residuals and FP64
+  // tolerances; whatever still fails there or failed in the FP32 tier
+  // (esc_list, ctl[2]) runs in the all-FP64 kernel.
+  hc::LaunchCommon cd = cm;
+  cd.count_dev = bt->d_ctl + 7;
+  cd.items = dup_list;
+  cd.queue = bt->d_ctl + 6;
+  cd.x32_out = nullptr;
+  cd.start_hi = 1;
   hc::LaunchCommon ce = cm;
   ce.count_dev = bt->d_ctl + 2;
   ce.items = esc_list;
@@ -946,8 +958,8 @@ hc_status hc_track_batch(hc_problem* p, const hc_batch_desc* b, hc_batch** out) 
   const int64_t esc_groups = std::min<int64_t>(items, 4 * (int64_t)sms);
   auto dedupe = [&]() -> hc_status {
     const int grid = (int)std::min<int64_t>((items + 255) / 256, 65535);
-    dedupe_kernel<<<std::max(grid, 1), 256, 0, st>>>(items, p->paths, n, x32, 1e-6f, esc_list,
-                                                    bt->d_ctl + 2, t_io);
+    dedupe_kernel<<<std::max(grid, 1), 256, 0, st>>>(items, p->paths, n, x32, 1e-6f, dup_list,
+                                                    bt->d_ctl + 7, t_io);
     HC_CUDA(cudaGetLastError());
     return HC_OK;
   };
@@ -976,6 +988,9 @@ hc_status hc_track_batch(hc_problem* p, const hc_batch_desc* b, hc_batch** out) 
     HC_TRYCUDA(cudaEventRecord(bt->evk1, st));
     if (escalate) {
       HC_TRY(dedupe());
+      hc::TermArgs td = ta;
+      td.c = cd;
+      HC_TRY(launch_generic(k, &td, smem, esc_groups, st));
       hc::TermArgs te = ta;
       te.c = ce;
       HC_TRY(launch_generic(hc::term_kernel(n, false), &te, smem, esc_groups, st));
@@ -1001,6 +1016,9 @@ hc_status hc_track_batch(hc_problem* p, const hc_batch_desc* b, hc_batch** out) 
     HC_TRYCUDA(cudaEventRecord(bt->evk1, st));
     if (escalate) {
       HC_TRY(dedupe());
+      hc::DenseArgs dd = a;
+      dd.c = cd;
+      HC_TRY(launch_tracker(k, dd, esc_groups, st));
       hc::DenseArgs e = a;
       e.c = ce;
       HC_TRY(launch_tracker(hc::dense_kernel(p->deg, n, false), e, esc_groups, st));
@@ -1064,7 +1082,7 @@ hc_status hc_poll(hc_batch* b, int64_t timeout_us, hc_batch_result* r) {
     r->steps_accepted = (int64_t)s[5];
     r->steps_rejected = (int64_t)s[6];
     r->newton_iters = (int64_t)s[7];
-    r->escalated = (int64_t)b->h_ctl[2];
+    r->escalated = (int64_t)b->h_ctl[2] + (int64_t)b->h_ctl[7];
     r->esc_accepted = (int64_t)b->h_ctl[3];
     r->esc_rejected = (int64_t)b->h_ctl[4];
     r->esc_newton = (int64_t)b->h_ctl[5];

@@ -207,9 +207,10 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
   const size_t d64_b = align256(sizeof(double2) * Ds * n_instances);
   const size_t d32_b = align256(sizeof(float2) * Ds * n_instances);
   const size_t esc_b = escalate ? align256(sizeof(int64_t) * items) : 0;
+  const size_t dup_b = esc_b;
   const size_t tio_b = escalate ? align256(sizeof(double) * items) : 0;
   const size_t x32_b = escalate ? align256(sizeof(float2) * n * items) : 0;
-  const size_t need = ctl_b + e_b + d64_b + d32_b + esc_b + tio_b + x32_b;
+  const size_t need = ctl_b + e_b + d64_b + d32_b + esc_b + dup_b + tio_b + x32_b;
   if (need > kNoAllocScratchBytes) {
     char msg[200];
     std::snprintf(msg, sizeof(msg),
@@ -233,6 +234,8 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
   p += d32_b;
   int64_t* esc = escalate ? reinterpret_cast<int64_t*>(p) : nullptr;
   p += esc_b;
+  int64_t* dup = escalate ? reinterpret_cast<int64_t*>(p) : nullptr;
+  p += dup_b;
   double* t_io = escalate ? reinterpret_cast<double*>(p) : nullptr;
   p += tio_b;
   float2* x32 = escalate ? reinterpret_cast<float2*>(p) : nullptr;
@@ -302,7 +305,14 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
   }
   NA_CUDA(launch(k, a, items));
   if (escalate) {
-    NA_CUDA(hc::launch_dedupe(items, paths, n, x32, 1e-6f, esc, ctl + 2, t_io, st));
+    NA_CUDA(hc::launch_dedupe(items, paths, n, x32, 1e-6f, dup, ctl + 7, t_io, st));
+    hc::DenseArgs dd = a;
+    dd.c.count_dev = ctl + 7;
+    dd.c.items = dup;
+    dd.c.queue = ctl + 6;
+    dd.c.x32_out = nullptr;
+    dd.c.start_hi = 1;
+    NA_CUDA(launch(k, dd, items < 4 * sms ? items : 4 * sms));
     hc::DenseArgs e = a;
     e.c.count_dev = ctl + 2;
     e.c.items = esc;

@@ -240,7 +240,7 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
         }
       }
       xf = cvt<float>(xd);
-      hi = !MIXED;
+      hi = !MIXED || c.start_hi;
       t = t0 > 0.0 ? t0 : 0.0;
       dt = s.dt_init;
       consec = nacc = nrej = nnewt = status = 0;
