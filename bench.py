@@ -356,6 +356,88 @@ def run_reference(args):
                          d2h_bytes_per_step=0))
 
 
+# ---------------------------------------------------------------- serving
+def serve_mix(args):
+    """Poisson arrivals of single-system requests drawn from {dense quadratics
+    n = 4..12, 4-view triangulation, trifocal pose}: continuous batching on
+    the GPU versus the plain FP64 one-launch-per-system form."""
+    import threading
+    import torch
+    from paper_2112_03444_gb300 import hc, inputs
+    torch.cuda.set_device(0)
+    start_dir = os.path.join(ROOT, "paper_2112_03444_gb300", "startsets")
+
+    def problems(precision):
+        probs = []
+        for n in range(4, 13):
+            probs.append((f"quad{n}", hc.Problem(inputs.dense_system(n, 2, 700 + n),
+                                                  gamma=inputs.unit_gamma(700 + n),
+                                                  settings=dict(precision=precision)),
+                          lambda s, n=n: inputs.dense_coefficients(n, 2, s).reshape(-1)))
+        z = np.load(os.path.join(start_dir, "triangulation4.npz"))
+        probs.append(("triangulation4", hc.Problem(inputs.triangulation_family(4).system,
+                                                    kind=hc.HC_PARAMETER, p0=z["p0"],
+                                                    start=z["start"],
+                                                    settings=dict(precision=precision)),
+                      lambda s: inputs.triangulation_scene(s)[0]))
+        tf = os.path.join(start_dir, "trifocal_f.npz")
+        if os.path.exists(tf) and not args.no_trifocal:
+            z = np.load(tf)
+            probs.append(("trifocal_f", hc.Problem(inputs.trifocal_family().system,
+                                                    kind=hc.HC_PARAMETER, p0=z["p0"],
+                                                    start=z["start"],
+                                                    settings=dict(precision=precision)),
+                          lambda s: inputs.trifocal_scene(s)[0]))
+        return probs
+
+    def run(probs, rate, count, streams, max_batch, seed):
+        rng = np.random.default_rng([seed, int(rate)])
+        kinds = rng.integers(0, len(probs), size=count)
+        gaps = rng.exponential(1.0 / rate, size=count)
+        payload = [probs[k][2](10_000 + j) for j, k in enumerate(kinds)]
+        srv = hc.Server(n_streams=streams, max_batch_instances=max_batch)
+        ids = [None] * count
+        t0 = time.perf_counter()
+
+        def producer():
+            t = t0
+            for j, k in enumerate(kinds):
+                t += gaps[j]
+                while time.perf_counter() < t:
+                    pass
+                ids[j] = srv.submit(probs[k][1], payload[j])
+
+        th = threading.Thread(target=producer)
+        th.start()
+        th.join()
+        lat, paths, finite = [], 0, 0
+        for j, k in enumerate(kinds):
+            x, st, info = srv.wait(ids[j], probs[k][1])
+            lat.append(info["latency_us"] / 1e3)
+            paths += info["paths"]
+            finite += info["finite"]
+        wall = time.perf_counter() - t0
+        stats = srv.stats()
+        srv.close()
+        return dict(offered_per_s=rate, requests=count, systems_per_s=count / wall,
+                    paths_per_s=finite / wall, p50_ms=float(np.percentile(lat, 50)),
+                    p99_ms=float(np.percentile(lat, 99)), recovery=finite / paths,
+                    batches=stats["batches"], max_inflight_batches=stats["max_inflight_batches"])
+
+    mixed = problems(hc.HC_PREC_MIXED)
+    rows = []
+    for rate in [float(r) for r in args.rates.split(",")]:
+        count = int(max(50, min(rate * args.duration, 20000)))
+        rows.append(dict(form="mixed continuous batching", **run(mixed, rate, count, 4, 64, 1)))
+    fp64 = problems(hc.HC_PREC_FP64)
+    rate = float(args.rates.split(",")[0])
+    rows.append(dict(form="plain FP64, one launch per system",
+                     **run(fp64, rate, args.fp64_requests, 1, 1, 1)))
+    line = dict(metric=METRIC, mode="serving", workload="Poisson mix of " +
+                ", ".join(p[0] for p in mixed), rows=rows)
+    print(json.dumps(line), flush=True)
+
+
 def run_case(spec):
     """One dense size class, tracked twice (for profilers): spec = "n,d,instances"."""
     import torch
@@ -379,11 +461,20 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=160)
     ap.add_argument("--ref-sample", type=int, default=48)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving mix: Poisson arrivals, continuous batching vs plain FP64")
+    ap.add_argument("--rates", default="1000,2000,5000,10000,20000")
+    ap.add_argument("--duration", type=float, default=2.0)
+    ap.add_argument("--fp64-requests", type=int, default=60)
+    ap.add_argument("--no-trifocal", action="store_true")
     ap.add_argument("--case", default=None,
                     help="profiling helper: track one dense class 'n,d,instances' twice and exit")
     args = ap.parse_args()
     if args.case:
         run_case(args.case)
+        return
+    if args.serve:
+        serve_mix(args)
         return
     if args.impl == "reference":
         line = run_reference(args)

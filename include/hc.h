@@ -211,6 +211,20 @@ hc_status hc_create_problem(const hc_problem_desc* d, hc_problem** out);
 /* Paths per instance of a problem (prod d_i, or n_start); -1 for NULL. */
 int64_t hc_problem_paths(const hc_problem* p);
 
+/* Static facts of a problem, for callers that size buffers or admit work. */
+typedef struct hc_problem_info {
+  int32_t n;                  /* unknowns                                        */
+  int32_t kind;               /* HC_TOTAL_DEGREE or HC_PARAMETER                 */
+  int32_t inputs_per_instance;/* complex inputs per instance: n_terms (coef) or
+                                 n_params (p1)                                   */
+  int32_t lanes;              /* lanes per path of its kernels                   */
+  int64_t paths;              /* paths per instance                              */
+  int64_t device_bytes_per_instance; /* device memory one instance of a batch
+                                 needs (inputs, encoded data, outputs, scratch)  */
+} hc_problem_info;
+
+hc_status hc_problem_query(const hc_problem* p, hc_problem_info* out);
+
 /*
  * Enqueue one batch on b->stream and return at once with *out set.  Staging
  * of coefficients, the tracking launch and the result copies all run on the
@@ -228,6 +242,61 @@ hc_status hc_poll(hc_batch* b, int64_t timeout_us, hc_batch_result* r);
 /* Free a problem or a batch (waits for a running batch first).  NULL is a
  * no-op.  A problem must outlive its batches. */
 void hc_destroy(void* handle);
+
+/*
+ * Continuous-batching server (serving form of the tracker; the paper tracks
+ * one system per launch).  Requests -- one system instance each: the
+ * coefficients (HC_TOTAL_DEGREE) or target parameters (HC_PARAMETER) of one
+ * problem -- are queued per problem.  A dispatcher thread forms a batch from
+ * whatever is pending for a problem as soon as one of n_streams streams is
+ * free and the device memory of the in-flight batches plus the new one stays
+ * within max_device_bytes (a request that alone exceeds the cap runs when
+ * nothing else is in flight).  Requests that arrive while others run are
+ * admitted as streams and memory free up, so their work overlaps on the
+ * device.  Results are the same whether a request runs alone or in a batch:
+ * every path is computed independently.
+ */
+typedef struct hc_server hc_server;  /* opaque */
+
+typedef struct hc_server_config {
+  int32_t n_streams;           /* concurrent batches (streams), default 4            */
+  int32_t max_batch_instances; /* instances per batch, default 64                    */
+  int64_t max_device_bytes;    /* admission cap on in-flight batches, default 8 GiB  */
+} hc_server_config;
+
+typedef struct hc_request_info {
+  int64_t paths;               /* paths of the request                               */
+  int64_t finite, real;        /* status counts                                      */
+  double queue_us;             /* submit -> dispatch                                 */
+  double latency_us;           /* submit -> result on the host                       */
+  int32_t batch_instances;     /* size of the batch it ran in                        */
+  int32_t reserved;
+} hc_request_info;
+
+/* Default configuration. */
+hc_server_config hc_server_default_config(void);
+
+/* Start a server on the current device (creates its streams and thread).
+ * Errors: HC_ERR_INVALID, HC_ERR_CUDA, HC_ERR_OOM. */
+hc_status hc_server_create(const hc_server_config* cfg, hc_server** out);
+
+/* Queue one request: input = host [inputs_per_instance][2] doubles (copied
+ * before return).  *request_id identifies it.  The problem must outlive the
+ * server.  Errors: HC_ERR_INVALID. */
+hc_status hc_server_submit(hc_server* s, hc_problem* p, const double* input,
+                           uint64_t* request_id);
+
+/* Wait at most timeout_us (< 0: without limit) for a request; on HC_OK copy
+ * its endpoints (host [paths][n][2] doubles, may be NULL) and statuses (host
+ * [paths] uint8, may be NULL), fill *info (may be NULL) and release the
+ * request.  HC_PENDING if not done within the timeout; HC_ERR_INVALID for an
+ * unknown id; a batch error is returned as its status. */
+hc_status hc_server_wait(hc_server* s, uint64_t request_id, int64_t timeout_us, double* x_out,
+                         uint8_t* status_out, hc_request_info* info);
+
+/* Counters since creation: [0] requests done [1] batches [2] max batches in
+ * flight at once [3] max in-flight device bytes [4] max instances in a batch. */
+hc_status hc_server_stats(hc_server* s, int64_t* out5);
 
 /*
  * Measurement utility (no counterpart in the paper): FMA throughput of the

@@ -232,6 +232,35 @@ struct hc_batch {
 
 namespace {
 
+// Pinned host slots for the per-batch control words (cudaMallocHost per
+// batch would cost far more than a small batch's tracking).
+struct PinnedPool {
+  std::mutex mu;
+  std::vector<void*> free_slots;
+};
+PinnedPool& pinned_pool() {
+  static PinnedPool pool;
+  return pool;
+}
+constexpr size_t kCtlBytes = sizeof(unsigned long long) * 16;
+void* pinned_slot_get() {
+  PinnedPool& pp = pinned_pool();
+  std::lock_guard<std::mutex> lk(pp.mu);
+  if (pp.free_slots.empty()) {
+    void* chunk = nullptr;
+    if (cudaMallocHost(&chunk, kCtlBytes * 256) != cudaSuccess) return nullptr;
+    for (int i = 0; i < 256; ++i) pp.free_slots.push_back(static_cast<char*>(chunk) + i * kCtlBytes);
+  }
+  void* q = pp.free_slots.back();
+  pp.free_slots.pop_back();
+  return q;
+}
+void pinned_slot_put(void* q) {
+  PinnedPool& pp = pinned_pool();
+  std::lock_guard<std::mutex> lk(pp.mu);
+  pp.free_slots.push_back(q);
+}
+
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -713,6 +742,25 @@ int64_t hc_problem_paths(const hc_problem* p) {
   return p->paths;
 }
 
+hc_status hc_problem_query(const hc_problem* p, hc_problem_info* out) {
+  if (!p || p->magic != kProblemMagic || !out) {
+    set_err("invalid problem");
+    return HC_ERR_INVALID;
+  }
+  out->n = p->n;
+  out->kind = p->kind;
+  out->inputs_per_instance = p->kind == HC_PARAMETER ? p->P : p->T;
+  out->lanes = p->terms ? hc::term_kernel(p->n, true).lanes : p->L;
+  out->paths = p->paths;
+  const int64_t P = p->paths, n = p->n;
+  int64_t b = 16 * (int64_t)out->inputs_per_instance;                // inputs
+  if (!p->terms) b += 16 * p->Estride + 24 * p->Dstride;             // E, D64, D32
+  b += P * (16 * n + 1 + 12 + 8);                                    // x, status, steps, be
+  b += P * (8 + 8 + 8 + 8 * n);                                      // two lists, t_io, x32
+  out->device_bytes_per_instance = b;
+  return HC_OK;
+}
+
 hc_status hc_track_batch(hc_problem* p, const hc_batch_desc* b, hc_batch** out) {
   g_err.clear();
   if (!p || p->magic != kProblemMagic || !b || !out || b->n_instances < 1 || !b->x_out ||
@@ -744,6 +792,7 @@ hc_status hc_track_batch(hc_problem* p, const hc_batch_desc* b, hc_batch** out) 
     cudaStreamSynchronize(st);
     for (void* q : bt->dev) cudaFree(q);
     for (void* q : bt->pinned) cudaFreeHost(q);
+    if (bt->h_ctl) pinned_slot_put(bt->h_ctl);
     for (cudaEvent_t e : {bt->ev0, bt->ev1, bt->evk0, bt->evk1, bt->evk2})
       if (e) cudaEventDestroy(e);
     delete bt;
@@ -892,12 +941,11 @@ hc_status hc_track_batch(hc_problem* p, const hc_batch_desc* b, hc_batch** out) 
     HC_TRY(dalloc(&q, sizeof(unsigned long long) * 16));
     bt->d_ctl = (unsigned long long*)q;
     HC_TRYCUDA(cudaMemsetAsync(q, 0, sizeof(unsigned long long) * 16, st));
-    void* pin;
-    if (cudaMallocHost(&pin, sizeof(unsigned long long) * 16) != cudaSuccess) {
+    void* pin = pinned_slot_get();
+    if (!pin) {
       set_err("cudaMallocHost failed");
       return fail(HC_ERR_OOM);
     }
-    bt->pinned.push_back(pin);
     bt->h_ctl = (unsigned long long*)pin;
     std::memset(pin, 0, sizeof(unsigned long long) * 16);
   }
@@ -1097,6 +1145,7 @@ hc_status hc_poll(hc_batch* b, int64_t timeout_us, hc_batch_result* r) {
 void hc_destroy(void* handle) {
   if (!handle) return;
   const uint32_t magic = *static_cast<uint32_t*>(handle);
+  if (hc::destroy_server_if(handle, magic)) return;
   if (magic == kProblemMagic) {
     free_problem(static_cast<hc_problem*>(handle));
   } else if (magic == kBatchMagic) {
@@ -1105,6 +1154,7 @@ void hc_destroy(void* handle) {
     for (void* q : b->dev) cudaFreeAsync(q, b->stream);
     cudaStreamSynchronize(b->stream);
     for (void* q : b->pinned) cudaFreeHost(q);
+    if (b->h_ctl) pinned_slot_put(b->h_ctl);
     for (cudaEvent_t e : {b->ev0, b->ev1, b->evk0, b->evk1, b->evk2}) cudaEventDestroy(e);
     b->magic = 0;
     delete b;

@@ -80,6 +80,9 @@ inline int lanes_for(int n) { return n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : 32
 KernelRef dense_kernel(int deg, int n, bool mixed);  // fn == nullptr if absent
 KernelRef term_kernel(int n, bool mixed);            // fn == nullptr if absent
 
+// Defined in server.cu: frees a server if magic is the server's magic.
+bool destroy_server_if(void* handle, uint32_t magic);
+
 // Host helpers defined in hc_api.cu.
 void set_last_error(const char* msg);
 DevSettings to_dev_settings(const hc_settings& s);

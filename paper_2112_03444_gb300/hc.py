@@ -105,14 +105,104 @@ _lib.hc_measure_fma_peak.restype = ctypes.c_int32
 _lib.hc_measure_fma_peak.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double)]
 
+class hc_problem_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("kind", ctypes.c_int32),
+                ("inputs_per_instance", ctypes.c_int32), ("lanes", ctypes.c_int32),
+                ("paths", ctypes.c_int64), ("device_bytes_per_instance", ctypes.c_int64)]
+
+
+class hc_server_config(ctypes.Structure):
+    _fields_ = [("n_streams", ctypes.c_int32), ("max_batch_instances", ctypes.c_int32),
+                ("max_device_bytes", ctypes.c_int64)]
+
+
+class hc_request_info(ctypes.Structure):
+    _fields_ = [("paths", ctypes.c_int64), ("finite", ctypes.c_int64), ("real", ctypes.c_int64),
+                ("queue_us", ctypes.c_double), ("latency_us", ctypes.c_double),
+                ("batch_instances", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+_lib.hc_problem_query.restype = ctypes.c_int32
+_lib.hc_problem_query.argtypes = [_P, ctypes.POINTER(hc_problem_info)]
+_lib.hc_server_default_config.restype = hc_server_config
+_lib.hc_server_create.restype = ctypes.c_int32
+_lib.hc_server_create.argtypes = [ctypes.POINTER(hc_server_config), ctypes.POINTER(_P)]
+_lib.hc_server_submit.restype = ctypes.c_int32
+_lib.hc_server_submit.argtypes = [_P, _P, _P, ctypes.POINTER(ctypes.c_uint64)]
+_lib.hc_server_wait.restype = ctypes.c_int32
+_lib.hc_server_wait.argtypes = [_P, ctypes.c_uint64, ctypes.c_int64, _P, _P,
+                                ctypes.POINTER(hc_request_info)]
+_lib.hc_server_stats.restype = ctypes.c_int32
+_lib.hc_server_stats.argtypes = [_P, ctypes.POINTER(ctypes.c_int64 * 5)]
+
 _lib.hc_track_dense_noalloc.restype = ctypes.c_int32
 _lib.hc_track_dense_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(hc_settings), ctypes.c_int32, _P, _P, _P, _P,
                                         _P, _P]
 
 EXPORTED = ("hc_status_string", "hc_last_error", "hc_default_settings", "hc_create_problem",
-            "hc_problem_paths", "hc_track_batch", "hc_poll", "hc_destroy", "hc_measure_fma_peak",
-            "hc_track_dense_noalloc")
+            "hc_problem_paths", "hc_problem_query", "hc_track_batch", "hc_poll", "hc_destroy",
+            "hc_measure_fma_peak", "hc_track_dense_noalloc", "hc_server_default_config",
+            "hc_server_create", "hc_server_submit", "hc_server_wait", "hc_server_stats")
+
+
+def problem_query(problem: int) -> dict:
+    info = hc_problem_info()
+    _check(_lib.hc_problem_query(problem, ctypes.byref(info)), "hc_problem_query")
+    return {k: getattr(info, k) for k, _ in info._fields_}
+
+
+class Server:
+    """Continuous-batching server (hc_server_*): submit single instances of
+    any number of problems; the library batches what is pending per problem
+    and overlaps batches on n_streams streams under a device-memory cap."""
+
+    def __init__(self, n_streams=None, max_batch_instances=None, max_device_bytes=None):
+        cfg = _lib.hc_server_default_config()
+        if n_streams is not None:
+            cfg.n_streams = n_streams
+        if max_batch_instances is not None:
+            cfg.max_batch_instances = max_batch_instances
+        if max_device_bytes is not None:
+            cfg.max_device_bytes = max_device_bytes
+        h = _P()
+        _check(_lib.hc_server_create(ctypes.byref(cfg), ctypes.byref(h)), "hc_server_create")
+        self.h = h.value
+
+    def submit(self, problem, inp) -> int:
+        a = np.ascontiguousarray(inp, np.complex128)
+        rid = ctypes.c_uint64()
+        _check(_lib.hc_server_submit(self.h, problem.h, a.ctypes.data, ctypes.byref(rid)),
+               "hc_server_submit")
+        return rid.value
+
+    def wait(self, rid, problem, timeout_us=-1):
+        x = np.zeros((problem.paths, problem.n), np.complex128)
+        st = np.zeros(problem.paths, np.uint8)
+        info = hc_request_info()
+        code = _lib.hc_server_wait(self.h, rid, int(timeout_us), x.ctypes.data, st.ctypes.data,
+                                   ctypes.byref(info))
+        if code == HC_PENDING:
+            return None
+        _check(code, "hc_server_wait")
+        return x, st, info.as_dict()
+
+    def stats(self) -> dict:
+        a = (ctypes.c_int64 * 5)()
+        _check(_lib.hc_server_stats(self.h, ctypes.byref(a)), "hc_server_stats")
+        return dict(done=a[0], batches=a[1], max_inflight_batches=a[2],
+                    max_inflight_bytes=a[3], max_batch_instances=a[4])
+
+    def close(self):
+        if getattr(self, "h", None):
+            destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
 
 
 def track_dense_noalloc(n, degree, gamma, settings, n_instances, coef, x_out, status_out,

@@ -78,3 +78,36 @@ def test_parameter_batch_device_pointers(hc):
                   status_out=so, steps_out=to, stream=torch.cuda.current_stream().cuda_stream).wait()
     assert np.array_equal(so.cpu().numpy(), hb.status)
     assert np.array_equal(xo.cpu().numpy(), hb.x)
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_trifocal_sampled_starts_match_oracle(hc, precision):
+    """Trifocal pose with unknown focal length, 192 sampled start roots and
+    two noisy scenes: GPU and oracle on the same subset."""
+    from paper_2112_03444_gb300 import inputs
+    fam = inputs.trifocal_family()
+    z = np.load(os.path.join(STARTS, "trifocal_f.npz"))
+    sel = np.random.default_rng(7).choice(len(z["start"]), size=192, replace=False)
+    p1s = [inputs.trifocal_scene(s)[0] for s in (51, 52)]
+    _check(hc, fam.system, z["p0"], p1s, z["start"][sel], precision)
+
+
+def test_trifocal_full_start_set_recovers_true_pose(hc):
+    """All 5344 start roots to a noise-free scene on the GPU (mixed
+    precision): the true pose is an endpoint (a property at any size)."""
+    from paper_2112_03444_gb300 import inputs
+    fam = inputs.trifocal_family()
+    z = np.load(os.path.join(STARTS, "trifocal_f.npz"))
+    _, truth = inputs.trifocal_scene(3, noise_px=0.0)
+    pr = hc.Problem(fam.system, kind=hc.HC_PARAMETER, p0=z["p0"], start=z["start"])
+    b = pr.track(n_instances=1, p1=truth["p_clean"][None, :]).wait()
+    fin = b.x[0][(b.status[0] & 0x7F) == hc.PATH_FINITE]
+    xt = truth["x_true"]
+    best = np.inf
+    for s12 in (1, -1):
+        for s13 in (1, -1):
+            v = xt.copy()
+            v[1:5] *= s12
+            v[5:9] *= s13
+            best = min(best, float(np.min(np.max(np.abs(fin - v), axis=1))))
+    assert best < 1e-8, best
