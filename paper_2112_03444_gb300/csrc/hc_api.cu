@@ -984,6 +984,8 @@ hc_status hc_track_batch(hc_problem* p, const hc_batch_desc* b, hc_batch** out) 
   cm.t_io = t_io;
   cm.x32_out = x32;
   cm.esc_steps = nullptr;
+  cm.dup_list = dup_list;
+  cm.dup_count = bt->d_ctl + 7;
   // Re-tracking tiers.  Colliding paths (dup_list, ctl[7]) run again from
   // t = 0 in the mixed kernel with the FP64 state, FP64 residuals and FP64
   // tolerances; whatever still fails there or failed in the FP32 tier
@@ -994,6 +996,8 @@ hc_status hc_track_batch(hc_problem* p, const hc_batch_desc* b, hc_batch** out) 
   cd.queue = bt->d_ctl + 6;
   cd.x32_out = nullptr;
   cd.start_hi = 1;
+  cd.dup_list = nullptr;
+  cd.dup_count = nullptr;
   hc::LaunchCommon ce = cm;
   ce.count_dev = bt->d_ctl + 2;
   ce.items = esc_list;
@@ -1001,9 +1005,13 @@ hc_status hc_track_batch(hc_problem* p, const hc_batch_desc* b, hc_batch** out) 
   ce.esc_list = nullptr;
   ce.x32_out = nullptr;
   ce.esc_steps = bt->d_ctl + 3;
+  ce.dup_list = nullptr;
+  ce.dup_count = nullptr;
   int sms = 0;
   HC_TRYCUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
-  const int64_t esc_groups = std::min<int64_t>(items, 4 * (int64_t)sms);
+  // re-tracking launches: the count is only known on the device, so the grid
+  // covers up to every item (capped at full occupancy by the launcher)
+  const int64_t esc_groups = items;
   auto dedupe = [&]() -> hc_status {
     const int grid = (int)std::min<int64_t>((items + 255) / 256, 65535);
     dedupe_kernel<<<std::max(grid, 1), 256, 0, st>>>(items, p->paths, n, x32, 1e-6f, dup_list,

@@ -181,7 +181,9 @@ enum : int {
 };
 
 // Largest FP32 condition estimate that still certifies cond_1 < 1e12 with
-// room to spare; above it a mixed-precision path is re-tracked in FP64.
-constexpr double kFp32CondTrust = 1.0e5;
+// room to spare: an FP32 inverse is accurate to about n * cond * 6e-8, so an
+// estimate of 2e6 bounds the true value within a small factor, six orders
+// below the singular threshold; above it the endpoint is re-checked in FP64.
+constexpr double kFp32CondTrust = 2.0e6;
 
 }  // namespace hc

@@ -33,6 +33,8 @@ struct LaunchCommon {
   double* t_io;                 // per item: t to resume from in FP64 (0 = restart at t = 0)
   float2* x32_out;              // per item endpoint copy for duplicate detection (NaN if not finite)
   unsigned long long* esc_steps;  // FP64 tier: accepted, rejected, Newton totals (atomic)
+  int64_t* dup_list;            // mixed kernel: failures to re-track with FP64 residuals
+  unsigned long long* dup_count;
   int start_hi;                 // mixed kernel: track every path with the FP64 state, FP64
                                 // residuals and FP64 tolerances from t = 0 (re-tracking of
                                 // colliding paths)

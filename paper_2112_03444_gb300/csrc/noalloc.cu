@@ -274,6 +274,8 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
   a.c.esc_count = ctl + 2;
   a.c.t_io = t_io;
   a.c.x32_out = x32;
+  a.c.dup_list = escalate ? dup : nullptr;
+  a.c.dup_count = ctl + 7;
   a.D32 = reinterpret_cast<const hc::cx<float>*>(D32);
   a.D64 = reinterpret_cast<const hc::cx<double>*>(D64);
   a.E = reinterpret_cast<const hc::cx<double>*>(E);
@@ -312,7 +314,9 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
     dd.c.queue = ctl + 6;
     dd.c.x32_out = nullptr;
     dd.c.start_hi = 1;
-    NA_CUDA(launch(k, dd, items < 4 * sms ? items : 4 * sms));
+    dd.c.dup_list = nullptr;
+    dd.c.dup_count = nullptr;
+    NA_CUDA(launch(k, dd, items));
     hc::DenseArgs e = a;
     e.c.count_dev = ctl + 2;
     e.c.items = esc;
@@ -320,7 +324,9 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
     e.c.esc_list = nullptr;
     e.c.x32_out = nullptr;
     e.c.esc_steps = ctl + 3;
-    NA_CUDA(launch(hc::dense_kernel(degree, n, false), e, items < 4 * sms ? items : 4 * sms));
+    e.c.dup_list = nullptr;
+    e.c.dup_count = nullptr;
+    NA_CUDA(launch(hc::dense_kernel(degree, n, false), e, items));
   }
 #undef NA_CUDA
   return HC_OK;

@@ -192,15 +192,25 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
           c.steps_out[item * 3 + 1] = nrej;
           c.steps_out[item * 3 + 2] = nnewt;
           if (c.esc_list && base != ST_FINITE) {
-            // resume point for the FP64 tier: the last accepted point after a
-            // step-size or budget failure, t = 1 (refinement and exact
-            // condition) for a suspect-condition endpoint, t = 0 otherwise
+            // Step-size and budget failures (of the FP64-residual mode) and
+            // suspect-condition endpoints go to the all-FP64 kernel, resuming
+            // from the last accepted point (t = 1: refinement and exact
+            // condition only).  Other failures of the FP32 tier (divergence,
+            // non-finite state, failed refinement) are first re-tracked from
+            // t = 0 with FP64 residuals, like colliding paths.
+            const bool to64 = base == ST_FAIL_STEP || base == ST_FAIL_MAXSTEPS ||
+                              base == ST_SINGULAR || c.start_hi || !c.dup_list;
             if (c.t_io)
               c.t_io[item] = (base == ST_FAIL_STEP || base == ST_FAIL_MAXSTEPS) ? t
                              : (base == ST_SINGULAR)                            ? 1.0
                                                                                : 0.0;
-            const unsigned long long pos = atomicAdd(c.esc_count, 1ull);
-            c.esc_list[pos] = item;
+            if (to64) {
+              const unsigned long long pos = atomicAdd(c.esc_count, 1ull);
+              c.esc_list[pos] = item;
+            } else {
+              const unsigned long long pos = atomicAdd(c.dup_count, 1ull);
+              c.dup_list[pos] = item;
+            }
           } else if (c.t_io) {
             c.t_io[item] = 0.0;
           }
