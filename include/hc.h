@@ -117,7 +117,8 @@ typedef struct hc_settings {
   int32_t refine_iters;   /* 8 */
   int32_t precision;      /* HC_PREC_MIXED */
   int32_t escalate;       /* 1: mixed-precision paths that fail are re-tracked in FP64 */
-  int32_t lanes;          /* lanes per path: 0 = automatic, else 4, 8, 16 or 32 */
+  int32_t lanes;          /* mixed precision: 0 = default group width (next power of two
+                             >= n, at least 4), 32 = one path per warp (n <= 16)   */
 } hc_settings;
 
 /*
@@ -242,6 +243,25 @@ hc_status hc_poll(hc_batch* b, int64_t timeout_us, hc_batch_result* r);
 /* Free a problem or a batch (waits for a running batch first).  NULL is a
  * no-op.  A problem must outlive its batches. */
 void hc_destroy(void* handle);
+
+/*
+ * Autotuner.  Runs the caller's representative batch (*sample, as for
+ * hc_track_batch; its outputs are overwritten) under each candidate
+ * configuration -- all-FP64; mixed precision with the default lane width or
+ * one path per warp; FP32 first-correction bound 0.01 or 0.1 -- twice each,
+ * and keeps in the problem's settings the candidate with the shortest
+ * device time among those that recover at least as many finite roots as the
+ * all-FP64 run.  *report (may be NULL) lists what was tried.
+ */
+typedef struct hc_tune_report {
+  int32_t n_candidates;
+  int32_t best;                /* index into the arrays below                    */
+  double ms[8];                /* device time of each candidate's second run     */
+  int64_t finite[8];           /* finite roots found by each candidate           */
+  hc_settings tried[8];
+} hc_tune_report;
+
+hc_status hc_autotune(hc_problem* p, const hc_batch_desc* sample, hc_tune_report* report);
 
 /*
  * Continuous-batching server (serving form of the tracker; the paper tracks

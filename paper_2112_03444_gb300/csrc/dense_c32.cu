@@ -1,9 +1,24 @@
 // Dense total-degree tracking kernels: degree 3, mixed FP32/FP64, n = 1..8.
+// lanes = 0 selects the default group width; the mixed kernels also come
+// with one path per warp (lanes = 32) for the autotuner.
 #include "dense_kernel.cuh"
 
 namespace hc {
 
-KernelRef dense_ref_d3_32(int n) {
+KernelRef dense_ref_d3_32(int n, int lanes) {
+  if (lanes == 32) {
+    switch (n) {
+      case 1: return dense_ref<3, true, 1, 32>();
+      case 2: return dense_ref<3, true, 2, 32>();
+      case 3: return dense_ref<3, true, 3, 32>();
+      case 4: return dense_ref<3, true, 4, 32>();
+      case 5: return dense_ref<3, true, 5, 32>();
+      case 6: return dense_ref<3, true, 6, 32>();
+      case 7: return dense_ref<3, true, 7, 32>();
+      case 8: return dense_ref<3, true, 8, 32>();
+      default: break;
+    }
+  }
   switch (n) {
     case 1: return dense_ref<3, true, 1>();
     case 2: return dense_ref<3, true, 2>();

@@ -24,9 +24,8 @@ struct DenseProblem {
   }
 };
 
-template <int N, int DEG, bool MIXED>
+template <int N, int DEG, bool MIXED, int L>
 __global__ void __launch_bounds__(kBlock, 4) dense_td_kernel(const DenseArgs a) {
-  constexpr int L = (N <= 4) ? 4 : (N <= 8) ? 8 : (N <= 16) ? 16 : 32;
   static_assert(group_smem_bytes(L, 0) == kGroupSmemBytesPerLane * L, "group smem layout");
   extern __shared__ __align__(16) unsigned char smem[];
   const Group g = make_group<L>();
@@ -35,9 +34,11 @@ __global__ void __launch_bounds__(kBlock, 4) dense_td_kernel(const DenseArgs a) 
   run_tracker<N, L, MIXED>(prob, a.c, g, sm);
 }
 
-template <int DEG, bool MIXED, int N>
+// lanes = 0: the default lanes_for(N); otherwise that group width.
+template <int DEG, bool MIXED, int N, int LANES = 0>
 KernelRef dense_ref() {
-  return KernelRef{reinterpret_cast<const void*>(&dense_td_kernel<N, DEG, MIXED>), lanes_for(N)};
+  constexpr int L = LANES ? LANES : ((N <= 4) ? 4 : (N <= 8) ? 8 : (N <= 16) ? 16 : 32);
+  return KernelRef{reinterpret_cast<const void*>(&dense_td_kernel<N, DEG, MIXED, L>), L};
 }
 
 }  // namespace hc

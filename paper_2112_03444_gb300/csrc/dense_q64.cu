@@ -1,9 +1,11 @@
 // Dense total-degree tracking kernels: degree 2, FP64, n = 1..12.
+// lanes = 0 selects the default group width; the mixed kernels also come
+// with one path per warp (lanes = 32) for the autotuner.
 #include "dense_kernel.cuh"
 
 namespace hc {
 
-KernelRef dense_ref_d2_64(int n) {
+KernelRef dense_ref_d2_64(int n, int lanes) {
   switch (n) {
     case 1: return dense_ref<2, false, 1>();
     case 2: return dense_ref<2, false, 2>();

@@ -40,9 +40,12 @@ struct DenseShape {
   }
 };
 
-template <int N, int DEG, int L>
+template <int N, int DEG, int L_GROUP>
 struct DenseTD {
   using S = DenseShape<N, DEG>;
+  // Lane stride of the encoded coefficients: fixed by the encoding (the
+  // default group width for N), independent of the kernel's group width.
+  static constexpr int L = (N <= 4) ? 4 : (N <= 8) ? 8 : (N <= 16) ? 16 : 32;
   const cx<float>* D32;
   const cx<double>* D64;
   const cx<double>* E;
@@ -66,7 +69,7 @@ struct DenseTD {
   template <class R>
   __device__ __forceinline__ void eval(const cx<R> (&x)[N], int i, R t, R omt, cx<R> (&row)[N + 1],
                                        cx<R>& H, cx<R>& Ht) const {
-    const cx<R>* D = dptr<R>() + i;
+    const cx<R>* D = dptr<R>() + (i < N ? i : 0);
     const cx<R>* V = vptr<R>();
     cx<R> a1[N];
 #pragma unroll
@@ -141,7 +144,7 @@ struct DenseTD {
   template <bool SCALE>
   __device__ __forceinline__ void residual64(const cx<double>* xs, int i, double t, double omt,
                                              cx<double>& H, double& sc) const {
-    const cx<double>* e = E + i;
+    const cx<double>* e = E + (i < N ? i : 0);
     int m = 0;
     cx<double> F = e[0];
     float Ssum = SCALE ? cabs2(cvt<float>(e[0])) : 0.f;
@@ -199,9 +202,9 @@ struct DenseTD {
   }
 };
 
-template <int N, int DEG, int L>
+template <int N, int DEG, int LG>
 template <class R>
-__device__ __forceinline__ const cx<R>* DenseTD<N, DEG, L>::dptr() const {
+__device__ __forceinline__ const cx<R>* DenseTD<N, DEG, LG>::dptr() const {
   if constexpr (std::is_same<R, float>::value)
     return D32;
   else

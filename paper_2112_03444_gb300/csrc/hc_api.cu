@@ -18,19 +18,21 @@
 #include "kernels.cuh"
 
 namespace hc {
-KernelRef dense_ref_d2_64(int n);
-KernelRef dense_ref_d2_32(int n);
-KernelRef dense_ref_d3_64(int n);
-KernelRef dense_ref_d3_32(int n);
+KernelRef dense_ref_d2_64(int n, int lanes);
+KernelRef dense_ref_d2_32(int n, int lanes);
+KernelRef dense_ref_d3_64(int n, int lanes);
+KernelRef dense_ref_d3_32(int n, int lanes);
 
-KernelRef term_ref_64(int n);
-KernelRef term_ref_32(int n);
+KernelRef term_ref_64(int n, int lanes);
+KernelRef term_ref_32(int n, int lanes);
 
-KernelRef term_kernel(int n, bool mixed) { return mixed ? term_ref_32(n) : term_ref_64(n); }
+KernelRef term_kernel(int n, bool mixed, int lanes) {
+  return mixed ? term_ref_32(n, lanes) : term_ref_64(n, lanes);
+}
 
-KernelRef dense_kernel(int deg, int n, bool mixed) {
-  if (deg == 2) return mixed ? dense_ref_d2_32(n) : dense_ref_d2_64(n);
-  if (deg == 3) return mixed ? dense_ref_d3_32(n) : dense_ref_d3_64(n);
+KernelRef dense_kernel(int deg, int n, bool mixed, int lanes) {
+  if (deg == 2) return mixed ? dense_ref_d2_32(n, lanes) : dense_ref_d2_64(n, lanes);
+  if (deg == 3) return mixed ? dense_ref_d3_32(n, lanes) : dense_ref_d3_64(n, lanes);
   return KernelRef{nullptr, 0};
 }
 }  // namespace hc
@@ -310,7 +312,7 @@ hc_status validate_settings(const hc_settings& s) {
       !(s.newton_tol_fp32 > 0) || !(s.max_first_corr > 0) || !(s.r_inf > 0) ||
       !(s.dt_min_fp32 >= s.dt_min) || !(s.max_first_corr_fp32 > 0) || s.max_steps_fp32 < 1 ||
       (s.precision != HC_PREC_FP64 && s.precision != HC_PREC_MIXED) ||
-      (s.lanes != 0 && s.lanes != 4 && s.lanes != 8 && s.lanes != 16 && s.lanes != 32)) {
+      (s.lanes != 0 && s.lanes != 32)) {
     set_err("invalid settings");
     return HC_ERR_INVALID;
   }
@@ -700,7 +702,7 @@ hc_status hc_create_problem(const hc_problem_desc* d, hc_problem** out) {
       set_err("parameter homotopy: n <= 32, at most 8 factors per term, L + 1 + 2 n_params <= 255");
       return HC_ERR_UNSUPPORTED;
     }
-    if (!hc::term_kernel(n, true).fn) {
+    if (!hc::term_kernel(n, true, 0).fn) {
       delete p;
       set_err("this build has parameter-homotopy kernels for n <= 24");
       return HC_ERR_UNSUPPORTED;
@@ -750,7 +752,7 @@ hc_status hc_problem_query(const hc_problem* p, hc_problem_info* out) {
   out->n = p->n;
   out->kind = p->kind;
   out->inputs_per_instance = p->kind == HC_PARAMETER ? p->P : p->T;
-  out->lanes = p->terms ? hc::term_kernel(p->n, true).lanes : p->L;
+  out->lanes = p->terms ? hc::term_kernel(p->n, true, 0).lanes : p->L;
   out->paths = p->paths;
   const int64_t P = p->paths, n = p->n;
   int64_t b = 16 * (int64_t)out->inputs_per_instance;                // inputs
@@ -1031,11 +1033,12 @@ hc_status hc_track_batch(hc_problem* p, const hc_batch_desc* b, hc_batch** out) 
       ta.kdeg[e] = p->kdeg[e];
     }
     ta.P = p->P;
+    ta.ls = p->L;
     ta.extra = p->extra;
     ta.p0 = p->d_p0;
     ta.p1 = d_p1;
     ta.start = p->d_start;
-    const hc::KernelRef k = hc::term_kernel(n, mixed);
+    const hc::KernelRef k = hc::term_kernel(n, mixed, mixed ? p->s.lanes : 0);
     const int L = k.lanes;
     const size_t smem = (size_t)(hc::kBlock / L) *
                         ((L + p->extra) * 16 + L * 16 + (L + p->extra) * 8);
@@ -1049,7 +1052,10 @@ hc_status hc_track_batch(hc_problem* p, const hc_batch_desc* b, hc_batch** out) 
       HC_TRY(launch_generic(k, &td, smem, esc_groups, st));
       hc::TermArgs te = ta;
       te.c = ce;
-      HC_TRY(launch_generic(hc::term_kernel(n, false), &te, smem, esc_groups, st));
+      const hc::KernelRef k64 = hc::term_kernel(n, false, 0);
+      const size_t smem64 = (size_t)(hc::kBlock / k64.lanes) *
+                            ((k64.lanes + p->extra) * 16 + k64.lanes * 16 + (k64.lanes + p->extra) * 8);
+      HC_TRY(launch_generic(k64, &te, smem64, esc_groups, st));
     }
     HC_TRYCUDA(cudaEventRecord(bt->evk2, st));
   } else {
@@ -1062,7 +1068,7 @@ hc_status hc_track_batch(hc_problem* p, const hc_batch_desc* b, hc_batch** out) 
     a.Dstride = p->Dstride;
     a.Estride = p->Estride;
     a.gamma = cx<double>{p->gamma[0], p->gamma[1]};
-    const hc::KernelRef k = hc::dense_kernel(p->deg, n, mixed);
+    const hc::KernelRef k = hc::dense_kernel(p->deg, n, mixed, mixed ? p->s.lanes : 0);
     if (!k.fn) {
       set_err("no kernel for this problem shape");
       return fail(HC_ERR_UNSUPPORTED);
@@ -1077,7 +1083,7 @@ hc_status hc_track_batch(hc_problem* p, const hc_batch_desc* b, hc_batch** out) 
       HC_TRY(launch_tracker(k, dd, esc_groups, st));
       hc::DenseArgs e = a;
       e.c = ce;
-      HC_TRY(launch_tracker(hc::dense_kernel(p->deg, n, false), e, esc_groups, st));
+      HC_TRY(launch_tracker(hc::dense_kernel(p->deg, n, false, 0), e, esc_groups, st));
     }
     HC_TRYCUDA(cudaEventRecord(bt->evk2, st));
   }
@@ -1146,6 +1152,69 @@ hc_status hc_poll(hc_batch* b, int64_t timeout_us, hc_batch_result* r) {
     if (cudaEventElapsedTime(&ms, b->ev0, b->ev1) == cudaSuccess) r->device_ms = ms;
     if (cudaEventElapsedTime(&ms, b->evk0, b->evk1) == cudaSuccess) r->track_ms = ms;
     if (cudaEventElapsedTime(&ms, b->evk1, b->evk2) == cudaSuccess) r->escalate_ms = ms;
+  }
+  return HC_OK;
+}
+
+hc_status hc_autotune(hc_problem* p, const hc_batch_desc* sample, hc_tune_report* report) {
+  if (!p || p->magic != kProblemMagic || !sample) {
+    set_err("invalid autotune arguments");
+    return HC_ERR_INVALID;
+  }
+  const hc_settings base = p->s;
+  std::vector<hc_settings> cand;
+  hc_settings c = base;
+  c.precision = HC_PREC_FP64;
+  cand.push_back(c);  // the recovery reference
+  for (int lanes : {0, 32}) {
+    const bool has = p->terms ? hc::term_kernel(p->n, true, lanes).lanes == (lanes ? lanes : hc::term_kernel(p->n, true, 0).lanes)
+                              : hc::dense_kernel(p->deg, p->n, true, lanes).lanes == (lanes ? lanes : p->L);
+    if (lanes && (!has || p->n > 16)) continue;
+    for (double corr : {0.01, 0.1}) {
+      c = base;
+      c.precision = HC_PREC_MIXED;
+      c.escalate = 1;
+      c.lanes = lanes;
+      c.max_first_corr_fp32 = corr;
+      cand.push_back(c);
+    }
+  }
+  if (cand.size() > 8) cand.resize(8);
+  std::vector<double> ms(cand.size(), 0.0);
+  std::vector<int64_t> fin(cand.size(), -1);
+  for (size_t i = 0; i < cand.size(); ++i) {
+    p->s = cand[i];
+    for (int rep = 0; rep < 2; ++rep) {
+      hc_batch* b = nullptr;
+      hc_status rc = hc_track_batch(p, sample, &b);
+      if (rc != HC_OK) {
+        p->s = base;
+        return rc;
+      }
+      hc_batch_result r;
+      rc = hc_poll(b, -1, &r);
+      hc_destroy(b);
+      if (rc != HC_OK) {
+        p->s = base;
+        return rc;
+      }
+      ms[i] = r.device_ms;
+      fin[i] = r.finite;
+    }
+  }
+  size_t best = 0;
+  for (size_t i = 1; i < cand.size(); ++i)
+    if (fin[i] >= fin[0] && ms[i] < ms[best]) best = i;
+  p->s = cand[best];
+  if (report) {
+    std::memset(report, 0, sizeof(*report));
+    report->n_candidates = (int32_t)cand.size();
+    report->best = (int32_t)best;
+    for (size_t i = 0; i < cand.size(); ++i) {
+      report->ms[i] = ms[i];
+      report->finite[i] = fin[i];
+      report->tried[i] = cand[i];
+    }
   }
   return HC_OK;
 }

@@ -64,6 +64,7 @@ struct TermArgs {
   const double2* s64;    // FP64 scalars, same layout
   int kcnt[kMaxTermEntries], koff[kMaxTermEntries], kdeg[kMaxTermEntries];
   int P;                 // number of parameters
+  int ls;                // lane stride of the tuple tables (and V's offset of the 1)
   int extra;             // shared-memory entries behind the point: 1 + 2P
   const double2* p0;     // [P]
   const double2* p1;     // [instances][P]
@@ -79,8 +80,9 @@ struct KernelRef {
 // of two so that a warp holds 32 / L paths).
 inline int lanes_for(int n) { return n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : 32; }
 
-KernelRef dense_kernel(int deg, int n, bool mixed);  // fn == nullptr if absent
-KernelRef term_kernel(int n, bool mixed);            // fn == nullptr if absent
+// lanes = 0: default group width; 32: one path per warp (mixed kernels, n <= 16)
+KernelRef dense_kernel(int deg, int n, bool mixed, int lanes);  // fn == nullptr if absent
+KernelRef term_kernel(int n, bool mixed, int lanes);            // fn == nullptr if absent
 
 // Defined in server.cu: frees a server if magic is the server's magic.
 bool destroy_server_if(void* handle, uint32_t magic);

@@ -300,7 +300,7 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
     void* argv[] = {(void*)&args};
     return cudaLaunchKernel(k.fn, dim3((unsigned)grid), dim3(hc::kBlock), argv, smem, st);
   };
-  const hc::KernelRef k = hc::dense_kernel(degree, n, mixed);
+  const hc::KernelRef k = hc::dense_kernel(degree, n, mixed, 0);
   if (!k.fn) {
     hc::set_last_error("hc_track_dense_noalloc: no kernel for this shape");
     return HC_ERR_UNSUPPORTED;
@@ -326,7 +326,7 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
     e.c.esc_steps = ctl + 3;
     e.c.dup_list = nullptr;
     e.c.dup_count = nullptr;
-    NA_CUDA(launch(hc::dense_kernel(degree, n, false), e, items));
+    NA_CUDA(launch(hc::dense_kernel(degree, n, false, 0), e, items));
   }
 #undef NA_CUDA
   return HC_OK;

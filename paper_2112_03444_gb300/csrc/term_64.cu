@@ -1,9 +1,11 @@
 // Parameter-homotopy (term-tuple) tracking kernels, FP64, n = 1..24.
+// lanes = 0 selects the default group width; the mixed kernels also come
+// with one path per warp (lanes = 32) for the autotuner.
 #include "term_param.cuh"
 
 namespace hc {
 
-KernelRef term_ref_64(int n) {
+KernelRef term_ref_64(int n, int lanes) {
   switch (n) {
     case 1: return term_ref<false, 1>();
     case 2: return term_ref<false, 2>();

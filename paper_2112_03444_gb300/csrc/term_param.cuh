@@ -21,6 +21,9 @@
 
 namespace hc {
 
+// The tuple tables and the V index positions (1 at LS, p(t) at LS + 1, dp at
+// LS + 1 + P) use the encoding's lane stride LS = a->ls, independent of the
+// kernel's group width L.
 template <int N, int L>
 struct TermEval {
   const TermArgs* a;
@@ -31,16 +34,16 @@ struct TermEval {
 
   // constant part of V for this path: the 1 and dp
   __device__ __forceinline__ void init(const Group&) const {
-    const int P = a->P;
+    const int P = a->P, LS = a->ls;
     const double2* p1 = a->p1 + inst * P;
     if (g.gl == 0) {
-      Vf[L] = mk<float>(1.f, 0.f);
-      Vd[L] = mk<double>(1.0, 0.0);
+      Vf[LS] = mk<float>(1.f, 0.f);
+      Vd[LS] = mk<double>(1.0, 0.0);
     }
     for (int l = g.gl; l < P; l += L) {
       const cx<double> d = mk<double>(p1[l].x - a->p0[l].x, p1[l].y - a->p0[l].y);
-      Vd[L + 1 + P + l] = d;
-      Vf[L + 1 + P + l] = cvt<float>(d);
+      Vd[LS + 1 + P + l] = d;
+      Vf[LS + 1 + P + l] = cvt<float>(d);
     }
   }
 
@@ -60,12 +63,12 @@ struct TermEval {
   // p(t) into V (each lane a share), then wait for the group
   template <class R>
   __device__ __forceinline__ void put_params(double t) const {
-    const int P = a->P;
+    const int P = a->P, LS = a->ls;
     const double2* p1 = a->p1 + inst * P;
     cx<R>* V = vptr<R>();
     for (int l = g.gl; l < P; l += L) {
       const double2 q0 = a->p0[l], q1 = p1[l];
-      V[L + 1 + l] = cvt<R>(mk<double>((1.0 - t) * q0.x + t * q1.x, (1.0 - t) * q0.y + t * q1.y));
+      V[LS + 1 + l] = cvt<R>(mk<double>((1.0 - t) * q0.x + t * q1.x, (1.0 - t) * q0.y + t * q1.y));
     }
     __syncwarp(g.mask);
   }
@@ -76,7 +79,7 @@ struct TermEval {
     cx<R> acc = czero<R>();
 #pragma unroll 1
     for (int k = 0; k < K; ++k) {
-      const int64_t r = (int64_t)(base + k) * L + i;
+      const int64_t r = (int64_t)(base + k) * a->ls + i;
       const TermRec rc = a->rec[r];
       cx<R> prod = V[rc.idx[0]];
 #pragma unroll 1
@@ -113,7 +116,7 @@ struct TermEval {
     float s_abs = 0.f;
 #pragma unroll 1
     for (int k = 0; k < K; ++k) {
-      const int64_t r = (int64_t)(base + k) * L + ii;
+      const int64_t r = (int64_t)(base + k) * a->ls + ii;
       const TermRec rc = a->rec[r];
       cx<double> prod = Vd[rc.idx[0]];
 #pragma unroll 1
@@ -137,9 +140,8 @@ struct TermProblem {
   }
 };
 
-template <int N, bool MIXED>
+template <int N, bool MIXED, int L>
 __global__ void __launch_bounds__(kBlock) term_param_kernel(const __grid_constant__ TermArgs a) {
-  constexpr int L = (N <= 4) ? 4 : (N <= 8) ? 8 : (N <= 16) ? 16 : 32;
   extern __shared__ __align__(16) unsigned char smem[];
   const Group g = make_group<L>();
   const GroupMem sm = make_group_mem<L>(smem, a.extra);
@@ -147,9 +149,10 @@ __global__ void __launch_bounds__(kBlock) term_param_kernel(const __grid_constan
   run_tracker<N, L, MIXED>(prob, a.c, g, sm);
 }
 
-template <bool MIXED, int N>
+template <bool MIXED, int N, int LANES = 0>
 KernelRef term_ref() {
-  return KernelRef{reinterpret_cast<const void*>(&term_param_kernel<N, MIXED>), lanes_for(N)};
+  constexpr int L = LANES ? LANES : ((N <= 4) ? 4 : (N <= 8) ? 8 : (N <= 16) ? 16 : 32);
+  return KernelRef{reinterpret_cast<const void*>(&term_param_kernel<N, MIXED, L>), L};
 }
 
 }  // namespace hc

@@ -125,6 +125,14 @@ class hc_request_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class hc_tune_report(ctypes.Structure):
+    _fields_ = [("n_candidates", ctypes.c_int32), ("best", ctypes.c_int32),
+                ("ms", ctypes.c_double * 8), ("finite", ctypes.c_int64 * 8),
+                ("tried", hc_settings * 8)]
+
+
+_lib.hc_autotune.restype = ctypes.c_int32
+_lib.hc_autotune.argtypes = [_P, ctypes.POINTER(hc_batch_desc), ctypes.POINTER(hc_tune_report)]
 _lib.hc_problem_query.restype = ctypes.c_int32
 _lib.hc_problem_query.argtypes = [_P, ctypes.POINTER(hc_problem_info)]
 _lib.hc_server_default_config.restype = hc_server_config
@@ -146,7 +154,8 @@ _lib.hc_track_dense_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.P
 EXPORTED = ("hc_status_string", "hc_last_error", "hc_default_settings", "hc_create_problem",
             "hc_problem_paths", "hc_problem_query", "hc_track_batch", "hc_poll", "hc_destroy",
             "hc_measure_fma_peak", "hc_track_dense_noalloc", "hc_server_default_config",
-            "hc_server_create", "hc_server_submit", "hc_server_wait", "hc_server_stats")
+            "hc_server_create", "hc_server_submit", "hc_server_wait", "hc_server_stats",
+            "hc_autotune")
 
 
 def problem_query(problem: int) -> dict:
@@ -369,6 +378,28 @@ class Problem:
         h = track_batch(self.h, b)
         return Batch(h, self, dict(x=x_out, status=status_out, steps=steps_out, be=be_out,
                                    coef=coef, p1=p1))
+
+    def autotune(self, n_instances=1, coef=None, p1=None):
+        """hc_autotune on a host sample batch; returns the report as a dict and
+        keeps the chosen settings in the problem (and in self.settings)."""
+        I, P, n = int(n_instances), self.paths, self.n
+        bufs = dict(x=np.zeros((I, P, n), np.complex128), st=np.zeros((I, P), np.uint8),
+                    steps=np.zeros((I, P, 3), np.int32))
+        coef = None if coef is None else _host(coef, np.complex128)
+        p1 = None if p1 is None else _host(p1, np.complex128)
+        b = hc_batch_desc()
+        b.n_instances = I
+        b.coef = _addr(coef)
+        b.p1 = _addr(p1)
+        b.x_out, b.status_out, b.steps_out = (_addr(bufs[k]) for k in ("x", "st", "steps"))
+        rep = hc_tune_report()
+        _check(_lib.hc_autotune(self.h, ctypes.byref(b), ctypes.byref(rep)), "hc_autotune")
+        self.settings = rep.tried[rep.best]
+        return dict(best=rep.best, ms=list(rep.ms[:rep.n_candidates]),
+                    finite=list(rep.finite[:rep.n_candidates]),
+                    tried=[dict(precision=rep.tried[i].precision, lanes=rep.tried[i].lanes,
+                                max_first_corr_fp32=rep.tried[i].max_first_corr_fp32)
+                           for i in range(rep.n_candidates)])
 
 
 class Batch:
