@@ -37,6 +37,33 @@ FP32_LANES_PER_SM = 128
 SM_COUNT = 152
 
 
+def source_sha() -> str:
+    """sha256 (16 hex) of the CUDA sources and the C-ABI header, sorted by path."""
+    import glob
+    import hashlib
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_2112_03444_gb300", "csrc", "*.cu")) +
+                   glob.glob(os.path.join(ROOT, "paper_2112_03444_gb300", "csrc", "*.cuh")) +
+                   [os.path.join(ROOT, "include", "hc.h")])
+    h = hashlib.sha256()
+    for f in sorted(files, key=lambda f: os.path.relpath(f, ROOT)):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per launch from the committed ncu capture, or None once the
+    kernel sources have changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    try:
+        kv = dict(l.split(None, 1) for l in open(path).read().splitlines()
+                  if l and not l.startswith("#"))
+    except (OSError, ValueError):
+        return None
+    if kv.get("source_sha", "").strip() != source_sha():
+        return None
+    return int(kv["dram_bytes_per_launch"])
+
+
 def env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
 
@@ -283,7 +310,7 @@ def run_gpu(args):
                  h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h, ms_per_step=e2e),
         gpu_launches=launches,
         roofline=dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s",
-                      frac=achieved / peak, traffic=None,
+                      frac=achieved / peak, traffic=recorded_traffic(),
                       kernel=f"dense_td_kernel<n={dw['n']}, d={dw['d']}, mixed>",
                       kernel_ms=statistics.mean(dk_ms),
                       peak_note="of measured: FP32 FMA throughput from hc_measure_fma_peak on this "
