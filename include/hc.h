@@ -240,9 +240,35 @@ hc_status hc_track_batch(hc_problem* p, const hc_batch_desc* b, hc_batch** out);
  */
 hc_status hc_poll(hc_batch* b, int64_t timeout_us, hc_batch_result* r);
 
-/* Free a problem or a batch (waits for a running batch first).  NULL is a
- * no-op.  A problem must outlive its batches. */
+/* Free a problem, a batch, a plan or a server (waits for running work
+ * first).  NULL is a no-op.  A problem must outlive its batches and plans. */
 void hc_destroy(void* handle);
+
+/*
+ * Plans: a batch shape replayed as one CUDA graph.  The paper (Sec. 5) runs
+ * each problem's batch as a fixed sequence of launches; a plan records that
+ * sequence once -- coefficient staging, the tracking launch, the re-tracking
+ * tiers on a high-priority branch, the summary -- with device buffers
+ * allocated for good, so each later batch of the same size costs one graph
+ * launch plus its input and output copies, and no allocation.
+ *
+ * hc_plan_create: fixes the problem's current settings, n_instances and the
+ * device (the current one).  Errors: HC_ERR_INVALID, HC_ERR_OOM, HC_ERR_CUDA,
+ * HC_ERR_UNSUPPORTED.
+ *
+ * hc_plan_run: *b as for hc_track_batch, with b->n_instances equal to the
+ * plan's (else HC_ERR_INVALID); coef NULL means the problem's own
+ * coefficients.  Host or device pointers are both accepted
+ * (HC_DEVICE_PTRS is not needed).  Returns a batch handle for hc_poll and
+ * hc_destroy at once.  Runs of one plan are ordered on the device (each
+ * starts after the previous run's last copy, on whatever stream); the
+ * batch's track_ms and escalate_ms report the plan's most recent run.
+ * The plan owns its device buffers: free it with hc_destroy after its
+ * batches are done.
+ */
+typedef struct hc_plan hc_plan;  /* opaque */
+hc_status hc_plan_create(hc_problem* p, int32_t n_instances, hc_plan** out);
+hc_status hc_plan_run(hc_plan* plan, const hc_batch_desc* b, hc_batch** out);
 
 /*
  * Autotuner.  Runs the caller's representative batch (*sample, as for

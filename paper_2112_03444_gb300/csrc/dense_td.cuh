@@ -74,7 +74,7 @@ struct DenseTD {
     cx<R> a1[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) a1[j] = czero<R>();
-#pragma unroll 1
+#pragma unroll 2
     for (int k = 0; k < N; ++k) {
       const cx<R> xk = V[k];
       const cx<R>* Dk = D + (1 + k) * L;
@@ -140,48 +140,57 @@ struct DenseTD {
   // FP64 residual of row i at (x, t); x is read from the group's shared copy
   // (xs[k], k < N) so that no FP64 vector occupies registers.  With SCALE the
   // backward-error denominator sum |c| |x^a| (FP32 accuracy is enough for a
-  // ratio test) is returned in sc.
-  template <bool SCALE>
+  // ratio test) is returned in sc.  Runtime loops: this code runs a few
+  // times per path and must not crowd the tracking loop out of the
+  // instruction cache.
+  template <bool SCALE_T>
   __device__ __forceinline__ void residual64(const cx<double>* xs, int i, double t, double omt,
                                              cx<double>& H, double& sc) const {
+    residual64_impl(xs, i, t, omt, SCALE_T, H, sc);
+  }
+
+  __device__ __noinline__ void residual64_impl(const cx<double>* xs, int i, double t, double omt,
+                                               bool scale, cx<double>& H, double& sc) const {
     const cx<double>* e = E + (i < N ? i : 0);
-    int m = 0;
     cx<double> F = e[0];
-    float Ssum = SCALE ? cabs2(cvt<float>(e[0])) : 0.f;
-    m = 1;
-#pragma unroll
+    float Ssum = scale ? cabs2(cvt<float>(e[0])) : 0.f;
+    int m = 1;
+#pragma unroll 1
     for (int j = 0; j < N; ++j) {
       cx<double> in = e[m * L];
-      float ins = SCALE ? cabs2(cvt<float>(e[m * L])) : 0.f;
+      float ins = scale ? cabs2(cvt<float>(e[m * L])) : 0.f;
       ++m;
-#pragma unroll
+#pragma unroll 1
       for (int k = 0; k <= j; ++k) {
+        const cx<double> xk = xs[k];
         if constexpr (DEG == 2) {
-          in = cfma(e[m * L], xs[k], in);
-          if (SCALE) ins += cabs2(cvt<float>(e[m * L])) * cabs2(cvt<float>(xs[k]));
+          in = cfma(e[m * L], xk, in);
+          if (scale) ins += cabs2(cvt<float>(e[m * L])) * cabs2(cvt<float>(xk));
           ++m;
         } else {
           cx<double> in2 = e[m * L];
-          float in2s = SCALE ? cabs2(cvt<float>(e[m * L])) : 0.f;
+          float in2s = scale ? cabs2(cvt<float>(e[m * L])) : 0.f;
           ++m;
-#pragma unroll
+#pragma unroll 1
           for (int l = 0; l <= k; ++l) {
-            in2 = cfma(e[m * L], xs[l], in2);
-            if (SCALE) in2s += cabs2(cvt<float>(e[m * L])) * cabs2(cvt<float>(xs[l]));
+            const cx<double> xl = xs[l];
+            in2 = cfma(e[m * L], xl, in2);
+            if (scale) in2s += cabs2(cvt<float>(e[m * L])) * cabs2(cvt<float>(xl));
             ++m;
           }
-          in = cfma(xs[k], in2, in);
-          if (SCALE) ins += cabs2(cvt<float>(xs[k])) * in2s;
+          in = cfma(xk, in2, in);
+          if (scale) ins += cabs2(cvt<float>(xk)) * in2s;
         }
       }
-      F = cfma(xs[j], in, F);
-      if (SCALE) Ssum += cabs2(cvt<float>(xs[j])) * ins;
+      const cx<double> xj = xs[j];
+      F = cfma(xj, in, F);
+      if (scale) Ssum += cabs2(cvt<float>(xj)) * ins;
     }
     const cx<double> xi = xs[i < N ? i : 0];
     const cx<double> xi2 = xi * xi;
     const cx<double> G = (DEG == 2 ? xi2 : xi2 * xi) - mk<double>(1.0, 0.0);
     H = t * F + omt * (gamma * G);
-    if (SCALE) {
+    if (scale) {
       const float axi = cabs2(cvt<float>(xi));
       sc = t * (double)Ssum + omt * (double)(1.0f + (DEG == 2 ? axi * axi : axi * axi * axi));
     } else {

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <string>
@@ -230,6 +231,8 @@ struct hc_batch {
   };
   std::vector<HostCopy> copies;
   std::vector<void*> pinned;
+  bool owns_ctl = false;            // h_ctl from the pinned pool (else a plan's)
+  bool owns_kernel_events = false;  // evk* created for this batch (else a plan's)
 };
 
 namespace {
@@ -261,6 +264,29 @@ void pinned_slot_put(void* q) {
   PinnedPool& pp = pinned_pool();
   std::lock_guard<std::mutex> lk(pp.mu);
   pp.free_slots.push_back(q);
+}
+
+// High-priority streams for the re-tracking launches (a few per device,
+// round-robin): when block slots free up they go to these small launches
+// before the pending blocks of other, normal-priority persistent launches.
+cudaStream_t retrack_stream(int device) {
+  constexpr int kPerDevice = 4, kMaxDev = 64;
+  static std::mutex mu;
+  static cudaStream_t streams[kMaxDev][kPerDevice] = {};
+  static int next[kMaxDev] = {};
+  if (device < 0 || device >= kMaxDev) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  int lo = 0, hi = 0;
+  if (!streams[device][0]) {
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    for (int i = 0; i < kPerDevice; ++i)
+      if (cudaStreamCreateWithPriority(&streams[device][i], cudaStreamNonBlocking, hi) !=
+          cudaSuccess)
+        streams[device][i] = nullptr;
+  }
+  cudaStream_t s = streams[device][next[device]];
+  next[device] = (next[device] + 1) % kPerDevice;
+  return s;
 }
 
 bool is_device_ptr(const void* p) {
@@ -763,264 +789,151 @@ hc_status hc_problem_query(const hc_problem* p, hc_problem_info* out) {
   return HC_OK;
 }
 
-hc_status hc_track_batch(hc_problem* p, const hc_batch_desc* b, hc_batch** out) {
-  g_err.clear();
-  if (!p || p->magic != kProblemMagic || !b || !out || b->n_instances < 1 || !b->x_out ||
-      !b->status_out) {
-    set_err("invalid batch descriptor");
-    return HC_ERR_INVALID;
-  }
-  if (p->kind == HC_PARAMETER && !b->p1) {
-    set_err("parameter homotopy batch needs p1");
-    return HC_ERR_INVALID;
-  }
-  int cur = 0;
-  HC_CUDA(cudaGetDevice(&cur));
-  if (cur != p->device) HC_CUDA(cudaSetDevice(p->device));
-  const bool devptrs = (b->flags & HC_DEVICE_PTRS) != 0;
-  const bool mixed = p->s.precision == HC_PREC_MIXED;
-  const bool escalate = mixed && p->s.escalate;
+}  // extern "C"
 
-  hc_batch* bt = new hc_batch;
-  bt->p = p;
-  bt->stream = (cudaStream_t)b->stream;
-  bt->n_inst = b->n_instances;
-  bt->items = bt->n_inst * p->paths;
-  const int64_t items = bt->items;
-  const int n = p->n;
-  cudaStream_t st = bt->stream;
+namespace {
 
-  auto fail = [&](hc_status s) {
-    cudaStreamSynchronize(st);
-    for (void* q : bt->dev) cudaFree(q);
-    for (void* q : bt->pinned) cudaFreeHost(q);
-    if (bt->h_ctl) pinned_slot_put(bt->h_ctl);
-    for (cudaEvent_t e : {bt->ev0, bt->ev1, bt->evk0, bt->evk1, bt->evk2})
-      if (e) cudaEventDestroy(e);
-    delete bt;
-    return s;
-  };
-  auto dalloc = [&](void** q, size_t bytes) -> hc_status {
-    cudaError_t e = cudaMallocAsync(q, std::max<size_t>(bytes, 16), st);
-    if (e != cudaSuccess) {
-      set_err(std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
-      return e == cudaErrorMemoryAllocation ? HC_ERR_OOM : HC_ERR_CUDA;
-    }
-    bt->dev.push_back(*q);
-    return HC_OK;
-  };
-#define HC_TRY(x)                        \
-  do {                                   \
-    hc_status s_ = (x);                  \
-    if (s_ != HC_OK) return fail(s_);    \
-  } while (0)
-#define HC_TRYCUDA(call)                                                     \
-  do {                                                                       \
-    cudaError_t e_ = (call);                                                 \
-    if (e_ != cudaSuccess) {                                                 \
-      set_err(std::string(#call) + ": " + cudaGetErrorString(e_));           \
-      return fail(HC_ERR_CUDA);                                              \
-    }                                                                        \
-  } while (0)
-
-  HC_TRYCUDA(cudaEventCreate(&bt->ev0));
-  HC_TRYCUDA(cudaEventCreate(&bt->ev1));
-  HC_TRYCUDA(cudaEventCreate(&bt->evk0));
-  HC_TRYCUDA(cudaEventCreate(&bt->evk1));
-  HC_TRYCUDA(cudaEventCreate(&bt->evk2));
-  HC_TRYCUDA(cudaEventRecord(bt->ev0, st));
-
+// Device buffers of one batch.
+struct Bufs {
+  const double* d_coef = nullptr;  // dense: per-instance coefficients (or the problem's)
+  int64_t coef_stride = 0;
+  const double2* d_p1 = nullptr;   // parameter families: target parameters
   void *E = nullptr, *D64 = nullptr, *D32 = nullptr;
-  const double2* d_p1 = nullptr;
-  if (p->terms) {
-    // ---- target parameters on the device
-    if (devptrs || is_device_ptr(b->p1)) {
-      d_p1 = (const double2*)b->p1;
-    } else {
-      void* q;
-      HC_TRY(dalloc(&q, sizeof(double2) * p->P * bt->n_inst));
-      HC_TRYCUDA(cudaMemcpyAsync(q, b->p1, sizeof(double2) * p->P * bt->n_inst,
-                                 cudaMemcpyHostToDevice, st));
-      d_p1 = (const double2*)q;
-    }
-  } else {
-    // ---- coefficients on the device
-    const double* d_coef = p->d_coef;
-    int64_t coef_stride = 0;
-    if (b->coef) {
-      coef_stride = (int64_t)p->T;
-      if (devptrs || is_device_ptr(b->coef)) {
-        d_coef = b->coef;
-      } else {
-        void* q;
-        HC_TRY(dalloc(&q, sizeof(double) * 2 * p->T * bt->n_inst));
-        HC_TRYCUDA(cudaMemcpyAsync(q, b->coef, sizeof(double) * 2 * p->T * bt->n_inst,
-                                   cudaMemcpyHostToDevice, st));
-        d_coef = (const double*)q;
-      }
-    }
-
-    // ---- encoded coefficients
-    const size_t eb = sizeof(cx<double>) * p->Estride * bt->n_inst;
-    const size_t db64 = sizeof(cx<double>) * p->Dstride * bt->n_inst;
-    const size_t db32 = sizeof(cx<float>) * p->Dstride * bt->n_inst;
-    HC_TRY(dalloc(&E, eb));
-    HC_TRYCUDA(cudaMemsetAsync(E, 0, eb, st));
-    if (!mixed || escalate) {
-      HC_TRY(dalloc(&D64, db64));
-      HC_TRYCUDA(cudaMemsetAsync(D64, 0, db64, st));
-    }
-    if (mixed) {
-      HC_TRY(dalloc(&D32, db32));
-      HC_TRYCUDA(cudaMemsetAsync(D32, 0, db32, st));
-    }
-    {
-      const int64_t work = bt->n_inst * (p->T + p->ndc);
-      const int grid = (int)std::min<int64_t>((work + 255) / 256, 4096);
-      stage_dense_kernel<<<grid, 256, 0, st>>>(bt->n_inst, p->T, (const double2*)d_coef, coef_stride,
-                                              p->d_emap, p->ndc, p->d_dterm, p->d_dslot,
-                                              p->d_dmult, (double2*)E, p->Estride, (float2*)D32,
-                                              (double2*)D64, p->Dstride);
-      HC_TRYCUDA(cudaGetLastError());
-    }
-
-  }
-
-  // ---- outputs (device side)
-  double* d_x = b->x_out;
-  uint8_t* d_status = b->status_out;
-  int32_t* d_steps = b->steps_out;
-  double* d_be = b->be_out;
-  auto out_buffer = [&](void* user, size_t bytes, void** dptr) -> hc_status {
-    void* q;
-    hc_status s = dalloc(&q, bytes);
-    if (s != HC_OK) return s;
-    *dptr = q;
-    if (user) {
-      if (is_pinned_host(user)) {
-        bt->copies.push_back({user, nullptr, bytes});
-      } else {
-        void* pin;
-        if (cudaMallocHost(&pin, bytes) != cudaSuccess) {
-          set_err("cudaMallocHost failed");
-          return HC_ERR_OOM;
-        }
-        bt->pinned.push_back(pin);
-        bt->copies.push_back({user, pin, bytes});
-      }
-    }
-    return HC_OK;
-  };
-  std::vector<std::pair<void*, size_t>> d2h;  // device source per copy
-  if (!devptrs) {
-    void* q;
-    HC_TRY(out_buffer(b->x_out, sizeof(double) * 2 * n * items, &q));
-    d_x = (double*)q;
-    d2h.push_back({q, 0});
-    HC_TRY(out_buffer(b->status_out, items, &q));
-    d_status = (uint8_t*)q;
-    d2h.push_back({q, 0});
-    HC_TRY(out_buffer(b->steps_out, sizeof(int32_t) * 3 * items, &q));
-    d_steps = (int32_t*)q;
-    if (b->steps_out) d2h.push_back({q, 0});
-    if (b->be_out) {
-      HC_TRY(out_buffer(b->be_out, sizeof(double) * items, &q));
-      d_be = (double*)q;
-      d2h.push_back({q, 0});
-    } else {
-      d_be = nullptr;
-    }
-  } else if (!d_steps) {
-    void* q;
-    HC_TRY(dalloc(&q, sizeof(int32_t) * 3 * items));
-    d_steps = (int32_t*)q;
-  }
-
-  // ---- control words: [0] queue [1] escalation queue [2] escalation count
-  //      [8..15] summary
-  {
-    void* q;
-    HC_TRY(dalloc(&q, sizeof(unsigned long long) * 16));
-    bt->d_ctl = (unsigned long long*)q;
-    HC_TRYCUDA(cudaMemsetAsync(q, 0, sizeof(unsigned long long) * 16, st));
-    void* pin = pinned_slot_get();
-    if (!pin) {
-      set_err("cudaMallocHost failed");
-      return fail(HC_ERR_OOM);
-    }
-    bt->h_ctl = (unsigned long long*)pin;
-    std::memset(pin, 0, sizeof(unsigned long long) * 16);
-  }
+  double* d_x = nullptr;
+  uint8_t* d_status = nullptr;
+  int32_t* d_steps = nullptr;
+  double* d_be = nullptr;
+  unsigned long long* d_ctl = nullptr;  // [0] queue [1] FP64 queue [2] FP64 list count
+                                        // [3..5] FP64 steps [6] re-track queue
+                                        // [7] re-track list count [8..15] summary
+  unsigned long long* h_ctl = nullptr;  // pinned copy of d_ctl
   int64_t* esc_list = nullptr;
   int64_t* dup_list = nullptr;
   double* t_io = nullptr;
   float2* x32 = nullptr;
-  if (escalate) {
-    void* q;
-    HC_TRY(dalloc(&q, sizeof(int64_t) * items));
-    esc_list = (int64_t*)q;
-    HC_TRY(dalloc(&q, sizeof(int64_t) * items));
-    dup_list = (int64_t*)q;
-    HC_TRY(dalloc(&q, sizeof(double) * items));
-    t_io = (double*)q;
-    HC_TRY(dalloc(&q, sizeof(float2) * n * items));
-    x32 = (float2*)q;
-  }
-  HC_TRYCUDA(cudaMemsetAsync(d_steps, 0, sizeof(int32_t) * 3 * items, st));
+};
 
-  // ---- tracking launch
+// Scratch of a batch (encoded coefficients, control words, re-tracking lists);
+// alloc(bytes, &ptr) returns an hc_status.
+template <class A>
+hc_status alloc_scratch(hc_problem* p, int64_t n_inst, Bufs& B, A&& alloc) {
+  const bool mixed = p->s.precision == HC_PREC_MIXED;
+  const bool escalate = mixed && p->s.escalate;
+  const int64_t items = n_inst * p->paths;
+  void* q;
+  hc_status rc;
+  if (!p->terms) {
+    if ((rc = alloc(sizeof(cx<double>) * p->Estride * n_inst, &B.E)) != HC_OK) return rc;
+    if (!mixed || escalate)
+      if ((rc = alloc(sizeof(cx<double>) * p->Dstride * n_inst, &B.D64)) != HC_OK) return rc;
+    if (mixed)
+      if ((rc = alloc(sizeof(cx<float>) * p->Dstride * n_inst, &B.D32)) != HC_OK) return rc;
+  }
+  if ((rc = alloc(sizeof(unsigned long long) * 16, &q)) != HC_OK) return rc;
+  B.d_ctl = (unsigned long long*)q;
+  if (escalate) {
+    if ((rc = alloc(sizeof(int64_t) * items, &q)) != HC_OK) return rc;
+    B.esc_list = (int64_t*)q;
+    if ((rc = alloc(sizeof(int64_t) * items, &q)) != HC_OK) return rc;
+    B.dup_list = (int64_t*)q;
+    if ((rc = alloc(sizeof(double) * items, &q)) != HC_OK) return rc;
+    B.t_io = (double*)q;
+    if ((rc = alloc(sizeof(float2) * p->n * items, &q)) != HC_OK) return rc;
+    B.x32 = (float2*)q;
+  }
+  return HC_OK;
+}
+
+// Events of one enqueue: ek0..ek2 time the tracking launch and the
+// re-tracking tiers; fork and join order the re-tracking stream after the
+// tracking launch and the summary after the re-tracking.  Under stream
+// capture the timing events become event-record nodes of the graph
+// (external), the fork/join events only graph edges.
+struct EnqEvents {
+  cudaEvent_t ek0, ek1, ek2, fork, join;
+  bool capture;
+};
+
+// Enqueues one batch on st: clearing, staging, the tracking launch, the
+// re-tracking tiers (on the stream hs, event-ordered), the summary and the
+// copy of the control words to B.h_ctl.  Allocates nothing and never waits
+// on the host, so it can be captured into a CUDA graph.
+hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStream_t st,
+                          cudaStream_t hs, const EnqEvents& ev) {
+  auto mark = [&](cudaEvent_t e, cudaStream_t s) {
+    return ev.capture ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal)
+                      : cudaEventRecord(e, s);
+  };
+  const bool mixed = p->s.precision == HC_PREC_MIXED;
+  const bool escalate = mixed && p->s.escalate;
+  const int64_t items = n_inst * p->paths;
+  const int n = p->n;
+  if (!p->terms) {
+    HC_CUDA(cudaMemsetAsync(B.E, 0, sizeof(cx<double>) * p->Estride * n_inst, st));
+    if (B.D64) HC_CUDA(cudaMemsetAsync(B.D64, 0, sizeof(cx<double>) * p->Dstride * n_inst, st));
+    if (B.D32) HC_CUDA(cudaMemsetAsync(B.D32, 0, sizeof(cx<float>) * p->Dstride * n_inst, st));
+    const int64_t work = n_inst * (p->T + p->ndc);
+    const int grid = (int)std::min<int64_t>((work + 255) / 256, 4096);
+    stage_dense_kernel<<<grid, 256, 0, st>>>(n_inst, p->T, (const double2*)B.d_coef, B.coef_stride,
+                                            p->d_emap, p->ndc, p->d_dterm, p->d_dslot,
+                                            p->d_dmult, (double2*)B.E, p->Estride, (float2*)B.D32,
+                                            (double2*)B.D64, p->Dstride);
+    HC_CUDA(cudaGetLastError());
+  }
+  HC_CUDA(cudaMemsetAsync(B.d_ctl, 0, sizeof(unsigned long long) * 16, st));
+  HC_CUDA(cudaMemsetAsync(B.d_steps, 0, sizeof(int32_t) * 3 * items, st));
+
   hc::LaunchCommon cm;
   std::memset(&cm, 0, sizeof(cm));
   cm.s = dev_settings(p->s);
   cm.n_items = items;
-  cm.count_dev = nullptr;
-  cm.items = nullptr;
-  cm.queue = bt->d_ctl + 0;
+  cm.queue = B.d_ctl + 0;
   cm.paths = p->paths;
-  cm.x_out = d_x;
-  cm.status_out = d_status;
-  cm.steps_out = d_steps;
-  cm.be_out = d_be;
-  cm.esc_list = esc_list;
-  cm.esc_count = bt->d_ctl + 2;
-  cm.t_io = t_io;
-  cm.x32_out = x32;
-  cm.esc_steps = nullptr;
-  cm.dup_list = dup_list;
-  cm.dup_count = bt->d_ctl + 7;
-  // Re-tracking tiers.  Colliding paths (dup_list, ctl[7]) run again from
-  // t = 0 in the mixed kernel with the FP64 state, FP64 residuals and FP64
-  // tolerances; whatever still fails there or failed in the FP32 tier
-  // (esc_list, ctl[2]) runs in the all-FP64 kernel.
+  cm.x_out = B.d_x;
+  cm.status_out = B.d_status;
+  cm.steps_out = B.d_steps;
+  cm.be_out = B.d_be;
+  cm.esc_list = B.esc_list;
+  cm.esc_count = B.d_ctl + 2;
+  cm.t_io = B.t_io;
+  cm.x32_out = B.x32;
+  cm.dup_list = B.dup_list;
+  cm.dup_count = B.d_ctl + 7;
+  // Re-tracking tiers.  Colliding paths and FP32-tier failures other than
+  // step-size ones (dup_list, ctl[7]) run again from t = 0 in the mixed
+  // kernel with the FP64 state, FP64 residuals and FP64 tolerances; whatever
+  // still fails there, step-size failures and suspect-condition endpoints
+  // (esc_list, ctl[2]) run in the all-FP64 kernel.
   hc::LaunchCommon cd = cm;
-  cd.count_dev = bt->d_ctl + 7;
-  cd.items = dup_list;
-  cd.queue = bt->d_ctl + 6;
+  cd.count_dev = B.d_ctl + 7;
+  cd.items = B.dup_list;
+  cd.queue = B.d_ctl + 6;
   cd.x32_out = nullptr;
   cd.start_hi = 1;
   cd.dup_list = nullptr;
   cd.dup_count = nullptr;
   hc::LaunchCommon ce = cm;
-  ce.count_dev = bt->d_ctl + 2;
-  ce.items = esc_list;
-  ce.queue = bt->d_ctl + 1;
+  ce.count_dev = B.d_ctl + 2;
+  ce.items = B.esc_list;
+  ce.queue = B.d_ctl + 1;
   ce.esc_list = nullptr;
   ce.x32_out = nullptr;
-  ce.esc_steps = bt->d_ctl + 3;
+  ce.esc_steps = B.d_ctl + 3;
   ce.dup_list = nullptr;
   ce.dup_count = nullptr;
-  int sms = 0;
-  HC_TRYCUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
-  // re-tracking launches: the count is only known on the device, so the grid
+  // the count of re-tracked items is only known on the device: the grid
   // covers up to every item (capped at full occupancy by the launcher)
   const int64_t esc_groups = items;
+  if (!hs) hs = st;
   auto dedupe = [&]() -> hc_status {
+    HC_CUDA(cudaStreamWaitEvent(hs, ev.capture ? ev.fork : ev.ek1, 0));
     const int grid = (int)std::min<int64_t>((items + 255) / 256, 65535);
-    dedupe_kernel<<<std::max(grid, 1), 256, 0, st>>>(items, p->paths, n, x32, 1e-6f, dup_list,
-                                                    bt->d_ctl + 7, t_io);
+    dedupe_kernel<<<std::max(grid, 1), 256, 0, hs>>>(items, p->paths, n, B.x32, 1e-6f,
+                                                    B.dup_list, B.d_ctl + 7, B.t_io);
     HC_CUDA(cudaGetLastError());
     return HC_OK;
   };
+  hc_status rc;
   if (p->terms) {
     hc::TermArgs ta;
     std::memset(&ta, 0, sizeof(ta));
@@ -1036,67 +949,251 @@ hc_status hc_track_batch(hc_problem* p, const hc_batch_desc* b, hc_batch** out) 
     ta.ls = p->L;
     ta.extra = p->extra;
     ta.p0 = p->d_p0;
-    ta.p1 = d_p1;
+    ta.p1 = B.d_p1;
     ta.start = p->d_start;
     const hc::KernelRef k = hc::term_kernel(n, mixed, mixed ? p->s.lanes : 0);
-    const int L = k.lanes;
-    const size_t smem = (size_t)(hc::kBlock / L) *
-                        ((L + p->extra) * 16 + L * 16 + (L + p->extra) * 8);
-    HC_TRYCUDA(cudaEventRecord(bt->evk0, st));
-    HC_TRY(launch_generic(k, &ta, smem, items, st));
-    HC_TRYCUDA(cudaEventRecord(bt->evk1, st));
+    auto smem_of = [&](int L) {
+      return (size_t)(hc::kBlock / L) * ((L + p->extra) * 16 + L * 16 + (L + p->extra) * 8);
+    };
+    HC_CUDA(mark(ev.ek0, st));
+    if ((rc = launch_generic(k, &ta, smem_of(k.lanes), items, st)) != HC_OK) return rc;
+    HC_CUDA(mark(ev.ek1, st));
     if (escalate) {
-      HC_TRY(dedupe());
+      if (ev.capture) HC_CUDA(cudaEventRecord(ev.fork, st));
+      if ((rc = dedupe()) != HC_OK) return rc;
       hc::TermArgs td = ta;
       td.c = cd;
-      HC_TRY(launch_generic(k, &td, smem, esc_groups, st));
+      if ((rc = launch_generic(k, &td, smem_of(k.lanes), esc_groups, hs)) != HC_OK) return rc;
       hc::TermArgs te = ta;
       te.c = ce;
       const hc::KernelRef k64 = hc::term_kernel(n, false, 0);
-      const size_t smem64 = (size_t)(hc::kBlock / k64.lanes) *
-                            ((k64.lanes + p->extra) * 16 + k64.lanes * 16 + (k64.lanes + p->extra) * 8);
-      HC_TRY(launch_generic(k64, &te, smem64, esc_groups, st));
+      if ((rc = launch_generic(k64, &te, smem_of(k64.lanes), esc_groups, hs)) != HC_OK) return rc;
+      HC_CUDA(mark(ev.ek2, hs));
+      if (ev.capture) HC_CUDA(cudaEventRecord(ev.join, hs));
+      HC_CUDA(cudaStreamWaitEvent(st, ev.capture ? ev.join : ev.ek2, 0));
+    } else {
+      HC_CUDA(mark(ev.ek2, st));
     }
-    HC_TRYCUDA(cudaEventRecord(bt->evk2, st));
   } else {
     hc::DenseArgs a;
     std::memset(&a, 0, sizeof(a));
     a.c = cm;
-    a.D32 = (const cx<float>*)D32;
-    a.D64 = (const cx<double>*)D64;
-    a.E = (const cx<double>*)E;
+    a.D32 = (const cx<float>*)B.D32;
+    a.D64 = (const cx<double>*)B.D64;
+    a.E = (const cx<double>*)B.E;
     a.Dstride = p->Dstride;
     a.Estride = p->Estride;
     a.gamma = cx<double>{p->gamma[0], p->gamma[1]};
     const hc::KernelRef k = hc::dense_kernel(p->deg, n, mixed, mixed ? p->s.lanes : 0);
     if (!k.fn) {
       set_err("no kernel for this problem shape");
-      return fail(HC_ERR_UNSUPPORTED);
+      return HC_ERR_UNSUPPORTED;
     }
-    HC_TRYCUDA(cudaEventRecord(bt->evk0, st));
-    HC_TRY(launch_tracker(k, a, items, st));
-    HC_TRYCUDA(cudaEventRecord(bt->evk1, st));
+    HC_CUDA(mark(ev.ek0, st));
+    if ((rc = launch_tracker(k, a, items, st)) != HC_OK) return rc;
+    HC_CUDA(mark(ev.ek1, st));
     if (escalate) {
-      HC_TRY(dedupe());
+      if (ev.capture) HC_CUDA(cudaEventRecord(ev.fork, st));
+      if ((rc = dedupe()) != HC_OK) return rc;
       hc::DenseArgs dd = a;
       dd.c = cd;
-      HC_TRY(launch_tracker(k, dd, esc_groups, st));
+      if ((rc = launch_tracker(k, dd, esc_groups, hs)) != HC_OK) return rc;
       hc::DenseArgs e = a;
       e.c = ce;
-      HC_TRY(launch_tracker(hc::dense_kernel(p->deg, n, false, 0), e, esc_groups, st));
+      if ((rc = launch_tracker(hc::dense_kernel(p->deg, n, false, 0), e, esc_groups, hs)) != HC_OK)
+        return rc;
+      HC_CUDA(mark(ev.ek2, hs));
+      if (ev.capture) HC_CUDA(cudaEventRecord(ev.join, hs));
+      HC_CUDA(cudaStreamWaitEvent(st, ev.capture ? ev.join : ev.ek2, 0));
+    } else {
+      HC_CUDA(mark(ev.ek2, st));
     }
-    HC_TRYCUDA(cudaEventRecord(bt->evk2, st));
   }
-  {
-    const int grid = (int)std::min<int64_t>((items + 255) / 256, 1024);
-    summarize_kernel<<<std::max(grid, 1), 256, 0, st>>>(items, d_status, d_steps, bt->d_ctl + 8);
-    HC_TRYCUDA(cudaGetLastError());
+  const int grid = (int)std::min<int64_t>((items + 255) / 256, 1024);
+  summarize_kernel<<<std::max(grid, 1), 256, 0, st>>>(items, B.d_status, B.d_steps, B.d_ctl + 8);
+  HC_CUDA(cudaGetLastError());
+  if (B.h_ctl)
+    HC_CUDA(cudaMemcpyAsync(B.h_ctl, B.d_ctl, sizeof(unsigned long long) * 16,
+                            cudaMemcpyDeviceToHost, st));
+  return HC_OK;
+}
+
+hc_status validate_batch(hc_problem* p, const hc_batch_desc* b) {
+  if (!p || p->magic != kProblemMagic || !b || b->n_instances < 1 || !b->x_out ||
+      !b->status_out) {
+    set_err("invalid batch descriptor");
+    return HC_ERR_INVALID;
   }
-  HC_TRYCUDA(cudaMemcpyAsync(bt->h_ctl, bt->d_ctl, sizeof(unsigned long long) * 16,
-                             cudaMemcpyDeviceToHost, st));
+  if (p->kind == HC_PARAMETER && !b->p1) {
+    set_err("parameter homotopy batch needs p1");
+    return HC_ERR_INVALID;
+  }
+  return HC_OK;
+}
+
+void release_batch(hc_batch* bt) {
+  for (void* q : bt->dev) cudaFree(q);
+  for (void* q : bt->pinned) cudaFreeHost(q);
+  if (bt->h_ctl && bt->owns_ctl) pinned_slot_put(bt->h_ctl);
+  for (cudaEvent_t e : {bt->ev0, bt->ev1})
+    if (e) cudaEventDestroy(e);
+  if (bt->owns_kernel_events)
+    for (cudaEvent_t e : {bt->evk0, bt->evk1, bt->evk2})
+      if (e) cudaEventDestroy(e);
+  bt->magic = 0;
+  delete bt;
+}
+
+// Output side of a batch: device destinations for the kernels (the user's
+// device buffers, or fresh ones copied back to the user's host buffers).
+hc_status setup_outputs(hc_batch* bt, const hc_batch_desc* b, int n, int64_t items, bool devptrs,
+                        Bufs& B, std::vector<void*>& d2h,
+                        const std::function<hc_status(size_t, void**)>& dalloc) {
+  B.d_x = b->x_out;
+  B.d_status = b->status_out;
+  B.d_steps = b->steps_out;
+  B.d_be = b->be_out;
+  auto out_buffer = [&](void* user, size_t bytes, void** dptr) -> hc_status {
+    hc_status s = dalloc(bytes, dptr);
+    if (s != HC_OK) return s;
+    if (user) {
+      if (is_pinned_host(user)) {
+        bt->copies.push_back({user, nullptr, bytes});
+      } else {
+        void* pin;
+        if (cudaMallocHost(&pin, bytes) != cudaSuccess) {
+          set_err("cudaMallocHost failed");
+          return HC_ERR_OOM;
+        }
+        bt->pinned.push_back(pin);
+        bt->copies.push_back({user, pin, bytes});
+      }
+      d2h.push_back(*dptr);
+    }
+    return HC_OK;
+  };
+  hc_status rc;
+  void* q;
+  if (!devptrs) {
+    if ((rc = out_buffer(b->x_out, sizeof(double) * 2 * n * items, &q)) != HC_OK) return rc;
+    B.d_x = (double*)q;
+    if ((rc = out_buffer(b->status_out, items, &q)) != HC_OK) return rc;
+    B.d_status = (uint8_t*)q;
+    if ((rc = out_buffer(b->steps_out, sizeof(int32_t) * 3 * items, &q)) != HC_OK) return rc;
+    B.d_steps = (int32_t*)q;
+    B.d_be = nullptr;
+    if (b->be_out) {
+      if ((rc = out_buffer(b->be_out, sizeof(double) * items, &q)) != HC_OK) return rc;
+      B.d_be = (double*)q;
+    }
+  } else if (!B.d_steps) {
+    if ((rc = dalloc(sizeof(int32_t) * 3 * items, &q)) != HC_OK) return rc;
+    B.d_steps = (int32_t*)q;
+  }
+  return HC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hc_status hc_track_batch(hc_problem* p, const hc_batch_desc* b, hc_batch** out) {
+  g_err.clear();
+  cudaGetLastError();  // launch errors checked below are this call's own
+  hc_status rc = validate_batch(p, b);
+  if (rc != HC_OK || !out) return rc != HC_OK ? rc : HC_ERR_INVALID;
+  int cur = 0;
+  HC_CUDA(cudaGetDevice(&cur));
+  if (cur != p->device) HC_CUDA(cudaSetDevice(p->device));
+  const bool devptrs = (b->flags & HC_DEVICE_PTRS) != 0;
+
+  hc_batch* bt = new hc_batch;
+  bt->p = p;
+  bt->stream = (cudaStream_t)b->stream;
+  bt->n_inst = b->n_instances;
+  bt->items = bt->n_inst * p->paths;
+  const int64_t items = bt->items;
+  cudaStream_t st = bt->stream;
+  auto fail = [&](hc_status s) {
+    cudaStreamSynchronize(st);
+    release_batch(bt);
+    if (cur != p->device) cudaSetDevice(cur);
+    return s;
+  };
+  std::function<hc_status(size_t, void**)> dalloc = [&](size_t bytes, void** q) -> hc_status {
+    cudaError_t e = cudaMallocAsync(q, std::max<size_t>(bytes, 16), st);
+    if (e != cudaSuccess) {
+      set_err(std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+      return e == cudaErrorMemoryAllocation ? HC_ERR_OOM : HC_ERR_CUDA;
+    }
+    bt->dev.push_back(*q);
+    return HC_OK;
+  };
+#define HC_TRY(x)                     \
+  do {                                \
+    hc_status s_ = (x);               \
+    if (s_ != HC_OK) return fail(s_); \
+  } while (0)
+#define HC_TRYCUDA(call)                                           \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) {                                       \
+      set_err(std::string(#call) + ": " + cudaGetErrorString(e_)); \
+      return fail(HC_ERR_CUDA);                                    \
+    }                                                              \
+  } while (0)
+  for (cudaEvent_t* e : {&bt->ev0, &bt->ev1, &bt->evk0, &bt->evk1, &bt->evk2})
+    HC_TRYCUDA(cudaEventCreate(e));
+  bt->owns_kernel_events = true;
+  HC_TRYCUDA(cudaEventRecord(bt->ev0, st));
+
+  Bufs B;
+  // ---- inputs on the device
+  if (p->terms) {
+    if (devptrs || is_device_ptr(b->p1)) {
+      B.d_p1 = (const double2*)b->p1;
+    } else {
+      void* q;
+      HC_TRY(dalloc(sizeof(double2) * p->P * bt->n_inst, &q));
+      HC_TRYCUDA(cudaMemcpyAsync(q, b->p1, sizeof(double2) * p->P * bt->n_inst,
+                                 cudaMemcpyHostToDevice, st));
+      B.d_p1 = (const double2*)q;
+    }
+  } else {
+    B.d_coef = p->d_coef;
+    if (b->coef) {
+      B.coef_stride = (int64_t)p->T;
+      if (devptrs || is_device_ptr(b->coef)) {
+        B.d_coef = b->coef;
+      } else {
+        void* q;
+        HC_TRY(dalloc(sizeof(double) * 2 * p->T * bt->n_inst, &q));
+        HC_TRYCUDA(cudaMemcpyAsync(q, b->coef, sizeof(double) * 2 * p->T * bt->n_inst,
+                                   cudaMemcpyHostToDevice, st));
+        B.d_coef = (const double*)q;
+      }
+    }
+  }
+  // ---- outputs and scratch
+  std::vector<void*> d2h;
+  HC_TRY(setup_outputs(bt, b, p->n, items, devptrs, B, d2h, dalloc));
+  HC_TRY(alloc_scratch(p, bt->n_inst, B, [&](size_t bytes, void** q) { return dalloc(bytes, q); }));
+  void* pin = pinned_slot_get();
+  if (!pin) {
+    set_err("cudaMallocHost failed");
+    return fail(HC_ERR_OOM);
+  }
+  bt->h_ctl = (unsigned long long*)pin;
+  bt->owns_ctl = true;
+  std::memset(pin, 0, sizeof(unsigned long long) * 16);
+  B.h_ctl = bt->h_ctl;
+  bt->d_ctl = B.d_ctl;
+  // ---- the computation
+  const EnqEvents ev{bt->evk0, bt->evk1, bt->evk2, nullptr, nullptr, false};
+  HC_TRY(enqueue_compute(p, bt->n_inst, B, st, retrack_stream(p->device), ev));
   for (size_t i = 0; i < bt->copies.size(); ++i) {
     void* dst = bt->copies[i].pinned ? bt->copies[i].pinned : bt->copies[i].dst;
-    HC_TRYCUDA(cudaMemcpyAsync(dst, d2h[i].first, bt->copies[i].bytes, cudaMemcpyDeviceToHost, st));
+    HC_TRYCUDA(cudaMemcpyAsync(dst, d2h[i], bt->copies[i].bytes, cudaMemcpyDeviceToHost, st));
   }
   HC_TRYCUDA(cudaEventRecord(bt->ev1, st));
   if (cur != p->device) cudaSetDevice(cur);
@@ -1104,6 +1201,237 @@ hc_status hc_track_batch(hc_problem* p, const hc_batch_desc* b, hc_batch** out) 
   return HC_OK;
 #undef HC_TRY
 #undef HC_TRYCUDA
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ plans (CUDA graphs)
+struct hc_plan {
+  uint32_t magic = 0x48435050u;  // "HCPP"
+  hc_problem* p = nullptr;
+  int64_t n_inst = 0, items = 0;
+  Bufs B;
+  void* d_in = nullptr;  // inputs of the instances (coef or p1)
+  size_t in_bytes = 0;
+  std::vector<void*> dev;
+  cudaEvent_t ek0 = nullptr, ek1 = nullptr, ek2 = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;  // graph edges of the re-tracking branch
+  cudaEvent_t done = nullptr;  // recorded after each run's last copy
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+void free_plan(hc_plan* pl) {
+  if (pl->exec) cudaGraphExecDestroy(pl->exec);
+  if (pl->graph) cudaGraphDestroy(pl->graph);
+  if (pl->done) cudaEventSynchronize(pl->done);
+  for (void* q : pl->dev) cudaFree(q);
+  for (cudaEvent_t e : {pl->ek0, pl->ek1, pl->ek2, pl->fork, pl->join, pl->done})
+    if (e) cudaEventDestroy(e);
+  pl->magic = 0;
+  delete pl;
+}
+}  // namespace
+
+namespace hc {
+bool destroy_plan_if(void* handle, uint32_t magic) {
+  if (magic != 0x48435050u) return false;
+  free_plan(static_cast<hc_plan*>(handle));
+  return true;
+}
+}  // namespace hc
+
+extern "C" {
+
+hc_status hc_plan_create(hc_problem* p, int32_t n_instances, hc_plan** out) {
+  g_err.clear();
+  cudaGetLastError();  // launch errors checked below are this call's own
+  if (!p || p->magic != kProblemMagic || n_instances < 1 || !out) {
+    set_err("invalid plan arguments");
+    return HC_ERR_INVALID;
+  }
+  int cur = 0;
+  HC_CUDA(cudaGetDevice(&cur));
+  if (cur != p->device) HC_CUDA(cudaSetDevice(p->device));
+  hc_plan* pl = new hc_plan;
+  pl->p = p;
+  pl->n_inst = n_instances;
+  pl->items = pl->n_inst * p->paths;
+  auto fail = [&](hc_status s) {
+    free_plan(pl);
+    if (cur != p->device) cudaSetDevice(cur);
+    return s;
+  };
+  auto dalloc = [&](size_t bytes, void** q) -> hc_status {
+    cudaError_t e = cudaMalloc(q, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess) {
+      set_err(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+      return e == cudaErrorMemoryAllocation ? HC_ERR_OOM : HC_ERR_CUDA;
+    }
+    pl->dev.push_back(*q);
+    return HC_OK;
+  };
+  hc_status rc;
+  const int64_t items = pl->items;
+  const int n = p->n;
+  pl->in_bytes = sizeof(double2) * (p->terms ? p->P : p->T) * pl->n_inst;
+  if ((rc = dalloc(pl->in_bytes, &pl->d_in)) != HC_OK) return fail(rc);
+  if (p->terms) {
+    pl->B.d_p1 = (const double2*)pl->d_in;
+  } else {
+    pl->B.d_coef = (const double*)pl->d_in;
+    pl->B.coef_stride = p->T;
+  }
+  void* q;
+  if ((rc = dalloc(sizeof(double) * 2 * n * items, &q)) != HC_OK) return fail(rc);
+  pl->B.d_x = (double*)q;
+  if ((rc = dalloc(items, &q)) != HC_OK) return fail(rc);
+  pl->B.d_status = (uint8_t*)q;
+  if ((rc = dalloc(sizeof(int32_t) * 3 * items, &q)) != HC_OK) return fail(rc);
+  pl->B.d_steps = (int32_t*)q;
+  if ((rc = dalloc(sizeof(double) * items, &q)) != HC_OK) return fail(rc);
+  pl->B.d_be = (double*)q;
+  if ((rc = alloc_scratch(p, pl->n_inst, pl->B, dalloc)) != HC_OK) return fail(rc);
+  for (cudaEvent_t* e : {&pl->ek0, &pl->ek1, &pl->ek2, &pl->fork, &pl->join, &pl->done})
+    if (cudaEventCreate(e) != cudaSuccess) {
+      set_err("cudaEventCreate failed");
+      return fail(HC_ERR_CUDA);
+    }
+  // Capture on private streams (a shared stream could pick up another
+  // thread's work while it is being captured); the re-tracking branch keeps
+  // the high priority it has outside graphs.
+  cudaStream_t cap = nullptr, cap_hi = nullptr;
+  int lo = 0, hi = 0;
+  cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&cap_hi, cudaStreamNonBlocking, hi) != cudaSuccess) {
+    if (cap) cudaStreamDestroy(cap);
+    set_err("cudaStreamCreate failed");
+    return fail(HC_ERR_CUDA);
+  }
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    const EnqEvents ev{pl->ek0, pl->ek1, pl->ek2, pl->fork, pl->join, true};
+    rc = enqueue_compute(p, pl->n_inst, pl->B, cap, cap_hi, ev);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cap, &g);
+    pl->graph = g;
+    if (rc == HC_OK && e == cudaSuccess)
+      e = cudaGraphInstantiateWithFlags(&pl->exec, pl->graph,
+                                        cudaGraphInstantiateFlagUseNodePriority);
+  }
+  cudaStreamDestroy(cap_hi);
+  cudaStreamDestroy(cap);
+  if (rc != HC_OK) return fail(rc);
+  if (e != cudaSuccess) {
+    set_err(std::string("graph capture: ") + cudaGetErrorString(e));
+    return fail(HC_ERR_CUDA);
+  }
+  if (cur != p->device) cudaSetDevice(cur);
+  *out = pl;
+  return HC_OK;
+}
+
+hc_status hc_plan_run(hc_plan* pl, const hc_batch_desc* b, hc_batch** out) {
+  g_err.clear();
+  cudaGetLastError();  // launch errors checked below are this call's own
+  if (!pl || pl->magic != 0x48435050u || !out) {
+    set_err("invalid plan");
+    return HC_ERR_INVALID;
+  }
+  hc_problem* p = pl->p;
+  hc_status rc = validate_batch(p, b);
+  if (rc != HC_OK) return rc;
+  if (b->n_instances != pl->n_inst) {
+    set_err("batch size differs from the plan's");
+    return HC_ERR_INVALID;
+  }
+  int cur = 0;
+  HC_CUDA(cudaGetDevice(&cur));
+  if (cur != p->device) HC_CUDA(cudaSetDevice(p->device));
+  const bool devptrs = (b->flags & HC_DEVICE_PTRS) != 0;
+  hc_batch* bt = new hc_batch;
+  bt->p = p;
+  bt->stream = (cudaStream_t)b->stream;
+  bt->n_inst = pl->n_inst;
+  bt->items = pl->items;
+  bt->evk0 = pl->ek0;
+  bt->evk1 = pl->ek1;
+  bt->evk2 = pl->ek2;
+  bt->owns_kernel_events = false;
+  cudaStream_t st = bt->stream;
+  auto fail = [&](hc_status s) {
+    cudaStreamSynchronize(st);
+    release_batch(bt);
+    if (cur != p->device) cudaSetDevice(cur);
+    return s;
+  };
+#define HC_TRYCUDA(call)                                           \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) {                                       \
+      set_err(std::string(#call) + ": " + cudaGetErrorString(e_)); \
+      return fail(HC_ERR_CUDA);                                    \
+    }                                                              \
+  } while (0)
+  HC_TRYCUDA(cudaEventCreate(&bt->ev0));
+  HC_TRYCUDA(cudaEventCreate(&bt->ev1));
+  void* pin = pinned_slot_get();
+  if (!pin) {
+    set_err("cudaMallocHost failed");
+    return fail(HC_ERR_OOM);
+  }
+  bt->h_ctl = (unsigned long long*)pin;
+  bt->owns_ctl = true;
+  std::memset(pin, 0, sizeof(unsigned long long) * 16);
+  // runs of one plan share its device buffers: each starts after the
+  // previous one's last copy, whatever stream it was enqueued on
+  HC_TRYCUDA(cudaStreamWaitEvent(st, pl->done, 0));
+  HC_TRYCUDA(cudaEventRecord(bt->ev0, st));
+  const void* src = p->terms ? (const void*)b->p1 : (const void*)b->coef;
+  if (src) {
+    HC_TRYCUDA(cudaMemcpyAsync(pl->d_in, src, pl->in_bytes, cudaMemcpyDefault, st));
+  } else if (!p->terms) {  // every instance uses the problem's coefficients
+    for (int64_t i = 0; i < pl->n_inst; ++i)
+      HC_TRYCUDA(cudaMemcpyAsync(static_cast<char*>(pl->d_in) + i * 16 * p->T, p->d_coef,
+                                 16 * (size_t)p->T, cudaMemcpyDeviceToDevice, st));
+  }
+  HC_TRYCUDA(cudaGraphLaunch(pl->exec, st));
+  HC_TRYCUDA(cudaMemcpyAsync(bt->h_ctl, pl->B.d_ctl, sizeof(unsigned long long) * 16,
+                             cudaMemcpyDeviceToHost, st));
+  const int64_t items = pl->items;
+  const size_t xb = sizeof(double) * 2 * p->n * items;
+  struct Out {
+    void* user;
+    const void* dev;
+    size_t bytes;
+  };
+  const Out outs[4] = {{b->x_out, pl->B.d_x, xb},
+                       {b->status_out, pl->B.d_status, (size_t)items},
+                       {b->steps_out, pl->B.d_steps, sizeof(int32_t) * 3 * items},
+                       {b->be_out, pl->B.d_be, sizeof(double) * items}};
+  for (const Out& o : outs) {
+    if (!o.user) continue;
+    if (devptrs || is_pinned_host(o.user) || is_device_ptr(o.user)) {
+      HC_TRYCUDA(cudaMemcpyAsync(o.user, o.dev, o.bytes, cudaMemcpyDefault, st));
+    } else {
+      void* pin;
+      if (cudaMallocHost(&pin, o.bytes) != cudaSuccess) {
+        set_err("cudaMallocHost failed");
+        return fail(HC_ERR_OOM);
+      }
+      bt->pinned.push_back(pin);
+      bt->copies.push_back({o.user, pin, o.bytes});
+      HC_TRYCUDA(cudaMemcpyAsync(pin, o.dev, o.bytes, cudaMemcpyDeviceToHost, st));
+    }
+  }
+  HC_TRYCUDA(cudaEventRecord(bt->ev1, st));
+  HC_TRYCUDA(cudaEventRecord(pl->done, st));
+#undef HC_TRYCUDA
+  if (cur != p->device) cudaSetDevice(cur);
+  *out = bt;
+  return HC_OK;
 }
 
 hc_status hc_poll(hc_batch* b, int64_t timeout_us, hc_batch_result* r) {
@@ -1148,10 +1476,15 @@ hc_status hc_poll(hc_batch* b, int64_t timeout_us, hc_batch_result* r) {
     r->esc_accepted = (int64_t)b->h_ctl[3];
     r->esc_rejected = (int64_t)b->h_ctl[4];
     r->esc_newton = (int64_t)b->h_ctl[5];
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, b->ev0, b->ev1) == cudaSuccess) r->device_ms = ms;
-    if (cudaEventElapsedTime(&ms, b->evk0, b->evk1) == cudaSuccess) r->track_ms = ms;
-    if (cudaEventElapsedTime(&ms, b->evk1, b->evk2) == cudaSuccess) r->escalate_ms = ms;
+    auto elapsed = [](cudaEvent_t a, cudaEvent_t z) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, a, z) == cudaSuccess) return (double)ms;
+      cudaGetLastError();  // not recorded: report 0 and leave no error behind
+      return 0.0;
+    };
+    r->device_ms = elapsed(b->ev0, b->ev1);
+    r->track_ms = elapsed(b->evk0, b->evk1);
+    r->escalate_ms = elapsed(b->evk1, b->evk2);
   }
   return HC_OK;
 }
@@ -1229,12 +1562,11 @@ void hc_destroy(void* handle) {
     hc_batch* b = static_cast<hc_batch*>(handle);
     if (!b->done) cudaEventSynchronize(b->ev1);
     for (void* q : b->dev) cudaFreeAsync(q, b->stream);
+    b->dev.clear();
     cudaStreamSynchronize(b->stream);
-    for (void* q : b->pinned) cudaFreeHost(q);
-    if (b->h_ctl) pinned_slot_put(b->h_ctl);
-    for (cudaEvent_t e : {b->ev0, b->ev1, b->evk0, b->evk1, b->evk2}) cudaEventDestroy(e);
-    b->magic = 0;
-    delete b;
+    release_batch(b);
+  } else {
+    hc::destroy_plan_if(handle, magic);
   }
 }
 

@@ -146,6 +146,11 @@ _lib.hc_server_wait.argtypes = [_P, ctypes.c_uint64, ctypes.c_int64, _P, _P,
 _lib.hc_server_stats.restype = ctypes.c_int32
 _lib.hc_server_stats.argtypes = [_P, ctypes.POINTER(ctypes.c_int64 * 5)]
 
+_lib.hc_plan_create.restype = ctypes.c_int32
+_lib.hc_plan_create.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(_P)]
+_lib.hc_plan_run.restype = ctypes.c_int32
+_lib.hc_plan_run.argtypes = [_P, ctypes.POINTER(hc_batch_desc), ctypes.POINTER(_P)]
+
 _lib.hc_track_dense_noalloc.restype = ctypes.c_int32
 _lib.hc_track_dense_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(hc_settings), ctypes.c_int32, _P, _P, _P, _P,
@@ -155,7 +160,7 @@ EXPORTED = ("hc_status_string", "hc_last_error", "hc_default_settings", "hc_crea
             "hc_problem_paths", "hc_problem_query", "hc_track_batch", "hc_poll", "hc_destroy",
             "hc_measure_fma_peak", "hc_track_dense_noalloc", "hc_server_default_config",
             "hc_server_create", "hc_server_submit", "hc_server_wait", "hc_server_stats",
-            "hc_autotune")
+            "hc_autotune", "hc_plan_create", "hc_plan_run")
 
 
 def problem_query(problem: int) -> dict:
@@ -351,10 +356,7 @@ class Problem:
     def __del__(self):
         self.close()
 
-    def track(self, n_instances=1, coef=None, p1=None, stream=None, device_out=None,
-              x_out=None, status_out=None, steps_out=None, be_out=None, device=False):
-        """Enqueue a batch; returns a Batch.  Host mode (default) allocates numpy
-        outputs; with device=True pass torch CUDA tensors (inputs and outputs)."""
+    def _desc(self, n_instances, coef, p1, stream, x_out, status_out, steps_out, be_out, device):
         I, P, n = int(n_instances), self.paths, self.n
         if not device:
             x_out = np.zeros((I, P, n), np.complex128) if x_out is None else x_out
@@ -375,9 +377,20 @@ class Problem:
         b.status_out = _addr(status_out)
         b.steps_out = _addr(steps_out)
         b.be_out = _addr(be_out)
+        return b, dict(x=x_out, status=status_out, steps=steps_out, be=be_out, coef=coef, p1=p1)
+
+    def track(self, n_instances=1, coef=None, p1=None, stream=None, device_out=None,
+              x_out=None, status_out=None, steps_out=None, be_out=None, device=False):
+        """Enqueue a batch; returns a Batch.  Host mode (default) allocates numpy
+        outputs; with device=True pass torch CUDA tensors (inputs and outputs)."""
+        b, bufs = self._desc(n_instances, coef, p1, stream, x_out, status_out, steps_out, be_out,
+                             device)
         h = track_batch(self.h, b)
-        return Batch(h, self, dict(x=x_out, status=status_out, steps=steps_out, be=be_out,
-                                   coef=coef, p1=p1))
+        return Batch(h, self, bufs)
+
+    def plan(self, n_instances=1):
+        """A Plan: this batch size captured once as a CUDA graph (hc_plan_create)."""
+        return Plan(self, n_instances)
 
     def autotune(self, n_instances=1, coef=None, p1=None):
         """hc_autotune on a host sample batch; returns the report as a dict and
@@ -400,6 +413,40 @@ class Problem:
                     tried=[dict(precision=rep.tried[i].precision, lanes=rep.tried[i].lanes,
                                 max_first_corr_fp32=rep.tried[i].max_first_corr_fp32)
                            for i in range(rep.n_candidates)])
+
+
+class Plan:
+    """hc_plan_create / hc_plan_run: replays one batch size of a problem as a
+    CUDA graph over device buffers the plan owns."""
+
+    def __init__(self, problem, n_instances):
+        h = _P()
+        _check(_lib.hc_plan_create(problem.h, int(n_instances), ctypes.byref(h)), "hc_plan_create")
+        self.h = h.value
+        self.problem = problem
+        self.n_instances = int(n_instances)
+
+    def run(self, coef=None, p1=None, stream=None, x_out=None, status_out=None, steps_out=None,
+            be_out=None, device=False):
+        """Enqueue one replay; returns a Batch (same outputs as Problem.track)."""
+        sysm = self.problem.system
+        for a, per in ((coef, sysm.n_terms), (p1, sysm.n_params)):
+            if a is not None and int(np.prod(a.shape)) != self.n_instances * int(per):
+                raise ValueError(f"input holds {int(np.prod(a.shape))} values, the plan takes "
+                                 f"{self.n_instances} x {int(per)}")
+        b, bufs = self.problem._desc(self.n_instances, coef, p1, stream, x_out, status_out,
+                                     steps_out, be_out, device)
+        h = _P()
+        _check(_lib.hc_plan_run(self.h, ctypes.byref(b), ctypes.byref(h)), "hc_plan_run")
+        return Batch(h.value, self.problem, bufs)
+
+    def close(self):
+        if getattr(self, "h", None):
+            destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
 
 
 class Batch:
