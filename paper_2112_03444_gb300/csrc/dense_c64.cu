@@ -1,11 +1,24 @@
 // Dense total-degree tracking kernels: degree 3, FP64, n = 1..8.
-// lanes = 0 selects the default group width; the mixed kernels also come
-// with one path per warp (lanes = 32) for the autotuner.
+// lanes = 0 selects the default group width; lanes = 32 one path per warp with
+// every row's contraction split over the warp (re-tracking of a few hard paths).
 #include "dense_kernel.cuh"
 
 namespace hc {
 
 KernelRef dense_ref_d3_64(int n, int lanes) {
+  if (lanes == 32) {
+    switch (n) {
+      case 1: return dense_ref<3, false, 1, 32>();
+      case 2: return dense_ref<3, false, 2, 32>();
+      case 3: return dense_ref<3, false, 3, 32>();
+      case 4: return dense_ref<3, false, 4, 32>();
+      case 5: return dense_ref<3, false, 5, 32>();
+      case 6: return dense_ref<3, false, 6, 32>();
+      case 7: return dense_ref<3, false, 7, 32>();
+      case 8: return dense_ref<3, false, 8, 32>();
+      default: break;
+    }
+  }
   switch (n) {
     case 1: return dense_ref<3, false, 1>();
     case 2: return dense_ref<3, false, 2>();

@@ -18,6 +18,7 @@ struct DenseProblem {
     h.D64 = a->D64 ? a->D64 + inst * a->Dstride : nullptr;
     h.E = a->E + inst * a->Estride;
     h.gamma = a->gamma;
+    h.gamma32 = a->gamma32;
     h.Vf = sm.vf;
     h.Vd = sm.vd;
     return h;

@@ -1,6 +1,6 @@
 // Dense total-degree tracking kernels: degree 2, mixed FP32/FP64, n = 1..12.
-// lanes = 0 selects the default group width; the mixed kernels also come
-// with one path per warp (lanes = 32) for the autotuner.
+// lanes = 0 selects the default group width; lanes = 32 one path per warp with
+// every row's contraction split over the warp (autotuner candidate).
 #include "dense_kernel.cuh"
 
 namespace hc {

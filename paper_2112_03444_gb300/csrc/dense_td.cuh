@@ -50,6 +50,7 @@ struct DenseTD {
   const cx<double>* D64;
   const cx<double>* E;
   cx<double> gamma;
+  cx<float> gamma32;
   const cx<float>* Vf;   // the group's shared copies of the evaluation point
   const cx<double>* Vd;
 
@@ -63,19 +64,48 @@ struct DenseTD {
       return Vd;
   }
 
+  // Groups wider than the encoding stride (one path per warp) split every
+  // row's contraction over PARTS lanes -- lane i works on row i mod L, part
+  // i / L -- and add the partial sums with shuffles: a path then keeps the
+  // whole warp busy, which is what bounds the FP64 re-tracking of a handful
+  // of hard paths (an FP64 warp instruction costs the same pipe time with 8
+  // or 32 active lanes).
+  static constexpr int PARTS = (L_GROUP > L) ? L_GROUP / L : 1;
+  static_assert(PARTS == 1 || L_GROUP == 32, "split rows need the whole warp");
+
+  template <class R>
+  __device__ __forceinline__ static cx<R> part_sum(cx<R> v) {
+    if constexpr (PARTS > 1) {
+#pragma unroll
+      for (int o = L; o < L * PARTS; o <<= 1) {
+        v.re += __shfl_xor_sync(0xffffffffu, v.re, o);
+        v.im += __shfl_xor_sync(0xffffffffu, v.im, o);
+      }
+    }
+    return v;
+  }
+  // m-th outer index of a part: zigzag over blocks of PARTS indices, so that
+  // triangular inner loops give every part the same work (identity for
+  // PARTS = 1)
+  __device__ __forceinline__ static int zigzag(int m, int part) {
+    return (m & 1) ? ((m + 1) * PARTS - 1 - part) : (m * PARTS + part);
+  }
+
   // The contraction index k runs in a loop that is not unrolled (x_k is read
   // from the group's shared copy of the point); the rows j stay unrolled so
   // that row[] lives in registers.  Code size O(N) instead of O(N^2) / O(N^3).
   template <class R>
   __device__ __forceinline__ void eval(const cx<R> (&x)[N], int i, R t, R omt, cx<R> (&row)[N + 1],
                                        cx<R>& H, cx<R>& Ht) const {
-    const cx<R>* D = dptr<R>() + (i < N ? i : 0);
+    const int r = i & (L - 1);                   // this lane's row
+    const int part = (PARTS > 1) ? i / L : 0;    // and its share of the contraction
+    const cx<R>* D = dptr<R>() + (r < N ? r : 0);
     const cx<R>* V = vptr<R>();
     cx<R> a1[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) a1[j] = czero<R>();
 #pragma unroll 2
-    for (int k = 0; k < N; ++k) {
+    for (int k = part; k < N; k += PARTS) {
       const cx<R> xk = V[k];
       const cx<R>* Dk = D + (1 + k) * L;
 #pragma unroll
@@ -83,6 +113,10 @@ struct DenseTD {
     }
     cx<R> F = D[(N * S::MP) * L];
     if constexpr (DEG == 2) {
+      if constexpr (PARTS > 1) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) a1[j] = part_sum(a1[j]);
+      }
 #pragma unroll
       for (int j = 0; j < N; ++j) {
         const cx<R> a0 = D[(j * S::MP) * L];
@@ -94,7 +128,9 @@ struct DenseTD {
 #pragma unroll
       for (int j = 0; j < N; ++j) a2[j] = czero<R>();
 #pragma unroll 1
-      for (int k = 0; k < N; ++k) {
+      for (int m = 0;; ++m) {
+        const int k = zigzag(m, part);
+        if (k >= N) break;
         cx<R> in[N];
 #pragma unroll
         for (int j = 0; j < N; ++j) in[j] = czero<R>();
@@ -110,22 +146,43 @@ struct DenseTD {
 #pragma unroll
         for (int j = 0; j < N; ++j) a2[j] = cfma(xk, in[j], a2[j]);
       }
+      if constexpr (PARTS > 1) {
+        // partial rows and the partial Euler sum, then one reduction each
+        cx<R> fp = czero<R>();
 #pragma unroll
-      for (int j = 0; j < N; ++j) {
-        const cx<R> a0 = D[(j * S::MP) * L];
-        row[j] = a0 + a1[j] + a2[j];
-        F = cfma(x[j], a0 + R(0.5) * a1[j] + R(1.0 / 3.0) * a2[j], F);
+        for (int j = 0; j < N; ++j) {
+          fp = cfma(x[j], R(0.5) * a1[j] + R(1.0 / 3.0) * a2[j], fp);
+          a1[j] = part_sum(a1[j] + a2[j]);
+        }
+        F = F + part_sum(fp);
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          const cx<R> a0 = D[(j * S::MP) * L];
+          row[j] = a0 + a1[j];
+          F = cfma(x[j], a0, F);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          const cx<R> a0 = D[(j * S::MP) * L];
+          row[j] = a0 + a1[j] + a2[j];
+          F = cfma(x[j], a0 + R(0.5) * a1[j] + R(1.0 / 3.0) * a2[j], F);
+        }
       }
     }
     cx<R> xi = x[0];
 #pragma unroll
     for (int k = 1; k < N; ++k)
-      if (k == i) xi = x[k];
+      if (k == r) xi = x[k];
     // G_i = xi^d - 1, dG_i/dx_i = d xi^(d-1)
     const cx<R> xi2 = xi * xi;
     const cx<R> G = (DEG == 2 ? xi2 : xi2 * xi) - mk<R>(R(1), R(0));
     const cx<R> Gd = R(DEG) * (DEG == 2 ? xi : xi2);
-    const cx<R> gm = cvt<R>(gamma);
+    cx<R> gm;
+    if constexpr (std::is_same<R, float>::value)
+      gm = gamma32;
+    else
+      gm = gamma;
     const cx<R> gG = gm * G;
     H = t * F + omt * gG;
     Ht = F - gG;
@@ -133,7 +190,7 @@ struct DenseTD {
 #pragma unroll
     for (int j = 0; j < N; ++j) {
       row[j] = t * row[j];
-      if (j == i) row[j] = row[j] + gd;
+      if (j == r) row[j] = row[j] + gd;
     }
   }
 
@@ -142,7 +199,7 @@ struct DenseTD {
   // backward-error denominator sum |c| |x^a| (FP32 accuracy is enough for a
   // ratio test) is returned in sc.  Runtime loops: this code runs a few
   // times per path and must not crowd the tracking loop out of the
-  // instruction cache.
+  // instruction cache.  Split over PARTS lanes like eval (outer index j).
   template <bool SCALE_T>
   __device__ __forceinline__ void residual64(const cx<double>* xs, int i, double t, double omt,
                                              cx<double>& H, double& sc) const {
@@ -151,12 +208,21 @@ struct DenseTD {
 
   __device__ __noinline__ void residual64_impl(const cx<double>* xs, int i, double t, double omt,
                                                bool scale, cx<double>& H, double& sc) const {
-    const cx<double>* e = E + (i < N ? i : 0);
-    cx<double> F = e[0];
-    float Ssum = scale ? cabs2(cvt<float>(e[0])) : 0.f;
-    int m = 1;
+    const int r = i & (L - 1);
+    const int part = (PARTS > 1) ? i / L : 0;
+    const cx<double>* e = E + (r < N ? r : 0);
+    cx<double> F = part == 0 ? e[0] : czero<double>();
+    float Ssum = (scale && part == 0) ? cabs2(cvt<float>(e[0])) : 0.f;
 #pragma unroll 1
-    for (int j = 0; j < N; ++j) {
+    for (int mm = 0;; ++mm) {
+      const int j = zigzag(mm, part);
+      if (j >= N) break;
+      // first Horner coefficient of block j: 1 + sum over earlier blocks
+      // (block j' holds 1 + sum_{k <= j'} (DEG == 2 ? 1 : k + 2) entries)
+      int m = 1;
+#pragma unroll 1
+      for (int jj = 0; jj < j; ++jj)
+        m += 1 + (DEG == 2 ? jj + 1 : (jj + 1) * jj / 2 + 2 * (jj + 1));
       cx<double> in = e[m * L];
       float ins = scale ? cabs2(cvt<float>(e[m * L])) : 0.f;
       ++m;
@@ -186,7 +252,14 @@ struct DenseTD {
       F = cfma(xj, in, F);
       if (scale) Ssum += cabs2(cvt<float>(xj)) * ins;
     }
-    const cx<double> xi = xs[i < N ? i : 0];
+    if constexpr (PARTS > 1) {
+      F = part_sum(F);
+      if (scale) {
+#pragma unroll
+        for (int o = L; o < L * PARTS; o <<= 1) Ssum += __shfl_xor_sync(0xffffffffu, Ssum, o);
+      }
+    }
+    const cx<double> xi = xs[r < N ? r : 0];
     const cx<double> xi2 = xi * xi;
     const cx<double> G = (DEG == 2 ? xi2 : xi2 * xi) - mk<double>(1.0, 0.0);
     H = t * F + omt * (gamma * G);

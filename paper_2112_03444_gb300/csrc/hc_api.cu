@@ -517,7 +517,7 @@ bool encode_terms(hc_problem* p, std::vector<hc::TermRec>& rec, std::vector<doub
       }
   p->terms = true;
   p->L = L;
-  p->extra = 1 + 2 * P;
+  p->extra = 1 + 3 * P;
   p->paths = p->n_start;
   return true;
 }
@@ -596,6 +596,14 @@ hc_status launch_tracker(const hc::KernelRef& k, const hc::DenseArgs& a, int64_t
 }  // namespace
 
 // ------------------------------------------------------------------ C-ABI
+namespace hc {
+KernelRef retrack_kernel(int deg, int n, bool mixed) {
+  const KernelRef k = dense_kernel(deg, n, mixed, 32);
+  return k.fn ? k : dense_kernel(deg, n, mixed, 0);
+}
+}  // namespace hc
+using hc::retrack_kernel;
+
 extern "C" {
 
 const char* hc_status_string(int32_t s) {
@@ -910,6 +918,7 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
   cd.queue = B.d_ctl + 6;
   cd.x32_out = nullptr;
   cd.start_hi = 1;
+  cd.spread = 1;
   cd.dup_list = nullptr;
   cd.dup_count = nullptr;
   hc::LaunchCommon ce = cm;
@@ -919,6 +928,7 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
   ce.esc_list = nullptr;
   ce.x32_out = nullptr;
   ce.esc_steps = B.d_ctl + 3;
+  ce.spread = 1;
   ce.dup_list = nullptr;
   ce.dup_count = nullptr;
   // the count of re-tracked items is only known on the device: the grid
@@ -984,6 +994,7 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
     a.Dstride = p->Dstride;
     a.Estride = p->Estride;
     a.gamma = cx<double>{p->gamma[0], p->gamma[1]};
+    a.gamma32 = cx<float>{(float)p->gamma[0], (float)p->gamma[1]};
     const hc::KernelRef k = hc::dense_kernel(p->deg, n, mixed, mixed ? p->s.lanes : 0);
     if (!k.fn) {
       set_err("no kernel for this problem shape");
@@ -995,12 +1006,15 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
     if (escalate) {
       if (ev.capture) HC_CUDA(cudaEventRecord(ev.fork, st));
       if ((rc = dedupe()) != HC_OK) return rc;
+      // the re-tracking tiers see a few paths each: one path per warp with
+      // the rows split over the warp where that variant exists
       hc::DenseArgs dd = a;
       dd.c = cd;
-      if ((rc = launch_tracker(k, dd, esc_groups, hs)) != HC_OK) return rc;
+      if ((rc = launch_tracker(retrack_kernel(p->deg, n, true), dd, esc_groups, hs)) != HC_OK)
+        return rc;
       hc::DenseArgs e = a;
       e.c = ce;
-      if ((rc = launch_tracker(hc::dense_kernel(p->deg, n, false, 0), e, esc_groups, hs)) != HC_OK)
+      if ((rc = launch_tracker(retrack_kernel(p->deg, n, false), e, esc_groups, hs)) != HC_OK)
         return rc;
       HC_CUDA(mark(ev.ek2, hs));
       if (ev.capture) HC_CUDA(cudaEventRecord(ev.join, hs));

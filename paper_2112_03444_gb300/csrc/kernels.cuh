@@ -38,6 +38,9 @@ struct LaunchCommon {
   int start_hi;                 // mixed kernel: track every path with the FP64 state, FP64
                                 // residuals and FP64 tolerances from t = 0 (re-tracking of
                                 // colliding paths)
+  int spread;                   // first round of items round-robin over the blocks (one
+                                // per block before any second), then the queue: a short
+                                // list of FP64-heavy paths lands on as many SMs as it can
 };
 
 struct DenseArgs {
@@ -47,6 +50,7 @@ struct DenseArgs {
   const cx<double>* E;
   int64_t Dstride, Estride;  // complex elements per instance
   cx<double> gamma;
+  cx<float> gamma32;         // FP32 copy (FP32 evaluations convert nothing)
 };
 
 // One homogenised term tuple: scalar (FP32 copy) and up to 8 factor indices
@@ -65,7 +69,7 @@ struct TermArgs {
   int kcnt[kMaxTermEntries], koff[kMaxTermEntries], kdeg[kMaxTermEntries];
   int P;                 // number of parameters
   int ls;                // lane stride of the tuple tables (and V's offset of the 1)
-  int extra;             // shared-memory entries behind the point: 1 + 2P
+  int extra;             // shared-memory entries behind the point: 1 + 3P
   const double2* p0;     // [P]
   const double2* p1;     // [instances][P]
   const double2* start;  // [paths][n]
@@ -83,6 +87,9 @@ inline int lanes_for(int n) { return n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : 32
 // lanes = 0: default group width; 32: one path per warp (mixed kernels, n <= 16)
 KernelRef dense_kernel(int deg, int n, bool mixed, int lanes);  // fn == nullptr if absent
 KernelRef term_kernel(int n, bool mixed, int lanes);            // fn == nullptr if absent
+// Kernel of the re-tracking tiers (few paths): one path per warp with split
+// rows where available, else the default width.
+KernelRef retrack_kernel(int deg, int n, bool mixed);
 
 // Defined in server.cu: frees a server if magic is the server's magic.
 bool destroy_server_if(void* handle, uint32_t magic);

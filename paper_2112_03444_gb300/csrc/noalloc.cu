@@ -282,6 +282,7 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
   a.Dstride = Ds;
   a.Estride = Es;
   a.gamma = hc::cx<double>{gamma[0], gamma[1]};
+  a.gamma32 = hc::cx<float>{(float)gamma[0], (float)gamma[1]};
 
   int dev = 0, sms = 0;
   NA_CUDA(cudaGetDevice(&dev));
@@ -314,9 +315,10 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
     dd.c.queue = ctl + 6;
     dd.c.x32_out = nullptr;
     dd.c.start_hi = 1;
+    dd.c.spread = 1;
     dd.c.dup_list = nullptr;
     dd.c.dup_count = nullptr;
-    NA_CUDA(launch(k, dd, items));
+    NA_CUDA(launch(hc::retrack_kernel(degree, n, true), dd, items));
     hc::DenseArgs e = a;
     e.c.count_dev = ctl + 2;
     e.c.items = esc;
@@ -324,9 +326,10 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
     e.c.esc_list = nullptr;
     e.c.x32_out = nullptr;
     e.c.esc_steps = ctl + 3;
+    e.c.spread = 1;
     e.c.dup_list = nullptr;
     e.c.dup_count = nullptr;
-    NA_CUDA(launch(hc::dense_kernel(degree, n, false, 0), e, items));
+    NA_CUDA(launch(hc::retrack_kernel(degree, n, false), e, items));
   }
 #undef NA_CUDA
   return HC_OK;

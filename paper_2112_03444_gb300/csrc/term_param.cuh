@@ -4,8 +4,9 @@
 // Every entry of row i -- dH_i/dx_j (j < N), dH_i/dt and H_i -- is a sum of
 // K_e tuples (s, m_1, ..., m_D): s * V[m_1] * ... * V[m_D], where V is the
 // per-path vector
-//   V = [ x_0 .. x_{N-1} | pad to L | 1 | p(t)_0 .. p(t)_{P-1} | dp_0 .. dp_{P-1} ]
-// (dp = p1 - p0 = dp/dt).  As in the paper, every entry is padded to the same
+//   V = [ x_0 .. x_{N-1} | pad to L | 1 | p(t)_0 .. p(t)_{P-1} | dp_0 .. dp_{P-1} | p0 ]
+// (dp = p1 - p0 = dp/dt; p0 is kept so that FP32 evaluations form p(t) =
+// p0 + t dp without FP64 arithmetic).  As in the paper, every entry is padded to the same
 // number of tuples K_e for all rows, and here also to the same number of
 // factors D_e (padding factors point at the constant 1), so that the lanes of
 // a path -- one row each -- run the same loop.  The library derives the
@@ -32,7 +33,7 @@ struct TermEval {
   cx<float>* Vf;
   cx<double>* Vd;
 
-  // constant part of V for this path: the 1 and dp
+  // constant part of V for this path: the 1, dp and (FP32) p0
   __device__ __forceinline__ void init(const Group&) const {
     const int P = a->P, LS = a->ls;
     const double2* p1 = a->p1 + inst * P;
@@ -44,6 +45,7 @@ struct TermEval {
       const cx<double> d = mk<double>(p1[l].x - a->p0[l].x, p1[l].y - a->p0[l].y);
       Vd[LS + 1 + P + l] = d;
       Vf[LS + 1 + P + l] = cvt<float>(d);
+      Vf[LS + 1 + 2 * P + l] = mk<float>((float)a->p0[l].x, (float)a->p0[l].y);
     }
   }
 
@@ -60,15 +62,20 @@ struct TermEval {
       return Vd;
   }
 
-  // p(t) into V (each lane a share), then wait for the group
+  // p(t) into V (each lane a share), then wait for the group.  FP64:
+  // (1-t) p0 + t p1 from the inputs; FP32: p0 + t dp from the FP32 copies.
   template <class R>
-  __device__ __forceinline__ void put_params(double t) const {
+  __device__ __forceinline__ void put_params(R t) const {
     const int P = a->P, LS = a->ls;
-    const double2* p1 = a->p1 + inst * P;
-    cx<R>* V = vptr<R>();
-    for (int l = g.gl; l < P; l += L) {
-      const double2 q0 = a->p0[l], q1 = p1[l];
-      V[LS + 1 + l] = cvt<R>(mk<double>((1.0 - t) * q0.x + t * q1.x, (1.0 - t) * q0.y + t * q1.y));
+    if constexpr (std::is_same<R, float>::value) {
+      for (int l = g.gl; l < P; l += L)
+        Vf[LS + 1 + l] = cfma(mk<float>(t, 0.f), Vf[LS + 1 + P + l], Vf[LS + 1 + 2 * P + l]);
+    } else {
+      const double2* p1 = a->p1 + inst * P;
+      for (int l = g.gl; l < P; l += L) {
+        const double2 q0 = a->p0[l], q1 = p1[l];
+        Vd[LS + 1 + l] = mk<double>((1.0 - t) * q0.x + t * q1.x, (1.0 - t) * q0.y + t * q1.y);
+      }
     }
     __syncwarp(g.mask);
   }
@@ -97,7 +104,7 @@ struct TermEval {
   template <class R>
   __device__ __forceinline__ void eval(const cx<R> (&)[N], int i, R t, R, cx<R> (&row)[N + 1],
                                        cx<R>& H, cx<R>& Ht) const {
-    put_params<R>((double)t);
+    put_params<R>(t);
     const cx<R>* V = vptr<R>();
     const int ii = i < N ? i : 0;
 #pragma unroll

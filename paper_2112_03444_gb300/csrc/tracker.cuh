@@ -107,6 +107,13 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
   // FP64, or FP32 solves refined by FP64 residuals) use the FP64 ones.
   const float tol32 = (float)s.newton_tol_fp32, tol64 = (float)s.newton_tol;
   const float corr32 = (float)s.max_first_corr_fp32, corr64 = (float)s.max_first_corr;
+  // Step control of the FP32 phase runs on FP32 copies of t, dt and the
+  // limits: the FP64 pipe issues at a small fraction of the FP32 rate, so a
+  // handful of FP64 bookkeeping instructions per evaluation would cost as
+  // much issue time as the evaluation itself.  t is exact to FP32 rounding
+  // there, far below the FP32 corrector's tolerance.
+  const float tAf = (float)tA, dt_maxf = (float)s.dt_max, dt_min32f = (float)s.dt_min_fp32;
+  const float rinf_f = (float)fmin(s.r_inf, 3.0e38);
 
   // ---- per-path state (identical control state in all lanes of the group)
   HOM hom = prob.hom(0);
@@ -114,14 +121,16 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
   cx<double> xd = czero<double>();  // FP64 state
   cx<float> xf = czero<float>();    // FP32 state
   bool hi = !MIXED;                 // the state lives in xd rather than xf
+  // t, dt, h, t1: FP64-state phase; tf, dtf, hf, t1f: FP32 phase
   double t = 0.0, dt = 0.0, h = 0.0, t1 = 0.0;
-  float tf = 0.f, hf = 0.f, t1f = 0.f;  // FP32 copies for the FP32 phase
+  float tf = 0.f, dtf = 0.f, hf = 0.f, t1f = 0.f;
   int consec = 0, nacc = 0, nrej = 0, nnewt = 0, status = 0;
   int mode = M_FETCH, stage = 0, it = 0;
   cx<R> kprev = czero<R>(), ksum = czero<R>();
   cx<float> xpf = czero<float>();   // corrector iterate (FP32 state)
   cx<double> xpd = czero<double>(); // corrector iterate (FP64 state)
   bool step_ok = true;
+  bool first_fetch = true;
   float cond_inorm = 0.f, cond_anorm = 0.f, be = 0.f;
 
   cx<R> row[N + 1];
@@ -129,22 +138,34 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
   cx<R> sol[1];
   int col;
 
+  // hi is constant true in the plain FP64 kernel; say so to the compiler
+  auto HI = [&]() { return !MIXED || hi; };
   auto begin_step = [&]() {
-    const double t_stop = hi ? 1.0 : tA;
-    const bool last = dt >= t_stop - t;
-    h = last ? t_stop - t : dt;
-    t1 = last ? t_stop : t + h;
-    tf = (float)t;
-    hf = (float)h;
-    t1f = (float)t1;
+    if (HI()) {
+      const bool last = dt >= 1.0 - t;
+      h = last ? 1.0 - t : dt;
+      t1 = last ? 1.0 : t + h;
+    } else {
+      // a step ending within FP32 rounding of the phase end takes the rest
+      const bool last = 1.0001f * dtf >= tAf - tf;
+      hf = last ? tAf - tf : dtf;
+      t1f = last ? tAf : tf + hf;
+    }
     stage = 0;
     ksum = czero<R>();
     kprev = czero<R>();
     step_ok = true;
     mode = M_RK;
   };
+  // FP32 phase -> FP64-state phase at the current accepted point
+  auto promote = [&](double dt_new) {
+    xd = cvt<double>(xf);
+    t = (double)tf;
+    dt = dt_new;
+    hi = true;
+  };
   auto enter_refine = [&]() {
-    if (!hi) xd = cvt<double>(xf);
+    if (!HI()) xd = cvt<double>(xf);
     hi = true;
     mode = M_REFINE;
     it = 0;
@@ -152,19 +173,22 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
   auto reject = [&]() {
     ++nrej;
     consec = 0;
-    dt *= 0.5;
-    if (MIXED && !hi && dt < s.dt_min_fp32) {
-      // FP32 cannot resolve this stretch of the path (its corrector stalls at
-      // the FP32 noise floor): continue from the last accepted point with the
-      // FP64 state and FP64 residuals instead of failing the path.
-      xd = cvt<double>(xf);
-      hi = true;
-      dt = s.dt_min_fp32;
-      begin_step();
-    } else if (dt < s.dt_min) {
-      status = ST_FAIL_STEP;
-      mode = M_DONE;
+    if (HI()) {
+      dt *= 0.5;
+      if (dt < s.dt_min) {
+        status = ST_FAIL_STEP;
+        mode = M_DONE;
+      } else {
+        begin_step();
+      }
     } else {
+      dtf *= 0.5f;
+      if (dtf < dt_min32f) {
+        // FP32 cannot resolve this stretch of the path (its corrector stalls
+        // at the FP32 noise floor): continue from the last accepted point
+        // with the FP64 state and FP64 residuals instead of failing the path.
+        promote(s.dt_min_fp32);
+      }
       begin_step();
     }
   };
@@ -201,7 +225,7 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
             const bool to64 = base == ST_FAIL_STEP || base == ST_FAIL_MAXSTEPS ||
                               base == ST_SINGULAR || c.start_hi || !c.dup_list;
             if (c.t_io)
-              c.t_io[item] = (base == ST_FAIL_STEP || base == ST_FAIL_MAXSTEPS) ? t
+              c.t_io[item] = (base == ST_FAIL_STEP || base == ST_FAIL_MAXSTEPS) ? (hi ? t : (double)tf)
                              : (base == ST_SINGULAR)                            ? 1.0
                                                                                : 0.0;
             if (to64) {
@@ -229,8 +253,16 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
     }
     if (mode == M_FETCH) {
       unsigned long long q = 0;
-      if (g.gl == 0) q = atomicAdd(c.queue, 1ull);
-      q = __shfl_sync(g.mask, q, leader);
+      if (c.spread && first_fetch) {
+        // ticket = slot * blocks + block: consecutive items on different blocks
+        // (and so, for the first blocks of the grid, on different SMs)
+        q = (unsigned long long)(threadIdx.x / L) * gridDim.x + blockIdx.x;
+        first_fetch = false;
+      } else {
+        if (g.gl == 0) q = atomicAdd(c.queue, 1ull);
+        q = __shfl_sync(g.mask, q, leader);
+        if (c.spread) q += (unsigned long long)gridDim.x * (blockDim.x / L);
+      }
       if ((int64_t)q >= total) break;
       item = c.items ? c.items[q] : (int64_t)q;
       const int64_t inst = item / c.paths;
@@ -253,6 +285,8 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
       hi = !MIXED || c.start_hi;
       t = t0 > 0.0 ? t0 : 0.0;
       dt = s.dt_init;
+      tf = (float)t;
+      dtf = (float)s.dt_init;
       consec = nacc = nrej = nnewt = status = 0;
       be = 0.f;
       if (t >= 1.0)
@@ -266,38 +300,44 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
         mode = M_DONE;
         continue;
       }
-      if (MIXED && !hi && nacc + nrej >= s.max_steps_fp32) {  // FP32 step budget spent
-        xd = cvt<double>(xf);
-        hi = true;
+      if (!HI() && nacc + nrej >= s.max_steps_fp32) {  // FP32 step budget spent
+        promote((double)dtf);
         begin_step();
       }
     }
 
     // ---- 1. evaluation point and time (FP32 arithmetic in the FP32 phase)
-    double te = 1.0;
-    float tef = 1.f;
+    double te = 1.0;      // FP64-state phases
+    R ter = R(1), omt = R(0);  // the time the evaluator sees, and 1 - t
     bool need64 = false;
     if (mode == M_RK) {
-      if (hi) {
+      if (HI()) {
         const double cst = (stage == 0) ? 0.0 : (stage == 3 ? 1.0 : 0.5);
         te = (stage == 3) ? t1 : t + cst * h;
+        ter = (R)te;
+        omt = (R)(1.0 - te);
         const cx<double> p = xd + (cst * h) * cvt<double>(kprev);
         if (act) sm.vd[g.gl] = p;
         if (act) sm.vf[g.gl] = cvt<float>(p);
       } else {
         const float cst = (stage == 0) ? 0.f : (stage == 3 ? 1.f : 0.5f);
-        tef = (stage == 3) ? t1f : tf + cst * hf;
+        const float tt = (stage == 3) ? t1f : tf + cst * hf;
+        ter = (R)tt;
+        omt = (R)(1.f - tt);
         const cx<float> p = xf + (cst * hf) * cvt<float>(kprev);
         if (act) sm.vf[g.gl] = p;
       }
     } else if (mode == M_NEWTON) {
-      te = t1;
-      tef = t1f;
-      need64 = MIXED && hi;
-      if (hi) {
+      if (HI()) {
+        te = t1;
+        ter = (R)t1;
+        omt = (R)(1.0 - t1);
+        need64 = MIXED;
         if (act) sm.vd[g.gl] = xpd;
         if (act) sm.vf[g.gl] = cvt<float>(xpd);
       } else {
+        ter = (R)t1f;
+        omt = (R)(1.f - t1f);
         if (act) sm.vf[g.gl] = xpf;
       }
     } else {  // M_REFINE, M_COND: at the endpoint, t = 1
@@ -315,8 +355,6 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
     // ---- 2. row i of [dH/dx | rhs] and the solve
     {
       cx<R> H, Ht;
-      const R ter = hi ? (R)te : (R)tef;
-      const R omt = hi ? (R)(1.0 - te) : R(1) - ter;
       hom.template eval<R>(x, g.gl, ter, omt, row, H, Ht);
       if (mode == M_RK) {
         row[N] = -Ht;
@@ -352,7 +390,7 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
         if (!step_ok) {
           reject();
         } else {
-          if (hi)
+          if (HI())
             xpd = xd + (h / 6.0) * cvt<double>(ksum);
           else
             xpf = xf + (hf / 6.0f) * cvt<float>(ksum);
@@ -362,7 +400,7 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
       }
     } else if (mode == M_NEWTON) {
       float xn2;
-      if (hi) {
+      if (HI()) {
         xpd = xpd + cvt<double>(d);
         xn2 = gmaxf(g, act ? cnorm2(cvt<float>(xpd)) : 0.f);
       } else {
@@ -373,29 +411,31 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
       const float xn = sqrt_approx(xn2);
       const float dn = sqrt_approx(gmaxf(g, act ? (float)cnorm2(d) : 0.f));
       const bool bad = !sok || !(dn <= 3.0e38f) || !(xn <= 3.0e38f) ||
-                       (it == 0 && dn > (hi ? corr64 : corr32) * (1.f + xn));
-      if (!bad && dn <= (hi ? tol64 : tol32) * (1.f + xn)) {
+                       (it == 0 && dn > (HI() ? corr64 : corr32) * (1.f + xn));
+      if (!bad && dn <= (HI() ? tol64 : tol32) * (1.f + xn)) {
         // accept the step
-        if (hi)
-          xd = xpd;
-        else
-          xf = xpf;
-        t = t1;
+        bool at_end;
         ++nacc;
-        if (++consec >= s.grow_after) {
-          dt = fmin(2.0 * dt, s.dt_max);
-          consec = 0;
+        const bool grow = ++consec >= s.grow_after;
+        if (grow) consec = 0;
+        if (HI()) {
+          xd = xpd;
+          t = t1;
+          if (grow) dt = fmin(2.0 * dt, s.dt_max);
+          at_end = t >= 1.0;
+        } else {
+          xf = xpf;
+          tf = t1f;
+          if (grow) dtf = fminf(2.f * dtf, dt_maxf);
+          at_end = tf >= 1.f;
         }
-        if ((double)xn > s.r_inf) {
+        if (xn > rinf_f) {
           status = ST_DIVERGED;
           mode = M_DONE;
-        } else if (t >= 1.0) {
+        } else if (at_end) {
           enter_refine();
         } else {
-          if (!hi && t >= tA) {  // enter the FP64-state phase
-            xd = cvt<double>(xf);
-            hi = true;
-          }
+          if (!HI() && tf >= tAf) promote((double)dtf);  // enter the FP64-state phase
           begin_step();
         }
       } else if (bad || ++it >= s.max_newton) {
@@ -414,7 +454,7 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
         if (!fin) {
           status = ST_FAIL_NAN;
           mode = M_DONE;
-        } else if ((double)xnf > s.r_inf) {
+        } else if (xnf > rinf_f) {
           status = ST_DIVERGED;
           mode = M_DONE;
         } else {
