@@ -27,7 +27,6 @@ struct DenseProblem {
 
 template <int N, int DEG, bool MIXED, int L>
 __global__ void __launch_bounds__(kBlock, 4) dense_td_kernel(const DenseArgs a) {
-  static_assert(group_smem_bytes(L, 0) == kGroupSmemBytesPerLane * L, "group smem layout");
   extern __shared__ __align__(16) unsigned char smem[];
   const Group g = make_group<L>();
   const GroupMem sm = make_group_mem<L>(smem, 0);

@@ -583,7 +583,7 @@ hc_status launch_generic(const hc::KernelRef& k, void* args, size_t smem, int64_
 
 hc_status launch_tracker(const hc::KernelRef& k, const hc::DenseArgs& a, int64_t max_items,
                          cudaStream_t st) {
-  const size_t smem = (size_t)hc::kBlock * hc::kGroupSmemBytesPerLane;
+  const size_t smem = (size_t)hc::block_smem_bytes(k.lanes, 0);
   const Occ o = occupancy(k.fn, smem);
   const int64_t groups_per_block = hc::kBlock / k.lanes;
   int64_t want = (max_items + groups_per_block - 1) / groups_per_block;
@@ -962,9 +962,7 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
     ta.p1 = B.d_p1;
     ta.start = p->d_start;
     const hc::KernelRef k = hc::term_kernel(n, mixed, mixed ? p->s.lanes : 0);
-    auto smem_of = [&](int L) {
-      return (size_t)(hc::kBlock / L) * ((L + p->extra) * 16 + L * 16 + (L + p->extra) * 8);
-    };
+    auto smem_of = [&](int L) { return (size_t)hc::block_smem_bytes(L, p->extra); };
     HC_CUDA(mark(ev.ek0, st));
     if ((rc = launch_generic(k, &ta, smem_of(k.lanes), items, st)) != HC_OK) return rc;
     HC_CUDA(mark(ev.ek1, st));

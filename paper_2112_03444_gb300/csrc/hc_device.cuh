@@ -46,8 +46,13 @@ __device__ __forceinline__ cx<R> cfms(cx<R> a, cx<R> b, cx<R> acc) {
   return {fma(-a.re, b.re, fma(a.im, b.im, acc.re)), fma(-a.re, b.im, fma(-a.im, b.re, acc.im))};
 }
 
-// Correctly rounded reciprocal without the IEEE-division slow path.
-__device__ __forceinline__ float rcp(float v) { return __frcp_rn(v); }
+// Reciprocals: FP32 with the hardware approximation (relative error about
+// one ulp, ample for the FP32 solve); FP64 correctly rounded.
+__device__ __forceinline__ float rcp(float v) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+  return r;
+}
 __device__ __forceinline__ double rcp(double v) { return __drcp_rn(v); }
 
 // 1/z with scaling by max(|re|, |im|) so that |z|^2 cannot overflow for
@@ -129,41 +134,81 @@ __device__ __forceinline__ R gsum(const Group& g, R v) {
 // ties, found with one __reduce_max_sync on a key whose high bits are the
 // magnitude's float bits and whose low 5 bits encode the lane.
 //
+// The pivot row reaches the other lanes through shared memory: the pivot
+// lane stores its remaining columns (FP32: two complex numbers per 16-byte
+// store; the pivot column's slot carries 1/pivot), the group synchronises,
+// and every lane reads them back with 16-byte broadcast loads.  Two buffers
+// alternate, so one __syncwarp per pivot step orders writes after the
+// previous step's reads.  pv: 2 * ((N + NR + 1) & ~1) entries, 16-byte
+// aligned, private to the group.
+//
 // On return lane i with i < N holds in col the column it pivoted on and in
 // sol[r] the solution component x[col] of right-hand side r.  Returns false
 // if a pivot was zero or non-finite (the caller rejects the step).
 template <int N, int NR, class R>
 __device__ __forceinline__ bool gj_solve(const Group& g, cx<R> (&a)[N + NR], cx<R> (&sol)[NR],
-                                         int& col) {
+                                         int& col, cx<R>* pv) {
+  constexpr int W = N + NR;
+  constexpr int S = (W + 1) & ~1;  // entries per buffer (even: FP32 pairs stay 16-byte aligned)
   bool used = g.gl >= N;
-  cx<R> diag = mk<R>(R(1), R(0));
+  cx<R> dinv = mk<R>(R(1), R(0));  // 1 / pivot of this lane's row
   col = -1;
   bool ok = true;
 #pragma unroll
   for (int k = 0; k < N; ++k) {
+    // Every lane forms 1 / a[k] of its own row while the reduction picks the
+    // pivot (the reciprocal stays off the critical path).
+    const cx<R> inv = crecip(a[k]);
     const float m = (float)cabs1(a[k]);
     const unsigned key = used ? 0u : ((__float_as_uint(m) & ~31u) | (unsigned)(31 - g.wl));
     const unsigned kmax = __reduce_max_sync(g.mask, key);
     const unsigned mbits = kmax & ~31u;
     ok = ok && (mbits != 0u) && (mbits < 0x7f800000u);
     const int p = 31 - (int)(kmax & 31u);
-    const cx<R> pk = shfl(g.mask, a[k], p);
     const bool me = (g.wl == p);
-    const cx<R> l = me ? czero<R>() : a[k] * crecip(pk);
+    cx<R>* buf = pv + (k & 1) * S;
+    const int j0 = k & ~1;  // first stored column (k, or k - 1 whose slot is ignored)
     if (me) {
+      if constexpr (sizeof(R) == 4) {
+#pragma unroll
+        for (int j = j0; j < W; j += 2) {
+          const cx<R> v0 = (j == k) ? inv : a[j];
+          const cx<R> v1 = (j + 1 == k) ? inv : (j + 1 < W ? a[j + 1 < W ? j + 1 : 0] : czero<R>());
+          reinterpret_cast<float4*>(buf)[j >> 1] = make_float4(v0.re, v0.im, v1.re, v1.im);
+        }
+      } else {
+#pragma unroll
+        for (int j = k; j < W; ++j) {
+          const cx<R> v = (j == k) ? inv : a[j];
+          reinterpret_cast<double2*>(buf)[j] = make_double2(v.re, v.im);
+        }
+      }
       used = true;
-      diag = a[k];
+      dinv = inv;
       col = k;
     }
+    __syncwarp(g.mask);
+    cx<R> row_p[W];  // the pivot row, columns k .. W-1 (slot k: 1/pivot)
+    if constexpr (sizeof(R) == 4) {
 #pragma unroll
-    for (int j = k + 1; j < N + NR; ++j) {
-      const cx<R> pj = shfl(g.mask, a[j], p);
-      a[j] = cfms(l, pj, a[j]);
+      for (int j = j0; j < W; j += 2) {
+        const float4 q = reinterpret_cast<const float4*>(buf)[j >> 1];
+        row_p[j] = mk<R>(q.x, q.y);
+        if (j + 1 < W) row_p[j + 1 < W ? j + 1 : 0] = mk<R>(q.z, q.w);
+      }
+    } else {
+#pragma unroll
+      for (int j = k; j < W; ++j) {
+        const double2 q = reinterpret_cast<const double2*>(buf)[j];
+        row_p[j] = mk<R>(q.x, q.y);
+      }
     }
-  }
-  const cx<R> id = crecip(diag);
+    const cx<R> l = me ? czero<R>() : a[k] * row_p[k];
 #pragma unroll
-  for (int r = 0; r < NR; ++r) sol[r] = a[N + r] * id;
+    for (int j = k + 1; j < W; ++j) a[j] = cfms(l, row_p[j], a[j]);
+  }
+#pragma unroll
+  for (int r = 0; r < NR; ++r) sol[r] = a[N + r] * dinv;
   return ok;
 }
 

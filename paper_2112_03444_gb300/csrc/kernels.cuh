@@ -10,7 +10,17 @@
 namespace hc {
 
 constexpr int kBlock = 128;  // threads per block of the tracking kernels
-constexpr int kGroupSmemBytesPerLane = 40;  // shared bytes per lane (see tracker.cuh)
+
+// Shared memory of one lane group of L lanes (layout in tracker.cuh):
+// pivot-row buffers 32 (L + 2), FP64 point (L + extra) 16, solution scatter
+// L 16, FP32 point (L + extra) 8, rounded up to 16 bytes.
+__host__ __device__ constexpr int group_smem_bytes(int L, int extra) {
+  return (32 * (L + 2) + (L + extra) * 16 + L * 16 + (L + extra) * 8 + 15) & ~15;
+}
+// Dynamic shared memory of one tracking block
+__host__ __device__ constexpr int block_smem_bytes(int L, int extra) {
+  return (kBlock / L) * group_smem_bytes(L, extra);
+}
 
 // Work distribution of a tracking launch: work item = (instance, path),
 // item = instance * paths + path; a lane group takes the next item with one

@@ -287,8 +287,8 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
   int dev = 0, sms = 0;
   NA_CUDA(cudaGetDevice(&dev));
   NA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const size_t smem = (size_t)hc::kBlock * hc::kGroupSmemBytesPerLane;
   auto launch = [&](const hc::KernelRef& k, const hc::DenseArgs& args, int64_t max_items) {
+    const size_t smem = (size_t)hc::block_smem_bytes(k.lanes, 0);
     int blocks = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k.fn, hc::kBlock, smem) !=
         cudaSuccess)

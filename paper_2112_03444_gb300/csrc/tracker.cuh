@@ -63,31 +63,29 @@ __device__ __forceinline__ void load_vec(const cx<S>* buf, cx<R> (&x)[N]) {
 
 enum : int { M_RK = 0, M_NEWTON = 1, M_REFINE = 2, M_COND = 3, M_DONE = 4, M_FETCH = 5 };
 
-// Shared memory of one lane group: vf = FP32 copy of the evaluation point,
-// vd = FP64 copy (phases with FP64 state), sb = solution scatter buffer.
-// vf and vd hold L + extra entries: the point occupies [0, N) and an
-// evaluator may keep its own per-path values behind index L.
+// Shared memory of one lane group: pv = two pivot-row buffers of the solve,
+// vd = FP64 copy of the evaluation point (phases with FP64 state), sb =
+// solution scatter buffer, vf = FP32 copy of the point.  vf and vd hold
+// L + extra entries: the point occupies [0, N) and an evaluator may keep its
+// own per-path values behind index L.  Size: group_smem_bytes (kernels.cuh).
 struct GroupMem {
+  unsigned char* pv;  // 32 (L + 2) bytes, 16-byte aligned
   cx<double>* vd;
   cx<double>* sb;  // holds L values of cx<R>
   cx<float>* vf;
 };
 
-__host__ __device__ constexpr int group_smem_bytes(int L, int extra) {
-  return (L + extra) * 16 + L * 16 + (L + extra) * 8;
-}
-
 template <int L>
 __device__ __forceinline__ GroupMem make_group_mem(unsigned char* smem, int extra) {
   unsigned char* b = smem + (threadIdx.x / L) * group_smem_bytes(L, extra);
   GroupMem m;
+  m.pv = b;
+  b += 32 * (L + 2);
   m.vd = reinterpret_cast<cx<double>*>(b);
   m.sb = reinterpret_cast<cx<double>*>(b + (L + extra) * 16);
   m.vf = reinterpret_cast<cx<float>*>(b + (L + extra) * 16 + L * 16);
   return m;
 }
-
-
 
 // Persistent loop of one lane group over the work items of a launch.
 // PROB::hom(inst) binds the evaluator to an instance.
@@ -376,7 +374,7 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
         row[N] = -H;
       }
     }
-    const bool sok = gj_solve<N, 1, R>(g, row, sol, col);
+    const bool sok = gj_solve<N, 1, R>(g, row, sol, col, reinterpret_cast<cx<R>*>(sm.pv));
     if (col >= 0) sb[col] = sol[0];
     __syncwarp(g.mask);
     const cx<R> d = act ? sb[g.gl] : czero<R>();
