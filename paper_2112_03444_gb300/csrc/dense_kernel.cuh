@@ -12,8 +12,10 @@ template <int N, int DEG, int L>
 struct DenseProblem {
   const DenseArgs* a;
   GroupMem sm;
+  unsigned gmask;
   __device__ __forceinline__ DenseTD<N, DEG, L> hom(int64_t inst) const {
     DenseTD<N, DEG, L> h;
+    h.gmask = gmask;
     h.D32 = a->D32 ? a->D32 + inst * a->Dstride : nullptr;
     h.D64 = a->D64 ? a->D64 + inst * a->Dstride : nullptr;
     h.E = a->E + inst * a->Estride;
@@ -29,8 +31,8 @@ template <int N, int DEG, bool MIXED, int L>
 __global__ void __launch_bounds__(kBlock, 4) dense_td_kernel(const DenseArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Group g = make_group<L>();
-  const GroupMem sm = make_group_mem<L>(smem, 0);
-  DenseProblem<N, DEG, L> prob{&a, sm};
+  const GroupMem sm = make_group_mem<L>(smem, DenseShape<N, DEG>::EXTRA);
+  DenseProblem<N, DEG, L> prob{&a, sm, g.mask};
   run_tracker<N, L, MIXED>(prob, a.c, g, sm);
 }
 
@@ -38,7 +40,8 @@ __global__ void __launch_bounds__(kBlock, 4) dense_td_kernel(const DenseArgs a) 
 template <int DEG, bool MIXED, int N, int LANES = 0>
 KernelRef dense_ref() {
   constexpr int L = LANES ? LANES : ((N <= 4) ? 4 : (N <= 8) ? 8 : (N <= 16) ? 16 : 32);
-  return KernelRef{reinterpret_cast<const void*>(&dense_td_kernel<N, DEG, MIXED, L>), L};
+  return KernelRef{reinterpret_cast<const void*>(&dense_td_kernel<N, DEG, MIXED, L>), L,
+                   DenseShape<N, DEG>::EXTRA};
 }
 
 }  // namespace hc

@@ -38,6 +38,10 @@ struct DenseShape {
   static constexpr __host__ __device__ int idx2(int k, int l) {
     return 1 + N + k * N - k * (k - 1) / 2 + (l - k);
   }
+  // quadratic monomials x_k x_l (k <= l), formed per evaluation in the
+  // group's shared memory behind the point (cubic systems only)
+  static constexpr int NQ = N * (N + 1) / 2;
+  static constexpr int EXTRA = (DEG == 3) ? NQ : 0;
 };
 
 template <int N, int DEG, int L_GROUP>
@@ -51,13 +55,14 @@ struct DenseTD {
   const cx<double>* E;
   cx<double> gamma;
   cx<float> gamma32;
-  const cx<float>* Vf;   // the group's shared copies of the evaluation point
-  const cx<double>* Vd;
+  cx<float>* Vf;   // the group's shared copies of the evaluation point (+ monomials)
+  cx<double>* Vd;
+  unsigned gmask;  // lanes of the group
 
   template <class R>
   __device__ __forceinline__ const cx<R>* dptr() const;
   template <class R>
-  __device__ __forceinline__ const cx<R>* vptr() const {
+  __device__ __forceinline__ cx<R>* vptr() const {
     if constexpr (std::is_same<R, float>::value)
       return Vf;
     else
@@ -91,16 +96,31 @@ struct DenseTD {
     return (m & 1) ? ((m + 1) * PARTS - 1 - part) : (m * PARTS + part);
   }
 
-  // The contraction index k runs in a loop that is not unrolled (x_k is read
-  // from the group's shared copy of the point); the rows j stay unrolled so
-  // that row[] lives in registers.  Code size O(N) instead of O(N^2) / O(N^3).
+  // The contraction indices run in loops that are not unrolled (x_k and the
+  // quadratic monomials are read from the group's shared memory); the rows j
+  // stay unrolled so that the accumulators live in registers.  The point is
+  // read from shared memory too (x is not needed in registers).
   template <class R>
-  __device__ __forceinline__ void eval(const cx<R> (&x)[N], int i, R t, R omt, cx<R> (&row)[N + 1],
+  __device__ __forceinline__ void eval(const cx<R> (&)[N], int i, R t, R omt, cx<R> (&row)[N + 1],
                                        cx<R>& H, cx<R>& Ht) const {
     const int r = i & (L - 1);                   // this lane's row
     const int part = (PARTS > 1) ? i / L : 0;    // and its share of the contraction
     const cx<R>* D = dptr<R>() + (r < N ? r : 0);
-    const cx<R>* V = vptr<R>();
+    cx<R>* V = vptr<R>();
+    if constexpr (DEG == 3) {
+      // x_k x_l for k <= l in graded order, the group's lanes sharing the work
+      cx<R>* Q = V + L;
+#pragma unroll 1
+      for (int m = i; m < S::NQ; m += L_GROUP) {
+        int k = 0, rem = m;
+        while (rem >= N - k) {
+          rem -= N - k;
+          ++k;
+        }
+        Q[m] = V[k] * V[k + rem];
+      }
+      __syncwarp(gmask);
+    }
     cx<R> a1[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) a1[j] = czero<R>();
@@ -121,37 +141,26 @@ struct DenseTD {
       for (int j = 0; j < N; ++j) {
         const cx<R> a0 = D[(j * S::MP) * L];
         row[j] = a0 + a1[j];
-        F = cfma(x[j], a0 + R(0.5) * a1[j], F);
+        F = cfma(V[j], a0 + R(0.5) * a1[j], F);
       }
     } else {
+      const cx<R>* Q = V + L;
       cx<R> a2[N];
 #pragma unroll
       for (int j = 0; j < N; ++j) a2[j] = czero<R>();
-#pragma unroll 1
-      for (int m = 0;; ++m) {
-        const int k = zigzag(m, part);
-        if (k >= N) break;
-        cx<R> in[N];
+#pragma unroll 2
+      for (int m = part; m < S::NQ; m += PARTS) {
+        const cx<R> mu = Q[m];
+        const cx<R>* Dm = D + (1 + N + m) * L;
 #pragma unroll
-        for (int j = 0; j < N; ++j) in[j] = czero<R>();
-        const int base = S::idx2(k, k);
-#pragma unroll 1
-        for (int l = k; l < N; ++l) {
-          const cx<R> xl = V[l];
-          const cx<R>* Dl = D + (base + (l - k)) * L;
-#pragma unroll
-          for (int j = 0; j < N; ++j) in[j] = cfma(Dl[j * S::MP * L], xl, in[j]);
-        }
-        const cx<R> xk = V[k];
-#pragma unroll
-        for (int j = 0; j < N; ++j) a2[j] = cfma(xk, in[j], a2[j]);
+        for (int j = 0; j < N; ++j) a2[j] = cfma(Dm[j * S::MP * L], mu, a2[j]);
       }
       if constexpr (PARTS > 1) {
         // partial rows and the partial Euler sum, then one reduction each
         cx<R> fp = czero<R>();
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-          fp = cfma(x[j], R(0.5) * a1[j] + R(1.0 / 3.0) * a2[j], fp);
+          fp = cfma(V[j], R(0.5) * a1[j] + R(1.0 / 3.0) * a2[j], fp);
           a1[j] = part_sum(a1[j] + a2[j]);
         }
         F = F + part_sum(fp);
@@ -159,21 +168,18 @@ struct DenseTD {
         for (int j = 0; j < N; ++j) {
           const cx<R> a0 = D[(j * S::MP) * L];
           row[j] = a0 + a1[j];
-          F = cfma(x[j], a0, F);
+          F = cfma(V[j], a0, F);
         }
       } else {
 #pragma unroll
         for (int j = 0; j < N; ++j) {
           const cx<R> a0 = D[(j * S::MP) * L];
           row[j] = a0 + a1[j] + a2[j];
-          F = cfma(x[j], a0 + R(0.5) * a1[j] + R(1.0 / 3.0) * a2[j], F);
+          F = cfma(V[j], a0 + R(0.5) * a1[j] + R(1.0 / 3.0) * a2[j], F);
         }
       }
     }
-    cx<R> xi = x[0];
-#pragma unroll
-    for (int k = 1; k < N; ++k)
-      if (k == r) xi = x[k];
+    const cx<R> xi = V[r < N ? r : 0];
     // G_i = xi^d - 1, dG_i/dx_i = d xi^(d-1)
     const cx<R> xi2 = xi * xi;
     const cx<R> G = (DEG == 2 ? xi2 : xi2 * xi) - mk<R>(R(1), R(0));

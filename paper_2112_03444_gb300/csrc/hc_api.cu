@@ -583,7 +583,7 @@ hc_status launch_generic(const hc::KernelRef& k, void* args, size_t smem, int64_
 
 hc_status launch_tracker(const hc::KernelRef& k, const hc::DenseArgs& a, int64_t max_items,
                          cudaStream_t st) {
-  const size_t smem = (size_t)hc::block_smem_bytes(k.lanes, 0);
+  const size_t smem = (size_t)hc::block_smem_bytes(k.lanes, k.extra);
   const Occ o = occupancy(k.fn, smem);
   const int64_t groups_per_block = hc::kBlock / k.lanes;
   int64_t want = (max_items + groups_per_block - 1) / groups_per_block;

@@ -154,14 +154,21 @@ __device__ __forceinline__ bool gj_solve(const Group& g, cx<R> (&a)[N + NR], cx<
   cx<R> dinv = mk<R>(R(1), R(0));  // 1 / pivot of this lane's row
   col = -1;
   bool ok = true;
-#pragma unroll
-  for (int k = 0; k < N; ++k) {
-    // Every lane forms 1 / a[k] of its own row while the reduction picks the
-    // pivot (the reciprocal stays off the critical path).
-    const cx<R> inv = crecip(a[k]);
+  // Pivot search of column k: every lane forms 1 / a[k] of its own row while
+  // the reduction picks the pivot (the reciprocal stays off the critical
+  // path).  The search of column k + 1 starts as soon as column k + 1 is
+  // updated, so that its reduction overlaps the rest of step k's update.
+  auto search = [&](int k, cx<R>& inv, unsigned& kmax) {
+    inv = crecip(a[k]);
     const float m = (float)cabs1(a[k]);
     const unsigned key = used ? 0u : ((__float_as_uint(m) & ~31u) | (unsigned)(31 - g.wl));
-    const unsigned kmax = __reduce_max_sync(g.mask, key);
+    kmax = __reduce_max_sync(g.mask, key);
+  };
+  cx<R> inv;
+  unsigned kmax;
+  search(0, inv, kmax);
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
     const unsigned mbits = kmax & ~31u;
     ok = ok && (mbits != 0u) && (mbits < 0x7f800000u);
     const int p = 31 - (int)(kmax & 31u);
@@ -204,8 +211,10 @@ __device__ __forceinline__ bool gj_solve(const Group& g, cx<R> (&a)[N + NR], cx<
       }
     }
     const cx<R> l = me ? czero<R>() : a[k] * row_p[k];
+    a[k + 1] = cfms(l, row_p[k + 1], a[k + 1]);
+    if (k + 1 < N) search(k + 1 < N ? k + 1 : 0, inv, kmax);
 #pragma unroll
-    for (int j = k + 1; j < W; ++j) a[j] = cfms(l, row_p[j], a[j]);
+    for (int j = k + 2; j < W; ++j) a[j] = cfms(l, row_p[j], a[j]);
   }
 #pragma unroll
   for (int r = 0; r < NR; ++r) sol[r] = a[N + r] * dinv;

@@ -88,6 +88,7 @@ struct TermArgs {
 struct KernelRef {
   const void* fn;   // __global__ function
   int lanes;        // lanes per path (L)
+  int extra;        // per-group shared entries behind the point the kernel itself needs
 };
 
 // Lanes per path chosen for n unknowns (one row per lane, groups are powers
