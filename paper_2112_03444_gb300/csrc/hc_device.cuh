@@ -12,8 +12,10 @@
 
 namespace hc {
 
+// Aligned to its size so that one complex number moves in one 64-bit (FP32)
+// or 128-bit (FP64) load or store.
 template <class R>
-struct cx {
+struct __align__(2 * sizeof(R)) cx {
   R re, im;
 };
 

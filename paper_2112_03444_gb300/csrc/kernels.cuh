@@ -13,9 +13,11 @@ constexpr int kBlock = 128;  // threads per block of the tracking kernels
 
 // Shared memory of one lane group of L lanes (layout in tracker.cuh):
 // pivot-row buffers 32 (L + 2), FP64 point (L + extra) 16, solution scatter
-// L 16, FP32 point (L + extra) 8, rounded up to 16 bytes.
+// L 16, FP32 point (L + extra) 8.  The stride between groups is 16 bytes
+// past a multiple of 128: the groups of a warp reading their own broadcast
+// word (a point entry, a monomial, the pivot row) then hit different banks.
 __host__ __device__ constexpr int group_smem_bytes(int L, int extra) {
-  return (32 * (L + 2) + (L + extra) * 16 + L * 16 + (L + extra) * 8 + 15) & ~15;
+  return ((32 * (L + 2) + (L + extra) * 16 + L * 16 + (L + extra) * 8 + 127) & ~127) + 16;
 }
 // Dynamic shared memory of one tracking block
 __host__ __device__ constexpr int block_smem_bytes(int L, int extra) {
