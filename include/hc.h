@@ -119,6 +119,12 @@ typedef struct hc_settings {
   int32_t escalate;       /* 1: mixed-precision paths that fail are re-tracked in FP64 */
   int32_t lanes;          /* mixed precision: 0 = default group width (next power of two
                              >= n, at least 4), 32 = one path per warp (n <= 16)   */
+  int32_t max_newton_ir;  /* mixed precision: corrector iterations allowed in the
+                             FP64-residual mode, 6.  Its iterations solve with the
+                             FP32 Jacobian and contract only linearly (about
+                             cond * 6e-8 per iteration), so one exact Newton step
+                             is worth about two of them                         */
+  int32_t reserved;       /* 0 */
 } hc_settings;
 
 /*

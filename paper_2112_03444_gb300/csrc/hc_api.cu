@@ -324,6 +324,7 @@ hc::DevSettings dev_settings(const hc_settings& s) {
   d.dt_min_fp32 = s.dt_min_fp32;
   d.max_first_corr_fp32 = s.max_first_corr_fp32;
   d.max_steps_fp32 = s.max_steps_fp32;
+  d.max_newton_ir = s.max_newton_ir;
   d.max_newton = s.max_newton;
   d.max_steps = s.max_steps;
   d.grow_after = s.grow_after;
@@ -338,7 +339,8 @@ hc_status validate_settings(const hc_settings& s) {
       !(s.newton_tol_fp32 > 0) || !(s.max_first_corr > 0) || !(s.r_inf > 0) ||
       !(s.dt_min_fp32 >= s.dt_min) || !(s.max_first_corr_fp32 > 0) || s.max_steps_fp32 < 1 ||
       (s.precision != HC_PREC_FP64 && s.precision != HC_PREC_MIXED) ||
-      (s.lanes != 0 && s.lanes != 32)) {
+      (s.lanes != 0 && s.lanes != 32) || s.max_newton_ir < 1 || s.max_newton_ir > 32 ||
+      s.reserved != 0) {
     set_err("invalid settings");
     return HC_ERR_INVALID;
   }
@@ -648,6 +650,8 @@ hc_settings hc_default_settings(void) {
   s.precision = HC_PREC_MIXED;
   s.escalate = 1;
   s.lanes = 0;
+  s.max_newton_ir = 6;
+  s.reserved = 0;
   return s;
 }
 

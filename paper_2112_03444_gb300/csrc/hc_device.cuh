@@ -228,7 +228,7 @@ struct DevSettings {
   double dt_min, dt_max, dt_init, newton_tol, newton_tol_fp32, max_first_corr;
   double refine_tol, r_inf, finite_tol, real_tol, singular_cond, t_endgame;
   double dt_min_fp32, max_first_corr_fp32;
-  int max_newton, max_steps, grow_after, refine_iters, max_steps_fp32;
+  int max_newton, max_steps, grow_after, refine_iters, max_steps_fp32, max_newton_ir;
 };
 
 enum : int {

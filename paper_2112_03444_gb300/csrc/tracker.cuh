@@ -26,7 +26,9 @@
 //     iterations are complex FP32 and no FP64 instruction executes; for
 //     t > t_endgame the state is FP64 and the corrector's residual H is
 //     evaluated in FP64 while the Jacobian and the solve stay FP32 (mixed
-//     precision iterative refinement, converged to the FP64 tolerance); the
+//     precision iterative refinement, converged to the FP64 tolerance within
+//     max_newton_ir iterations: each contracts only linearly, by about
+//     cond * 6e-8, so one exact Newton step is worth about two); the
 //     final refinement and the backward error use FP64 residuals the same way.
 //     A path whose FP32 steps fall below dt_min_fp32 (the corrector stalls
 //     at the FP32 noise floor near an ill-conditioned stretch) or exhaust
@@ -436,7 +438,7 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
           if (!HI() && tf >= tAf) promote((double)dtf);  // enter the FP64-state phase
           begin_step();
         }
-      } else if (bad || ++it >= s.max_newton) {
+      } else if (bad || ++it >= ((MIXED && HI()) ? s.max_newton_ir : s.max_newton)) {
         reject();
       }
     } else if (mode == M_REFINE) {

@@ -46,7 +46,8 @@ class hc_settings(ctypes.Structure):
                 ("max_steps_fp32", ctypes.c_int32), ("max_newton", ctypes.c_int32), ("max_steps", ctypes.c_int32),
                 ("grow_after", ctypes.c_int32), ("refine_iters", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("escalate", ctypes.c_int32),
-                ("lanes", ctypes.c_int32)]
+                ("lanes", ctypes.c_int32), ("max_newton_ir", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -34,8 +34,8 @@ def test_every_declared_symbol_is_exported(hc):
 
 
 def test_struct_layouts_match_header_sizes(hc):
-    # hc_settings: 14 doubles + 8 int32 = 144 bytes
-    assert ctypes.sizeof(hc.hc_settings) == 144
+    # hc_settings: 14 doubles + 10 int32 = 152 bytes
+    assert ctypes.sizeof(hc.hc_settings) == 152
     assert ctypes.sizeof(hc.hc_batch_result) == 16 * 8
 
 
