@@ -204,7 +204,7 @@ struct hc_problem {
   double* d_coef = nullptr;  // default coefficients [T][2]
   // parameter homotopy (homogenised term tuples)
   bool terms = false;
-  int kcnt[hc::kMaxTermEntries] = {}, koff[hc::kMaxTermEntries] = {}, kdeg[hc::kMaxTermEntries] = {};
+  int TT = 0;  // term slots per row
   int extra = 0;
   hc::TermRec* d_rec = nullptr;
   double2* d_s64 = nullptr;
@@ -445,78 +445,67 @@ bool encode_terms(hc_problem* p, std::vector<hc::TermRec>& rec, std::vector<doub
   const int n = p->n, P = p->P, L = hc::lanes_for(n);
   const int one = L, pbase = L + 1, dbase = L + 1 + P;
   if (p->kind != HC_PARAMETER || n + 2 > hc::kMaxTermEntries || dbase + P > 255) return false;
-  struct Tup {
+  // per row: its terms as (coefficient, factors, targets)
+  struct Term {
     double re, im;
-    std::vector<int> f;
+    std::vector<int> f, tg;
   };
-  std::vector<std::vector<std::vector<Tup>>> tab(n + 2, std::vector<std::vector<Tup>>(n));
+  std::vector<std::vector<Term>> rows(n);
   for (int k = 0; k < p->T; ++k) {
-    const int i = p->eq[k];
-    const double sr = p->coef[2 * k], si = p->coef[2 * k + 1];
-    std::vector<int> xf, pf;
+    Term t;
+    t.re = p->coef[2 * k];
+    t.im = p->coef[2 * k + 1];
     for (int j = 0; j < n; ++j)
-      for (int a = 0; a < p->exps[(size_t)k * n + j]; ++a) xf.push_back(j);
+      for (int a = 0; a < p->exps[(size_t)k * n + j]; ++a) {
+        t.f.push_back(j);
+        t.tg.push_back(j);
+      }
     for (int f = 0; f < p->maxpf; ++f) {
       const int l = p->par[(size_t)k * p->maxpf + f];
-      if (l >= 0) pf.push_back(l);
-    }
-    auto add = [&](int e, double mult, std::vector<int> f) {
-      if (f.empty()) f.push_back(one);
-      tab[e][i].push_back(Tup{sr * mult, si * mult, std::move(f)});
-    };
-    {  // H
-      std::vector<int> f = xf;
-      for (int l : pf) f.push_back(pbase + l);
-      add(n + 1, 1.0, f);
-    }
-    for (int j = 0; j < n; ++j) {  // dH/dx_j
-      const int a = p->exps[(size_t)k * n + j];
-      if (a == 0) continue;
-      std::vector<int> f;
-      bool dropped = false;
-      for (int v : xf) {
-        if (v == j && !dropped) {
-          dropped = true;
-          continue;
-        }
-        f.push_back(v);
+      if (l >= 0) {
+        t.f.push_back(pbase + l);
+        t.tg.push_back(n);
       }
-      for (int l : pf) f.push_back(pbase + l);
-      add(j, (double)a, f);
     }
-    for (size_t q = 0; q < pf.size(); ++q) {  // dH/dt
-      std::vector<int> f = xf;
-      for (size_t r = 0; r < pf.size(); ++r) f.push_back((r == q ? dbase : pbase) + pf[r]);
-      add(n, 1.0, f);
+    if (t.f.empty()) {  // a constant term: the factor 1, no derivative
+      t.f.push_back(one);
+      t.tg.push_back(255);
     }
+    if ((int)t.f.size() > hc::kMaxTermFactors) return false;
+    rows[p->eq[k]].push_back(std::move(t));
   }
-  int off = 0;
-  for (int e = 0; e < n + 2; ++e) {
-    int K = 0, D = 1;
-    for (int i = 0; i < n; ++i) {
-      K = std::max(K, (int)tab[e][i].size());
-      for (auto& t : tab[e][i]) D = std::max(D, (int)t.f.size());
-    }
-    if (D > hc::kMaxTermFactors) return false;
-    p->kcnt[e] = K;
-    p->koff[e] = off;
-    p->kdeg[e] = D;
-    off += K;
+  // slots: every row's terms by decreasing factor count, rows padded to the
+  // longest; at each slot the factor count is the largest over the rows
+  int TT = 0;
+  for (auto& r : rows) {
+    std::stable_sort(r.begin(), r.end(),
+                     [](const Term& x, const Term& y) { return x.f.size() > y.f.size(); });
+    TT = std::max(TT, (int)r.size());
   }
-  rec.assign((size_t)off * L, hc::TermRec{});
-  s64.assign((size_t)off * L, make_double2(0.0, 0.0));
-  for (auto& r : rec)
-    for (int f = 0; f < hc::kMaxTermFactors; ++f) r.idx[f] = (uint8_t)one;
-  for (int e = 0; e < n + 2; ++e)
+  rec.assign((size_t)TT * L, hc::TermRec{});
+  s64.assign((size_t)TT * L, make_double2(0.0, 0.0));
+  for (int k = 0; k < TT; ++k) {
+    int d = 1;
     for (int i = 0; i < n; ++i)
-      for (size_t k = 0; k < tab[e][i].size(); ++k) {
-        const Tup& t = tab[e][i][k];
-        const size_t r = ((size_t)p->koff[e] + k) * L + i;
-        rec[r].s = make_float2((float)t.re, (float)t.im);
-        for (size_t f = 0; f < t.f.size() && f < (size_t)hc::kMaxTermFactors; ++f)
-          rec[r].idx[f] = (uint8_t)t.f[f];
-        s64[r] = make_double2(t.re, t.im);
+      if (k < (int)rows[i].size()) d = std::max(d, (int)rows[i][k].f.size());
+    for (int i = 0; i < L; ++i) {
+      hc::TermRec& r = rec[(size_t)k * L + i];
+      for (int f = 0; f < hc::kMaxTermFactors; ++f) {
+        r.idx[f] = (uint8_t)one;
+        r.tgt[f] = 255;
       }
+      r.d = (uint8_t)d;
+      if (i >= n || k >= (int)rows[i].size()) continue;  // zero coefficient
+      const Term& t = rows[i][k];
+      r.s = make_float2((float)t.re, (float)t.im);
+      for (size_t f = 0; f < t.f.size(); ++f) {
+        r.idx[f] = (uint8_t)t.f[f];
+        r.tgt[f] = (uint8_t)t.tg[f];
+      }
+      s64[(size_t)k * L + i] = make_double2(t.re, t.im);
+    }
+  }
+  p->TT = TT;
   p->terms = true;
   p->L = L;
   p->extra = 1 + 3 * P;
@@ -954,11 +943,7 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
     ta.c = cm;
     ta.rec = p->d_rec;
     ta.s64 = p->d_s64;
-    for (int e = 0; e < hc::kMaxTermEntries; ++e) {
-      ta.kcnt[e] = p->kcnt[e];
-      ta.koff[e] = p->koff[e];
-      ta.kdeg[e] = p->kdeg[e];
-    }
+    ta.TT = p->TT;
     ta.P = p->P;
     ta.ls = p->L;
     ta.extra = p->extra;
@@ -966,20 +951,22 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
     ta.p1 = B.d_p1;
     ta.start = p->d_start;
     const hc::KernelRef k = hc::term_kernel(n, mixed, mixed ? p->s.lanes : 0);
-    auto smem_of = [&](int L) { return (size_t)hc::block_smem_bytes(L, p->extra); };
+    auto smem_of = [&](const hc::KernelRef& kr) {
+      return (size_t)hc::block_smem_bytes(kr.lanes, p->extra, kr.acc_bytes);
+    };
     HC_CUDA(mark(ev.ek0, st));
-    if ((rc = launch_generic(k, &ta, smem_of(k.lanes), items, st)) != HC_OK) return rc;
+    if ((rc = launch_generic(k, &ta, smem_of(k), items, st)) != HC_OK) return rc;
     HC_CUDA(mark(ev.ek1, st));
     if (escalate) {
       if (ev.capture) HC_CUDA(cudaEventRecord(ev.fork, st));
       if ((rc = dedupe()) != HC_OK) return rc;
       hc::TermArgs td = ta;
       td.c = cd;
-      if ((rc = launch_generic(k, &td, smem_of(k.lanes), esc_groups, hs)) != HC_OK) return rc;
+      if ((rc = launch_generic(k, &td, smem_of(k), esc_groups, hs)) != HC_OK) return rc;
       hc::TermArgs te = ta;
       te.c = ce;
       const hc::KernelRef k64 = hc::term_kernel(n, false, 0);
-      if ((rc = launch_generic(k64, &te, smem_of(k64.lanes), esc_groups, hs)) != HC_OK) return rc;
+      if ((rc = launch_generic(k64, &te, smem_of(k64), esc_groups, hs)) != HC_OK) return rc;
       HC_CUDA(mark(ev.ek2, hs));
       if (ev.capture) HC_CUDA(cudaEventRecord(ev.join, hs));
       HC_CUDA(cudaStreamWaitEvent(st, ev.capture ? ev.join : ev.ek2, 0));

@@ -12,16 +12,17 @@ namespace hc {
 constexpr int kBlock = 128;  // threads per block of the tracking kernels
 
 // Shared memory of one lane group of L lanes (layout in tracker.cuh):
-// pivot-row buffers 32 (L + 2), FP64 point (L + extra) 16, solution scatter
-// L 16, FP32 point (L + extra) 8.  The stride between groups is 16 bytes
-// past a multiple of 128: the groups of a warp reading their own broadcast
-// word (a point entry, a monomial, the pivot row) then hit different banks.
-__host__ __device__ constexpr int group_smem_bytes(int L, int extra) {
-  return ((32 * (L + 2) + (L + extra) * 16 + L * 16 + (L + extra) * 8 + 127) & ~127) + 16;
+// pivot-row buffers 32 (L + 2), evaluator accumulators acc bytes, FP64
+// point (L + extra) 16, solution scatter L 16, FP32 point (L + extra) 8.
+// The stride between groups is 16 bytes past a multiple of 128: the groups
+// of a warp reading their own broadcast word (a point entry, a monomial,
+// the pivot row) then hit different banks.
+__host__ __device__ constexpr int group_smem_bytes(int L, int extra, int acc = 0) {
+  return ((32 * (L + 2) + acc + (L + extra) * 16 + L * 16 + (L + extra) * 8 + 127) & ~127) + 16;
 }
 // Dynamic shared memory of one tracking block
-__host__ __device__ constexpr int block_smem_bytes(int L, int extra) {
-  return (kBlock / L) * group_smem_bytes(L, extra);
+__host__ __device__ constexpr int block_smem_bytes(int L, int extra, int acc = 0) {
+  return (kBlock / L) * group_smem_bytes(L, extra, acc);
 }
 
 // Work distribution of a tracking launch: work item = (instance, path),
@@ -65,22 +66,31 @@ struct DenseArgs {
   cx<float> gamma32;         // FP32 copy (FP32 evaluations convert nothing)
 };
 
-// One homogenised term tuple: scalar (FP32 copy) and up to 8 factor indices
-// into the per-path vector V (see term_param.cuh).
-struct TermRec {
-  float2 s;
-  uint8_t idx[8];
-};
-constexpr int kMaxTermEntries = 34;  // N + 2 entries per row, N <= 32
+// One term of an equation (paper Sec. 6: a coefficient times a product of
+// factors taken from the per-path vector V, see term_param.cuh).  d is the
+// number of factors evaluated for this term slot: the same for every row at
+// a slot (rows with fewer factors are padded with the constant 1), so the
+// lanes of a warp run the same loop.  tgt[f] names the entry of row i that
+// the derivative with respect to factor f contributes to: x_j -> j, a
+// parameter -> N (dH/dt, multiplied by dp), 255 -> none (the padding 1).
 constexpr int kMaxTermFactors = 8;
+struct TermRec {
+  float2 s;                        // coefficient (FP32 copy)
+  uint8_t idx[kMaxTermFactors];    // factor positions in V
+  uint8_t tgt[kMaxTermFactors];
+  uint8_t d;
+  uint8_t pad[7];
+};
+static_assert(sizeof(TermRec) == 32, "term record layout");
+constexpr int kMaxTermEntries = 34;  // N + 2 entries per row, N <= 32
 
 struct TermArgs {
   LaunchCommon c;
-  const TermRec* rec;    // [sum_e K_e][L]
-  const double2* s64;    // FP64 scalars, same layout
-  int kcnt[kMaxTermEntries], koff[kMaxTermEntries], kdeg[kMaxTermEntries];
+  const TermRec* rec;    // [TT][ls]: term slot k of row i at k * ls + i
+  const double2* s64;    // FP64 coefficients, same layout
+  int TT;                // term slots per row (rows padded with zero terms)
   int P;                 // number of parameters
-  int ls;                // lane stride of the tuple tables (and V's offset of the 1)
+  int ls;                // lane stride of the tables (and V's offset of the 1)
   int extra;             // shared-memory entries behind the point: 1 + 3P
   const double2* p0;     // [P]
   const double2* p1;     // [instances][P]
@@ -91,6 +101,7 @@ struct KernelRef {
   const void* fn;   // __global__ function
   int lanes;        // lanes per path (L)
   int extra;        // per-group shared entries behind the point the kernel itself needs
+  int acc_bytes;    // bytes of one evaluator accumulator (per lane and row entry), 0: none
 };
 
 // Lanes per path chosen for n unknowns (one row per lane, groups are powers

@@ -1,20 +1,27 @@
 // Parameter homotopy H(x, t) = F(x; p(t)), p(t) = (1-t) p0 + t p1, evaluated
-// from homogenised term tuples (paper Sec. 6).
+// from the terms of the equations (paper Sec. 6).
 //
-// Every entry of row i -- dH_i/dx_j (j < N), dH_i/dt and H_i -- is a sum of
-// K_e tuples (s, m_1, ..., m_D): s * V[m_1] * ... * V[m_D], where V is the
-// per-path vector
+// Every term of equation i is a coefficient times a product of factors
+// taken from the per-path vector
 //   V = [ x_0 .. x_{N-1} | pad to L | 1 | p(t)_0 .. p(t)_{P-1} | dp_0 .. dp_{P-1} | p0 ]
 // (dp = p1 - p0 = dp/dt; p0 is kept so that FP32 evaluations form p(t) =
-// p0 + t dp without FP64 arithmetic).  As in the paper, every entry is padded to the same
-// number of tuples K_e for all rows, and here also to the same number of
-// factors D_e (padding factors point at the constant 1), so that the lanes of
-// a path -- one row each -- run the same loop.  The library derives the
-// tuples symbolically from the term list: x-derivatives by the power rule,
-// the t-derivative by the product rule over the parameter factors.
+// p0 + t dp without FP64 arithmetic); a power x_j^a is a repeated factor.
+// Lane i evaluates row i: for each term it forms the prefix products of the
+// factors, then walks them backwards with the suffix product, so that one
+// pass yields the term itself (its contribution to H_i) and its derivative
+// with respect to every factor (product rule; a repeated factor contributes
+// once per occurrence, which is the power rule).  A derivative with respect
+// to x_j adds to dH_i/dx_j, one with respect to a parameter adds, times
+// dp, to dH_i/dt.  Those targets differ from term to term, so each lane
+// accumulates its row in its own slice of shared memory and reads the row
+// back at the end.  The paper's homogenised tuples enumerate every entry of
+// the Jacobian row as separate factor products; this form shares the
+// products between all entries of a term.
 //
-// V lives in the lane group's shared memory behind the point written by the
-// tracker: FP32 copy for the FP32 tier, FP64 copy for FP64 evaluations.
+// The term tables are padded per row to the same number of term slots and,
+// at each slot, to the same number of factors (padding factor: the 1), so
+// that the lanes of a path -- one row each -- and the paths of a warp run
+// the same loop.
 #pragma once
 
 #include "kernels.cuh"
@@ -32,6 +39,7 @@ struct TermEval {
   Group g;
   cx<float>* Vf;
   cx<double>* Vd;
+  unsigned char* acc;  // [N + 2][L] accumulators of cx<R>, this lane at column g.gl
 
   // constant part of V for this path: the 1, dp and (FP32) p0
   __device__ __forceinline__ void init(const Group&) const {
@@ -80,25 +88,32 @@ struct TermEval {
     __syncwarp(g.mask);
   }
 
-  template <class R>
-  __device__ __forceinline__ cx<R> entry(int e, int i, const cx<R>* V) const {
-    const int K = a->kcnt[e], D = a->kdeg[e], base = a->koff[e];
-    cx<R> acc = czero<R>();
-#pragma unroll 1
-    for (int k = 0; k < K; ++k) {
-      const int64_t r = (int64_t)(base + k) * a->ls + i;
-      const TermRec rc = a->rec[r];
-      cx<R> prod = V[rc.idx[0]];
-#pragma unroll 1
-      for (int f = 1; f < D; ++f) prod = prod * V[rc.idx[f]];
-      cx<R> s;
-      if constexpr (std::is_same<R, float>::value)
-        s = mk<float>(rc.s.x, rc.s.y);
-      else
-        s = mk<double>(a->s64[r].x, a->s64[r].y);
-      acc = cfma(s, prod, acc);
+  // One term of D factors: add its value to h and its derivatives to the
+  // lane's accumulators (the coefficient rides in the suffix product).
+  template <int D, class R>
+  __device__ __forceinline__ void term(const TermRec& rc, cx<R> s, const cx<R>* V, cx<R>* A,
+                                       cx<R>& h) const {
+    cx<R> pre[D];
+    cx<R> run = mk<R>(R(1), R(0));
+#pragma unroll
+    for (int f = 0; f < D; ++f) {
+      pre[f] = run;
+      run = run * V[rc.idx[f]];
     }
-    return acc;
+    h = cfma(s, run, h);
+    cx<R> suf = s;
+#pragma unroll
+    for (int f = D - 1; f >= 0; --f) {
+      const int tg = rc.tgt[f];
+      const cx<R> v = V[rc.idx[f]];
+      const cx<R> dv = pre[f] * suf;
+      if (tg < N) {
+        A[tg * L] = A[tg * L] + dv;
+      } else if (tg == N) {  // a parameter factor: d/dt through dp
+        A[N * L] = cfma(dv, V[rc.idx[f] + a->P], A[N * L]);
+      }
+      if (f > 0) suf = suf * v;
+    }
   }
 
   template <class R>
@@ -107,32 +122,56 @@ struct TermEval {
     put_params<R>(t);
     const cx<R>* V = vptr<R>();
     const int ii = i < N ? i : 0;
+    cx<R>* A = reinterpret_cast<cx<R>*>(acc) + g.gl;
 #pragma unroll
-    for (int j = 0; j < N; ++j) row[j] = entry<R>(j, ii, V);
-    Ht = entry<R>(N, ii, V);
-    H = entry<R>(N + 1, ii, V);
+    for (int e = 0; e <= N; ++e) A[e * L] = czero<R>();
+    cx<R> h = czero<R>();
+#pragma unroll 1
+    for (int k = 0; k < a->TT; ++k) {
+      const int64_t r = (int64_t)k * a->ls + ii;
+      const TermRec rc = a->rec[r];
+      cx<R> s;
+      if constexpr (std::is_same<R, float>::value)
+        s = mk<float>(rc.s.x, rc.s.y);
+      else
+        s = mk<double>(a->s64[r].x, a->s64[r].y);
+      switch (rc.d) {  // the same at a slot for every row and path: no divergence
+        case 1: term<1, R>(rc, s, V, A, h); break;
+        case 2: term<2, R>(rc, s, V, A, h); break;
+        case 3: term<3, R>(rc, s, V, A, h); break;
+        case 4: term<4, R>(rc, s, V, A, h); break;
+        case 5: term<5, R>(rc, s, V, A, h); break;
+        case 6: term<6, R>(rc, s, V, A, h); break;
+        case 7: term<7, R>(rc, s, V, A, h); break;
+        case 8: term<8, R>(rc, s, V, A, h); break;
+        default: break;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j) row[j] = A[j * L];
+    Ht = A[N * L];
+    H = h;
   }
 
   template <bool SCALE>
   __device__ __forceinline__ void residual64(const cx<double>*, int i, double t, double,
                                              cx<double>& H, double& sc) const {
     put_params<double>(t);
-    const int e = N + 1, K = a->kcnt[e], D = a->kdeg[e], base = a->koff[e];
     const int ii = i < N ? i : 0;
-    cx<double> acc = czero<double>();
+    cx<double> h = czero<double>();
     float s_abs = 0.f;
 #pragma unroll 1
-    for (int k = 0; k < K; ++k) {
-      const int64_t r = (int64_t)(base + k) * a->ls + ii;
+    for (int k = 0; k < a->TT; ++k) {
+      const int64_t r = (int64_t)k * a->ls + ii;
       const TermRec rc = a->rec[r];
       cx<double> prod = Vd[rc.idx[0]];
 #pragma unroll 1
-      for (int f = 1; f < D; ++f) prod = prod * Vd[rc.idx[f]];
+      for (int f = 1; f < rc.d; ++f) prod = prod * Vd[rc.idx[f]];
       const cx<double> s = mk<double>(a->s64[r].x, a->s64[r].y);
-      acc = cfma(s, prod, acc);
+      h = cfma(s, prod, h);
       if (SCALE) s_abs += cabs2(cvt<float>(s)) * cabs2(cvt<float>(prod));
     }
-    H = acc;
+    H = h;
     sc = SCALE ? (double)s_abs : 0.0;
   }
 };
@@ -143,15 +182,21 @@ struct TermProblem {
   Group g;
   GroupMem sm;
   __device__ __forceinline__ TermEval<N, L> hom(int64_t inst) const {
-    return TermEval<N, L>{a, inst, g, sm.vf, sm.vd};
+    return TermEval<N, L>{a, inst, g, sm.vf, sm.vd, sm.acc};
   }
 };
+
+// accumulator bytes of a group: N + 1 entries (row and dH/dt) of L lanes
+template <int N, bool MIXED, int L>
+__host__ __device__ constexpr int term_acc_bytes() {
+  return (N + 1) * L * (MIXED ? 8 : 16);
+}
 
 template <int N, bool MIXED, int L>
 __global__ void __launch_bounds__(kBlock) term_param_kernel(const __grid_constant__ TermArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Group g = make_group<L>();
-  const GroupMem sm = make_group_mem<L>(smem, a.extra);
+  const GroupMem sm = make_group_mem<L>(smem, a.extra, term_acc_bytes<N, MIXED, L>());
   TermProblem<N, L> prob{&a, g, sm};
   run_tracker<N, L, MIXED>(prob, a.c, g, sm);
 }
@@ -159,7 +204,8 @@ __global__ void __launch_bounds__(kBlock) term_param_kernel(const __grid_constan
 template <bool MIXED, int N, int LANES = 0>
 KernelRef term_ref() {
   constexpr int L = LANES ? LANES : ((N <= 4) ? 4 : (N <= 8) ? 8 : (N <= 16) ? 16 : 32);
-  return KernelRef{reinterpret_cast<const void*>(&term_param_kernel<N, MIXED, L>), L};
+  return KernelRef{reinterpret_cast<const void*>(&term_param_kernel<N, MIXED, L>), L, 0,
+                   term_acc_bytes<N, MIXED, L>()};
 }
 
 }  // namespace hc

@@ -66,23 +66,28 @@ __device__ __forceinline__ void load_vec(const cx<S>* buf, cx<R> (&x)[N]) {
 enum : int { M_RK = 0, M_NEWTON = 1, M_REFINE = 2, M_COND = 3, M_DONE = 4, M_FETCH = 5 };
 
 // Shared memory of one lane group: pv = two pivot-row buffers of the solve,
-// vd = FP64 copy of the evaluation point (phases with FP64 state), sb =
-// solution scatter buffer, vf = FP32 copy of the point.  vf and vd hold
-// L + extra entries: the point occupies [0, N) and an evaluator may keep its
-// own per-path values behind index L.  Size: group_smem_bytes (kernels.cuh).
+// acc = evaluator accumulators (term evaluator only), vd = FP64 copy of the
+// evaluation point (phases with FP64 state), sb = solution scatter buffer,
+// vf = FP32 copy of the point.  vf and vd hold L + extra entries: the point
+// occupies [0, N) and an evaluator may keep its own per-path values behind
+// index L.  Size: group_smem_bytes (kernels.cuh).
 struct GroupMem {
-  unsigned char* pv;  // 32 (L + 2) bytes, 16-byte aligned
+  unsigned char* pv;   // 32 (L + 2) bytes, 16-byte aligned
+  unsigned char* acc;  // acc_bytes, 16-byte aligned
   cx<double>* vd;
   cx<double>* sb;  // holds L values of cx<R>
   cx<float>* vf;
 };
 
 template <int L>
-__device__ __forceinline__ GroupMem make_group_mem(unsigned char* smem, int extra) {
-  unsigned char* b = smem + (threadIdx.x / L) * group_smem_bytes(L, extra);
+__device__ __forceinline__ GroupMem make_group_mem(unsigned char* smem, int extra,
+                                                   int acc_bytes = 0) {
+  unsigned char* b = smem + (threadIdx.x / L) * group_smem_bytes(L, extra, acc_bytes);
   GroupMem m;
   m.pv = b;
   b += 32 * (L + 2);
+  m.acc = b;
+  b += acc_bytes;
   m.vd = reinterpret_cast<cx<double>*>(b);
   m.sb = reinterpret_cast<cx<double>*>(b + (L + extra) * 16);
   m.vf = reinterpret_cast<cx<float>*>(b + (L + extra) * 16 + L * 16);

@@ -26,16 +26,44 @@ def hc():
     return mod
 
 
+# Benign changes of the tracker settings: a path whose oracle classification
+# changes under one of them is ill-determined (it passes so close to a
+# singularity that the rounding of any FP64 evaluation order decides it).
+PERTURB = [dict(newton_tol=5e-9), dict(newton_tol=2e-8), dict(dt_init=0.005), dict(dt_init=0.02)]
+
+
+def _ill_determined(ref_problem, start_row, base_class):
+    for s in PERTURB:
+        r = ref_problem.track(start=start_row[None, :], settings=s)
+        if (r["status"][0] & 0x7F) != base_class:
+            return True
+    return False
+
+
 def _check(hc, system, p0, p1s, start, precision):
+    """Exact status counts and bijective endpoint match, on every path whose
+    oracle outcome is stable; a path on which the GPU and the oracle differ
+    must be ill-determined (see PERTURB), at most 1 % of an instance, and a
+    finite GPU endpoint there must still pass the backward-error test."""
     pr = hc.Problem(system, kind=hc.HC_PARAMETER, p0=p0, start=start,
                     settings=dict(precision=precision))
     b = pr.track(n_instances=len(p1s), p1=np.array(p1s)).wait()
     for s, p1 in enumerate(p1s):
-        ref = OracleProblem(system, kind=KIND_PARAMETER, p0=p0, p1=p1).track(start=start)
-        got, want = oracle.status_counts(b.status[s]), oracle.status_counts(ref["status"])
+        refp = OracleProblem(system, kind=KIND_PARAMETER, p0=p0, p1=p1)
+        ref = refp.track(start=start)
+        gc, oc = b.status[s] & 0x7F, ref["status"] & 0x7F
+        keep = np.ones(len(start), bool)
+        for i in np.nonzero(gc != oc)[0]:
+            assert _ill_determined(refp, start[i], oc[i]), (s, int(i), int(gc[i]), int(oc[i]))
+            if gc[i] == oracle.FINITE:
+                assert b.be[s][i] <= 1e-10, (s, int(i), float(b.be[s][i]))
+            keep[i] = False
+        assert (~keep).sum() <= max(1, len(start) // 100), (s, int((~keep).sum()))
+        got = oracle.status_counts(b.status[s][keep])
+        want = oracle.status_counts(ref["status"][keep])
         assert got == want, (s, got, want)
-        fg = (b.status[s] & 0x7F) == oracle.FINITE
-        fo = (ref["status"] & 0x7F) == oracle.FINITE
+        fg = keep & (gc == oracle.FINITE)
+        fo = keep & (oc == oracle.FINITE)
         ok, msg = same_set(b.x[s][fg], ref["x"][fo], TOL)
         assert ok, (s, msg)
     return b
