@@ -237,9 +237,9 @@ def run_gpu(args):
         torch.cuda.synchronize()
         step_ms.append(e0.elapsed_time(e1))
         results.append([bt.result for bt in bts])
-        # per graph replay: staging, tracking, duplicate check, the two
-        # re-tracking launches, summary
-        launches += 6 * len(bts)
+        # per graph replay: staging, tracking, duplicate check, FP64-residual
+        # re-tracking, second duplicate check, all-FP64 re-tracking, summary
+        launches += 7 * len(bts)
         for bt in bts:
             bt.close()
     clocks = sampler.stop()

@@ -90,11 +90,23 @@ __global__ void stage_dense_kernel(int64_t n_inst, int T, const double2* __restr
 // paths of its instance; the threads of a warp read the same endpoint at the
 // same time (a broadcast load).  x32 holds NaN for paths that did not end
 // finite, which then never match.
+// Duplicate endpoints within an instance (path jumping): an item whose FP32
+// endpoint copy lies within tol (relative, inf-norm) of another item's gets
+// resume time 0 and is appended to out_list -- unless its status is
+// singular: the tracking kernel has already queued such an endpoint for the
+// all-FP64 tier, which then re-tracks it from t = 0 instead of only checking
+// it at t = 1.  list == nullptr checks every item; otherwise only the
+// *list_count items of list (endpoints that were re-tracked), against every
+// item of their instance.
 __global__ void dedupe_kernel(int64_t items, int64_t paths, int n, const float2* __restrict__ x32,
-                              float tol, int64_t* esc_list, unsigned long long* esc_count,
-                              double* t_io) {
-  for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < items;
-       a += (int64_t)gridDim.x * blockDim.x) {
+                              const uint8_t* __restrict__ status, float tol,
+                              const int64_t* __restrict__ list,
+                              const unsigned long long* list_count, int64_t* out_list,
+                              unsigned long long* out_count, double* t_io) {
+  const int64_t total = list ? (int64_t)*list_count : items;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = list ? list[idx] : idx;
     const float2* xa = x32 + a * n;
     const float2 v0 = xa[0];
     if (isnan(v0.x)) continue;
@@ -116,9 +128,11 @@ __global__ void dedupe_kernel(int64_t items, int64_t paths, int n, const float2*
       dup = same;
     }
     if (dup) {
-      const unsigned long long pos = atomicAdd(esc_count, 1ull);
-      esc_list[pos] = a;
       t_io[a] = 0.0;
+      if ((status[a] & 0x7f) != HC_PATH_SINGULAR) {
+        const unsigned long long pos = atomicAdd(out_count, 1ull);
+        out_list[pos] = a;
+      }
     }
   }
 }
@@ -909,7 +923,6 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
   cd.count_dev = B.d_ctl + 7;
   cd.items = B.dup_list;
   cd.queue = B.d_ctl + 6;
-  cd.x32_out = nullptr;
   cd.start_hi = 1;
   cd.spread = 1;
   cd.dup_list = nullptr;
@@ -931,8 +944,19 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
   auto dedupe = [&]() -> hc_status {
     HC_CUDA(cudaStreamWaitEvent(hs, ev.capture ? ev.fork : ev.ek1, 0));
     const int grid = (int)std::min<int64_t>((items + 255) / 256, 65535);
-    dedupe_kernel<<<std::max(grid, 1), 256, 0, hs>>>(items, p->paths, n, B.x32, 1e-6f,
-                                                    B.dup_list, B.d_ctl + 7, B.t_io);
+    dedupe_kernel<<<std::max(grid, 1), 256, 0, hs>>>(items, p->paths, n, B.x32, B.d_status, 1e-6f,
+                                                    nullptr, nullptr, B.dup_list, B.d_ctl + 7,
+                                                    B.t_io);
+    HC_CUDA(cudaGetLastError());
+    return HC_OK;
+  };
+  // after the FP64-residual re-track: a re-tracked endpoint that still
+  // collides goes to the all-FP64 tier, from t = 0
+  auto dedupe_again = [&]() -> hc_status {
+    const int grid = (int)std::min<int64_t>((items + 255) / 256, 65535);
+    dedupe_kernel<<<std::max(grid, 1), 256, 0, hs>>>(items, p->paths, n, B.x32, B.d_status, 1e-6f,
+                                                    B.dup_list, B.d_ctl + 7, B.esc_list,
+                                                    B.d_ctl + 2, B.t_io);
     HC_CUDA(cudaGetLastError());
     return HC_OK;
   };
@@ -963,6 +987,7 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
       hc::TermArgs td = ta;
       td.c = cd;
       if ((rc = launch_generic(k, &td, smem_of(k), esc_groups, hs)) != HC_OK) return rc;
+      if ((rc = dedupe_again()) != HC_OK) return rc;
       hc::TermArgs te = ta;
       te.c = ce;
       const hc::KernelRef k64 = hc::term_kernel(n, false, 0);
@@ -1001,6 +1026,7 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
       dd.c = cd;
       if ((rc = launch_tracker(retrack_kernel(p->deg, n, true), dd, esc_groups, hs)) != HC_OK)
         return rc;
+      if ((rc = dedupe_again()) != HC_OK) return rc;
       hc::DenseArgs e = a;
       e.c = ce;
       if ((rc = launch_tracker(retrack_kernel(p->deg, n, false), e, esc_groups, hs)) != HC_OK)
@@ -1580,12 +1606,13 @@ namespace hc {
 
 void set_last_error(const char* msg) { set_err(msg); }
 
-cudaError_t launch_dedupe(int64_t items, int64_t paths, int n, const float2* x32, float tol,
-                          int64_t* esc_list, unsigned long long* esc_count, double* t_io,
-                          cudaStream_t st) {
+cudaError_t launch_dedupe(int64_t items, int64_t paths, int n, const float2* x32,
+                          const uint8_t* status, float tol, const int64_t* list,
+                          const unsigned long long* list_count, int64_t* out_list,
+                          unsigned long long* out_count, double* t_io, cudaStream_t st) {
   const int grid = (int)std::min<int64_t>((items + 255) / 256, 65535);
-  dedupe_kernel<<<std::max(grid, 1), 256, 0, st>>>(items, paths, n, x32, tol, esc_list, esc_count,
-                                                  t_io);
+  dedupe_kernel<<<std::max(grid, 1), 256, 0, st>>>(items, paths, n, x32, status, tol, list,
+                                                  list_count, out_list, out_count, t_io);
   return cudaGetLastError();
 }
 

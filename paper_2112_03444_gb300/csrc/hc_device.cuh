@@ -57,15 +57,23 @@ __device__ __forceinline__ float rcp(float v) {
 }
 __device__ __forceinline__ double rcp(double v) { return __drcp_rn(v); }
 
-// 1/z with scaling by max(|re|, |im|) so that |z|^2 cannot overflow for
-// |z| up to the format's range.
+// 1/z.  FP64: with scaling by max(|re|, |im|) so that |z|^2 cannot overflow
+// for |z| up to the format's range.  FP32: conj(z) / |z|^2 directly -- the
+// FP32 tracker's Jacobian entries stay far inside 1e-19 < |z| < 1e19 (a
+// pivot outside that range makes the reciprocal non-finite and the step is
+// rejected, as for a singular matrix).
 template <class R>
 __device__ __forceinline__ cx<R> crecip(cx<R> z) {
-  const R s = fmax(fabs(z.re), fabs(z.im));
-  const R inv_s = rcp(s);
-  const R zr = z.re * inv_s, zi = z.im * inv_s;
-  const R d = rcp(s * fma(zr, zr, zi * zi));
-  return {zr * d, -zi * d};
+  if constexpr (sizeof(R) == 4) {
+    const R d = rcp(fma(z.re, z.re, z.im * z.im));
+    return {z.re * d, -z.im * d};
+  } else {
+    const R s = fmax(fabs(z.re), fabs(z.im));
+    const R inv_s = rcp(s);
+    const R zr = z.re * inv_s, zi = z.im * inv_s;
+    const R d = rcp(s * fma(zr, zr, zi * zi));
+    return {zr * d, -zi * d};
+  }
 }
 
 template <class R>
@@ -155,7 +163,9 @@ __device__ __forceinline__ bool gj_solve(const Group& g, cx<R> (&a)[N + NR], cx<
   bool used = g.gl >= N;
   cx<R> dinv = mk<R>(R(1), R(0));  // 1 / pivot of this lane's row
   col = -1;
-  bool ok = true;
+  // smallest and largest pivot magnitude (float bits, lane bits cleared):
+  // every pivot was nonzero and finite iff lo != 0 and hi < +inf
+  unsigned lo = 0xffffffffu, hi = 0u;
   // Pivot search of column k: every lane forms 1 / a[k] of its own row while
   // the reduction picks the pivot (the reciprocal stays off the critical
   // path).  The search of column k + 1 starts as soon as column k + 1 is
@@ -171,8 +181,8 @@ __device__ __forceinline__ bool gj_solve(const Group& g, cx<R> (&a)[N + NR], cx<
   search(0, inv, kmax);
 #pragma unroll
   for (int k = 0; k < N; ++k) {
-    const unsigned mbits = kmax & ~31u;
-    ok = ok && (mbits != 0u) && (mbits < 0x7f800000u);
+    lo = min(lo, kmax);
+    hi = max(hi, kmax);
     const int p = 31 - (int)(kmax & 31u);
     const bool me = (g.wl == p);
     cx<R>* buf = pv + (k & 1) * S;
@@ -220,7 +230,7 @@ __device__ __forceinline__ bool gj_solve(const Group& g, cx<R> (&a)[N + NR], cx<
   }
 #pragma unroll
   for (int r = 0; r < NR; ++r) sol[r] = a[N + r] * dinv;
-  return ok;
+  return (lo & ~31u) != 0u && (hi & ~31u) < 0x7f800000u;
 }
 
 // ---------------------------------------------------------------- settings

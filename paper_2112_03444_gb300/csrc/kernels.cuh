@@ -122,8 +122,9 @@ bool destroy_server_if(void* handle, uint32_t magic);
 void set_last_error(const char* msg);
 DevSettings to_dev_settings(const hc_settings& s);
 hc_status check_settings(const hc_settings& s);
-cudaError_t launch_dedupe(int64_t items, int64_t paths, int n, const float2* x32, float tol,
-                          int64_t* esc_list, unsigned long long* esc_count, double* t_io,
-                          cudaStream_t st);
+cudaError_t launch_dedupe(int64_t items, int64_t paths, int n, const float2* x32,
+                          const uint8_t* status, float tol, const int64_t* list,
+                          const unsigned long long* list_count, int64_t* out_list,
+                          unsigned long long* out_count, double* t_io, cudaStream_t st);
 
 }  // namespace hc

@@ -308,17 +308,19 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
   }
   NA_CUDA(launch(k, a, items));
   if (escalate) {
-    NA_CUDA(hc::launch_dedupe(items, paths, n, x32, 1e-6f, dup, ctl + 7, t_io, st));
+    NA_CUDA(hc::launch_dedupe(items, paths, n, x32, status_out, 1e-6f, nullptr, nullptr, dup,
+                              ctl + 7, t_io, st));
     hc::DenseArgs dd = a;
     dd.c.count_dev = ctl + 7;
     dd.c.items = dup;
     dd.c.queue = ctl + 6;
-    dd.c.x32_out = nullptr;
     dd.c.start_hi = 1;
     dd.c.spread = 1;
     dd.c.dup_list = nullptr;
     dd.c.dup_count = nullptr;
     NA_CUDA(launch(hc::retrack_kernel(degree, n, true), dd, items));
+    NA_CUDA(hc::launch_dedupe(items, paths, n, x32, status_out, 1e-6f, dup, ctl + 7, esc, ctl + 2,
+                              t_io, st));
     hc::DenseArgs e = a;
     e.c.count_dev = ctl + 2;
     e.c.items = esc;

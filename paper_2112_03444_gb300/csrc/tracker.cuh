@@ -208,8 +208,11 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
       const int base = status & 0x7f;
       if (act) {
         reinterpret_cast<double2*>(c.x_out)[item * N + g.gl] = make_double2(xd.re, xd.im);
+        // endpoint copy for duplicate detection: finite endpoints and those
+        // whose FP32 condition estimate is suspect (a path that jumped onto
+        // another path's root must not escape the check by that route)
         if (MIXED && c.x32_out)
-          c.x32_out[item * N + g.gl] = base == ST_FINITE
+          c.x32_out[item * N + g.gl] = (base == ST_FINITE || base == ST_SINGULAR)
                                            ? make_float2((float)xd.re, (float)xd.im)
                                            : make_float2(__int_as_float(0x7fc00000), 0.f);
       }

@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 from oracle import KIND_PARAMETER, OracleProblem
-from hcmatch import same_set
+from hcmatch import distinct, match, rel_dist, same_set
 
 pytestmark = pytest.mark.gpu
 
@@ -40,11 +40,18 @@ def _ill_determined(ref_problem, start_row, base_class):
     return False
 
 
-def _check(hc, system, p0, p1s, start, precision):
+def _check(hc, system, p0, p1s, start, precision, sampled=False):
     """Exact status counts and bijective endpoint match, on every path whose
     oracle outcome is stable; a path on which the GPU and the oracle differ
     must be ill-determined (see PERTURB), at most 1 % of an instance, and a
-    finite GPU endpoint there must still pass the backward-error test."""
+    finite GPU endpoint there must still pass the backward-error test.
+
+    sampled: the start set is a sample of the full one.  Duplicate
+    detection then cannot see an FP32-tier path that jumped onto the root of
+    a start outside the sample, so in mixed precision such jumps are
+    accepted -- a finite GPU endpoint that differs from the oracle's endpoint
+    of the same start and matches none of the oracle's roots, at most 1 % of
+    the sample -- and the full-set tests below cover them."""
     pr = hc.Problem(system, kind=hc.HC_PARAMETER, p0=p0, start=start,
                     settings=dict(precision=precision))
     b = pr.track(n_instances=len(p1s), p1=np.array(p1s)).wait()
@@ -64,6 +71,16 @@ def _check(hc, system, p0, p1s, start, precision):
         assert got == want, (s, got, want)
         fg = keep & (gc == oracle.FINITE)
         fo = keep & (oc == oracle.FINITE)
+        if sampled and precision == 1:
+            _, dist = match(b.x[s][fg], ref["x"][fo], TOL)
+            rows = np.nonzero(fg)[0]
+            jumped = rows[dist > TOL]
+            assert len(jumped) <= max(1, len(start) // 100), (s, len(jumped))
+            for i in jumped:
+                assert rel_dist(b.x[s][i], ref["x"][i])[0] > TOL, (s, int(i))
+                assert b.be[s][i] <= 1e-10, (s, int(i))
+            fg[jumped] = False
+            fo[jumped] = False
         ok, msg = same_set(b.x[s][fg], ref["x"][fo], TOL)
         assert ok, (s, msg)
     return b
@@ -117,7 +134,7 @@ def test_trifocal_sampled_starts_match_oracle(hc, precision):
     z = np.load(os.path.join(STARTS, "trifocal_f.npz"))
     sel = np.random.default_rng(7).choice(len(z["start"]), size=192, replace=False)
     p1s = [inputs.trifocal_scene(s)[0] for s in (51, 52)]
-    _check(hc, fam.system, z["p0"], p1s, z["start"][sel], precision)
+    _check(hc, fam.system, z["p0"], p1s, z["start"][sel], precision, sampled=True)
 
 
 def test_trifocal_full_start_set_recovers_true_pose(hc):
@@ -139,3 +156,29 @@ def test_trifocal_full_start_set_recovers_true_pose(hc):
             v[5:9] *= s13
             best = min(best, float(np.min(np.max(np.abs(fin - v), axis=1))))
     assert best < 1e-8, best
+
+
+def test_trifocal_full_start_set_mixed_matches_fp64(hc):
+    """All 5344 start roots to one noisy scene: the mixed-precision pipeline
+    (with duplicate detection over the full set) finds the same distinct
+    finite roots as the plain FP64 kernel, whose sampled paths match the
+    oracle above.  Allowed: ill-determined paths, at most 0.5 % of the roots
+    on either side."""
+    from paper_2112_03444_gb300 import inputs
+    fam = inputs.trifocal_family()
+    z = np.load(os.path.join(STARTS, "trifocal_f.npz"))
+    p1 = inputs.trifocal_scene(53)[0][None, :]
+    out = {}
+    for prec in (0, 1):
+        pr = hc.Problem(fam.system, kind=hc.HC_PARAMETER, p0=z["p0"], start=z["start"],
+                        settings=dict(precision=prec))
+        b = pr.track(n_instances=1, p1=p1).wait()
+        out[prec] = b.x[0][(b.status[0] & 0x7F) == hc.PATH_FINITE]
+    n64, nmx = len(out[0]), len(out[1])
+    assert abs(n64 - nmx) <= n64 // 200, (n64, nmx)
+    _, d_mx = match(out[1], out[0], TOL)      # mixed roots found by FP64
+    _, d_64 = match(out[0], out[1], TOL)      # FP64 roots found by mixed
+    assert (d_mx > TOL).sum() <= n64 // 200, int((d_mx > TOL).sum())
+    assert (d_64 > TOL).sum() <= n64 // 200, int((d_64 > TOL).sum())
+    # no root twice in the mixed result (duplicates were re-tracked)
+    assert distinct(out[1]) == nmx
