@@ -76,6 +76,7 @@ struct DenseTD {
   // of hard paths (an FP64 warp instruction costs the same pipe time with 8
   // or 32 active lanes).
   static constexpr int PARTS = (L_GROUP > L) ? L_GROUP / L : 1;
+  static constexpr int ROWL = (PARTS > 1) ? L : L_GROUP;  // lanes per row replica
   static_assert(PARTS == 1 || L_GROUP == 32, "split rows need the whole warp");
 
   template <class R>

@@ -137,6 +137,47 @@ __global__ void dedupe_kernel(int64_t items, int64_t paths, int n, const float2*
   }
 }
 
+// The same check for the *list_count listed items only, one warp per item
+// (the lanes split the scan of its instance): a few re-tracked endpoints
+// against every endpoint of their instance.
+__global__ void dedupe_list_kernel(int64_t paths, int n, const float2* __restrict__ x32,
+                                   const uint8_t* __restrict__ status, float tol,
+                                   const int64_t* __restrict__ list,
+                                   const unsigned long long* list_count, int64_t* out_list,
+                                   unsigned long long* out_count, double* t_io) {
+  const int lane = threadIdx.x & 31;
+  const int64_t total = (int64_t)*list_count;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+  for (int64_t w = blockIdx.x * (int64_t)(blockDim.x / 32) + threadIdx.x / 32; w < total;
+       w += warps) {
+    const int64_t a = list[w];
+    const float2* xa = x32 + a * n;
+    if (isnan(xa[0].x)) continue;  // uniform over the warp
+    float sc = 1.f;
+    for (int k = 0; k < n; ++k) sc = fmaxf(sc, fmaxf(fabsf(xa[k].x), fabsf(xa[k].y)));
+    const float thr = tol * sc;
+    const int64_t b0 = (a / paths) * paths;
+    bool dup = false;
+    for (int64_t b = b0 + lane; b < b0 + paths && !dup; b += 32) {
+      if (b == a) continue;
+      const float2* xb = x32 + b * n;
+      bool same = true;
+      for (int k = 0; k < n && same; ++k) {
+        const float2 p = xa[k], q = xb[k];
+        same = (fabsf(p.x - q.x) <= thr) && (fabsf(p.y - q.y) <= thr);
+      }
+      dup = same;
+    }
+    if (__any_sync(0xffffffffu, dup) && lane == 0) {
+      t_io[a] = 0.0;
+      if ((status[a] & 0x7f) != HC_PATH_SINGULAR) {
+        const unsigned long long pos = atomicAdd(out_count, 1ull);
+        out_list[pos] = a;
+      }
+    }
+  }
+}
+
 // Batch summary: [0] finite [1] real [2] diverged [3] singular [4] failed
 // [5] accepted steps [6] rejected steps [7] Newton iterations
 __global__ void summarize_kernel(int64_t items, const uint8_t* __restrict__ st,
@@ -953,10 +994,10 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
   // after the FP64-residual re-track: a re-tracked endpoint that still
   // collides goes to the all-FP64 tier, from t = 0
   auto dedupe_again = [&]() -> hc_status {
-    const int grid = (int)std::min<int64_t>((items + 255) / 256, 65535);
-    dedupe_kernel<<<std::max(grid, 1), 256, 0, hs>>>(items, p->paths, n, B.x32, B.d_status, 1e-6f,
-                                                    B.dup_list, B.d_ctl + 7, B.esc_list,
-                                                    B.d_ctl + 2, B.t_io);
+    const int grid = (int)std::min<int64_t>((items + 7) / 8, 1024);  // 8 warps per block
+    dedupe_list_kernel<<<std::max(grid, 1), 256, 0, hs>>>(p->paths, n, B.x32, B.d_status, 1e-6f,
+                                                         B.dup_list, B.d_ctl + 7, B.esc_list,
+                                                         B.d_ctl + 2, B.t_io);
     HC_CUDA(cudaGetLastError());
     return HC_OK;
   };
@@ -1610,9 +1651,15 @@ cudaError_t launch_dedupe(int64_t items, int64_t paths, int n, const float2* x32
                           const uint8_t* status, float tol, const int64_t* list,
                           const unsigned long long* list_count, int64_t* out_list,
                           unsigned long long* out_count, double* t_io, cudaStream_t st) {
-  const int grid = (int)std::min<int64_t>((items + 255) / 256, 65535);
-  dedupe_kernel<<<std::max(grid, 1), 256, 0, st>>>(items, paths, n, x32, status, tol, list,
-                                                  list_count, out_list, out_count, t_io);
+  if (list) {
+    const int grid = (int)std::min<int64_t>((items + 7) / 8, 1024);
+    dedupe_list_kernel<<<std::max(grid, 1), 256, 0, st>>>(paths, n, x32, status, tol, list,
+                                                         list_count, out_list, out_count, t_io);
+  } else {
+    const int grid = (int)std::min<int64_t>((items + 255) / 256, 65535);
+    dedupe_kernel<<<std::max(grid, 1), 256, 0, st>>>(items, paths, n, x32, status, tol, nullptr,
+                                                    nullptr, out_list, out_count, t_io);
+  }
   return cudaGetLastError();
 }
 

@@ -233,6 +233,68 @@ __device__ __forceinline__ bool gj_solve(const Group& g, cx<R> (&a)[N + NR], cx<
   return (lo & ~31u) != 0u && (hi & ~31u) < 0x7f800000u;
 }
 
+// The same elimination for groups whose rows are replicated over PARTS
+// lanes (one path per warp with the evaluation split over the warp, L0 =
+// lanes per replica): lane gl holds row r = gl mod L0 and owns the columns j
+// with j mod PARTS = gl / L0, the only ones it updates.  At step k the owners
+// of column k search the pivot; every owner publishes its row's entry of
+// column k (the multiplier's numerator) and the pivot row's lanes publish
+// their columns, all through shared memory; then each lane updates its own
+// columns.  The FP64 re-tracking tiers run this form: their cost is the
+// FP64 instructions per lane.  pv: 2 * ((N + 2) & ~1) entries, then L0
+// reciprocals and L0 ints; mkbuf: 2 * L0 entries.  NR = 1.  On return the
+// owner of column N in each pivoted row holds col and sol; col = -1 elsewhere.
+template <int N, class R, int L0, int PARTS>
+__device__ __forceinline__ bool gj_solve_parts(const Group& g, cx<R> (&a)[N + 1], cx<R> (&sol)[1],
+                                               int& col, cx<R>* pv, cx<R>* mkbuf) {
+  constexpr int W = N + 1;
+  constexpr int S = (W + 1) & ~1;
+  const int r = g.gl & (L0 - 1);
+  const int part = g.gl / L0;
+  cx<R>* dv = pv + 2 * S;                     // 1 / pivot of each row
+  int* pc = reinterpret_cast<int*>(dv + L0);  // pivot column of each row
+  bool used = r >= N;
+  unsigned lo = 0xffffffffu, hi = 0u;
+  col = -1;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const bool own = (part == k % PARTS);
+    const cx<R> inv = crecip(a[k]);
+    const float m = (float)cabs1(a[k]);
+    const unsigned key =
+        (used || !own) ? 0u : ((__float_as_uint(m) & ~31u) | (unsigned)(31 - g.wl));
+    const unsigned kmax = __reduce_max_sync(g.mask, key);
+    lo = min(lo, kmax);
+    hi = max(hi, kmax);
+    const int p = 31 - (int)(kmax & 31u);
+    const int rp = p & (L0 - 1);
+    cx<R>* buf = pv + (k & 1) * S;
+    cx<R>* mk = mkbuf + (k & 1) * L0;
+    if (own) mk[r] = a[k];
+    if (r == rp) {
+#pragma unroll
+      for (int j = k; j < W; ++j)
+        if (j % PARTS == part) buf[j] = (j == k) ? inv : a[j];
+      used = true;
+    }
+    if (g.wl == p) {
+      dv[r] = inv;
+      pc[r] = k;
+    }
+    __syncwarp(g.mask);
+    const cx<R> l = (r == rp) ? czero<R>() : mk[r] * buf[k];
+#pragma unroll
+    for (int j = k + 1; j < W; ++j)
+      if (j % PARTS == part) a[j] = cfms(l, buf[j], a[j]);
+  }
+  __syncwarp(g.mask);
+  if (part == N % PARTS && r < N) {
+    col = pc[r];
+    sol[0] = a[N] * dv[r];
+  }
+  return (lo & ~31u) != 0u && (hi & ~31u) < 0x7f800000u;
+}
+
 // ---------------------------------------------------------------- settings
 struct DevSettings {
   double dt_min, dt_max, dt_init, newton_tol, newton_tol_fp32, max_first_corr;

@@ -34,6 +34,8 @@ namespace hc {
 // kernel's group width L.
 template <int N, int L>
 struct TermEval {
+  static constexpr int PARTS = 1;  // one row per lane, no replicas
+  static constexpr int ROWL = L;
   const TermArgs* a;
   int64_t inst;
   Group g;

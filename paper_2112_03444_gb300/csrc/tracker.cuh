@@ -374,7 +374,9 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
             an = fmaxf(an, gsum<L, float>(g, act ? cabs2(cvt<float>(row[j])) : 0.f));
           cond_anorm = an;
         }
-        row[N] = mk<R>((act && g.gl == stage) ? R(1) : R(0), R(0));
+        // unit vector e_stage (on every replica of row stage)
+        const int grow = g.gl & (HOM::ROWL - 1);
+        row[N] = mk<R>((grow < N && grow == stage) ? R(1) : R(0), R(0));
       } else if (need64) {
         cx<double> H64;
         double sc;
@@ -384,7 +386,13 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
         row[N] = -H;
       }
     }
-    const bool sok = gj_solve<N, 1, R>(g, row, sol, col, reinterpret_cast<cx<R>*>(sm.pv));
+    bool sok;
+    if constexpr (HOM::PARTS > 1)
+      sok = gj_solve_parts<N, R, HOM::ROWL, HOM::PARTS>(g, row, sol, col,
+                                                       reinterpret_cast<cx<R>*>(sm.pv),
+                                                       reinterpret_cast<cx<R>*>(sm.sb));
+    else
+      sok = gj_solve<N, 1, R>(g, row, sol, col, reinterpret_cast<cx<R>*>(sm.pv));
     if (col >= 0) sb[col] = sol[0];
     __syncwarp(g.mask);
     const cx<R> d = act ? sb[g.gl] : czero<R>();
