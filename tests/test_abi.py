@@ -107,3 +107,25 @@ def test_null_handles_are_rejected(hc):
     assert hc._lib.hc_poll(None, 0, ctypes.byref(r)) == hc.HC_ERR_INVALID
     assert hc._lib.hc_problem_paths(None) == -1
     hc._lib.hc_destroy(None)  # no-op
+
+
+@pytest.mark.parametrize("field,value", [("max_newton_ir", 0), ("max_newton_ir", 33), ("reserved", 1),
+                                         ("lanes", 16)])
+def test_create_problem_rejects_bad_iteration_limits(hc, field, value):
+    from paper_2112_03444_gb300 import inputs
+    d, keep = _desc(hc, inputs.dense_system(2, 2, 0))
+    setattr(d.settings, field, value)
+    h = ctypes.c_void_p()
+    assert hc._lib.hc_create_problem(ctypes.byref(d), ctypes.byref(h)) == hc.HC_ERR_INVALID
+
+
+def test_default_refinement_iterations(hc):
+    s = hc.default_settings()
+    assert s.max_newton_ir == 2 * s.max_newton and s.reserved == 0
+
+
+def test_plan_calls_reject_null_handles(hc):
+    h = ctypes.c_void_p()
+    assert hc._lib.hc_plan_create(None, 1, ctypes.byref(h)) == hc.HC_ERR_INVALID
+    b = hc.hc_batch_desc()
+    assert hc._lib.hc_plan_run(None, ctypes.byref(b), ctypes.byref(h)) == hc.HC_ERR_INVALID
