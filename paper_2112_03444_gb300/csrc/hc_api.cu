@@ -955,11 +955,14 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
   cm.x32_out = B.x32;
   cm.dup_list = B.dup_list;
   cm.dup_count = B.d_ctl + 7;
-  // Re-tracking tiers.  Colliding paths and FP32-tier failures other than
-  // step-size ones (dup_list, ctl[7]) run again from t = 0 in the mixed
-  // kernel with the FP64 state, FP64 residuals and FP64 tolerances; whatever
-  // still fails there, step-size failures and suspect-condition endpoints
-  // (esc_list, ctl[2]) run in the all-FP64 kernel.
+  // Re-tracking tiers.  FP32-tier failures other than step-size ones
+  // (divergence, non-finite state, failed refinement: dup_list, ctl[7]) run
+  // again from t = 0 in the mixed kernel with the FP64 state, FP64 residuals
+  // and FP64 tolerances.  Colliding endpoints (path jumps, found by the
+  // duplicate check), whatever still fails or collides after that tier,
+  // step-size failures and suspect-condition endpoints (esc_list, ctl[2])
+  // run in the all-FP64 kernel: from t = 0, from the last accepted point, or
+  // only the refinement and condition at t = 1.
   hc::LaunchCommon cd = cm;
   cd.count_dev = B.d_ctl + 7;
   cd.items = B.dup_list;
@@ -986,13 +989,13 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
     HC_CUDA(cudaStreamWaitEvent(hs, ev.capture ? ev.fork : ev.ek1, 0));
     const int grid = (int)std::min<int64_t>((items + 255) / 256, 65535);
     dedupe_kernel<<<std::max(grid, 1), 256, 0, hs>>>(items, p->paths, n, B.x32, B.d_status, 1e-6f,
-                                                    nullptr, nullptr, B.dup_list, B.d_ctl + 7,
+                                                    nullptr, nullptr, B.esc_list, B.d_ctl + 2,
                                                     B.t_io);
     HC_CUDA(cudaGetLastError());
     return HC_OK;
   };
-  // after the FP64-residual re-track: a re-tracked endpoint that still
-  // collides goes to the all-FP64 tier, from t = 0
+  // after the FP64-residual re-track: a re-tracked endpoint that collides
+  // goes to the all-FP64 tier, from t = 0
   auto dedupe_again = [&]() -> hc_status {
     const int grid = (int)std::min<int64_t>((items + 7) / 8, 1024);  // 8 warps per block
     dedupe_list_kernel<<<std::max(grid, 1), 256, 0, hs>>>(p->paths, n, B.x32, B.d_status, 1e-6f,

@@ -50,7 +50,7 @@ struct LaunchCommon {
   unsigned long long* dup_count;
   int start_hi;                 // mixed kernel: track every path with the FP64 state, FP64
                                 // residuals and FP64 tolerances from t = 0 (re-tracking of
-                                // colliding paths)
+                                // FP32-tier failures)
   int spread;                   // first round of items round-robin over the blocks (one
                                 // per block before any second), then the queue: a short
                                 // list of FP64-heavy paths lands on as many SMs as it can

@@ -308,8 +308,8 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
   }
   NA_CUDA(launch(k, a, items));
   if (escalate) {
-    NA_CUDA(hc::launch_dedupe(items, paths, n, x32, status_out, 1e-6f, nullptr, nullptr, dup,
-                              ctl + 7, t_io, st));
+    NA_CUDA(hc::launch_dedupe(items, paths, n, x32, status_out, 1e-6f, nullptr, nullptr, esc,
+                              ctl + 2, t_io, st));
     hc::DenseArgs dd = a;
     dd.c.count_dev = ctl + 7;
     dd.c.items = dup;
