@@ -11,6 +11,7 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -597,46 +598,42 @@ struct Occ {
   int sms = 0;
 };
 
-Occ occupancy(const void* fn, size_t smem) {
+Occ occupancy(const void* fn, size_t smem, int threads) {
   static std::mutex mu;
-  static std::map<std::pair<const void*, size_t>, Occ> cache;
+  static std::map<std::tuple<const void*, size_t, int>, Occ> cache;
   std::lock_guard<std::mutex> lk(mu);
-  auto key = std::make_pair(fn, smem);
+  auto key = std::make_tuple(fn, smem, threads);
   auto it = cache.find(key);
   if (it != cache.end()) return it->second;
   Occ o;
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&o.sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.blocks, fn, hc::kBlock, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.blocks, fn, threads, smem);
   if (o.blocks < 1) o.blocks = 1;
   cache[key] = o;
   return o;
 }
 
+// Persistent launch: grid = resident blocks per SM x SMs, or fewer when the
+// items (at most max_items) need fewer groups.
 hc_status launch_generic(const hc::KernelRef& k, void* args, size_t smem, int64_t max_items,
-                         cudaStream_t st) {
+                         cudaStream_t st, int threads = hc::kBlock) {
   if (smem > 48 * 1024)
     HC_CUDA(cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const Occ o = occupancy(k.fn, smem);
-  const int64_t groups_per_block = hc::kBlock / k.lanes;
+  const Occ o = occupancy(k.fn, smem, threads);
+  const int64_t groups_per_block = threads / k.lanes;
   int64_t want = (max_items + groups_per_block - 1) / groups_per_block;
   int64_t grid = std::min<int64_t>((int64_t)o.blocks * o.sms, std::max<int64_t>(want, 1));
   void* argv[] = {args};
-  HC_CUDA(cudaLaunchKernel(k.fn, dim3((unsigned)grid), dim3(hc::kBlock), argv, smem, st));
+  HC_CUDA(cudaLaunchKernel(k.fn, dim3((unsigned)grid), dim3(threads), argv, smem, st));
   return HC_OK;
 }
 
 hc_status launch_tracker(const hc::KernelRef& k, const hc::DenseArgs& a, int64_t max_items,
-                         cudaStream_t st) {
-  const size_t smem = (size_t)hc::block_smem_bytes(k.lanes, k.extra);
-  const Occ o = occupancy(k.fn, smem);
-  const int64_t groups_per_block = hc::kBlock / k.lanes;
-  int64_t want = (max_items + groups_per_block - 1) / groups_per_block;
-  int64_t grid = std::min<int64_t>((int64_t)o.blocks * o.sms, std::max<int64_t>(want, 1));
-  void* args[] = {(void*)&a};
-  HC_CUDA(cudaLaunchKernel(k.fn, dim3((unsigned)grid), dim3(hc::kBlock), args, smem, st));
-  return HC_OK;
+                         cudaStream_t st, int threads = hc::kBlock) {
+  const size_t smem = (size_t)hc::block_smem_bytes(k.lanes, k.extra, 0, threads);
+  return launch_generic(k, (void*)&a, smem, max_items, st, threads);
 }
 
 }  // namespace
@@ -955,11 +952,11 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
   cm.x32_out = B.x32;
   cm.dup_list = B.dup_list;
   cm.dup_count = B.d_ctl + 7;
-  // Re-tracking tiers.  FP32-tier failures other than step-size ones
+  // Re-tracking tiers.  Colliding endpoints (path jumps, found by the
+  // duplicate check) and FP32-tier failures other than step-size ones
   // (divergence, non-finite state, failed refinement: dup_list, ctl[7]) run
   // again from t = 0 in the mixed kernel with the FP64 state, FP64 residuals
-  // and FP64 tolerances.  Colliding endpoints (path jumps, found by the
-  // duplicate check), whatever still fails or collides after that tier,
+  // and FP64 tolerances.  Whatever still fails or collides after that tier,
   // step-size failures and suspect-condition endpoints (esc_list, ctl[2])
   // run in the all-FP64 kernel: from t = 0, from the last accepted point, or
   // only the refinement and condition at t = 1.
@@ -989,7 +986,7 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
     HC_CUDA(cudaStreamWaitEvent(hs, ev.capture ? ev.fork : ev.ek1, 0));
     const int grid = (int)std::min<int64_t>((items + 255) / 256, 65535);
     dedupe_kernel<<<std::max(grid, 1), 256, 0, hs>>>(items, p->paths, n, B.x32, B.d_status, 1e-6f,
-                                                    nullptr, nullptr, B.esc_list, B.d_ctl + 2,
+                                                    nullptr, nullptr, B.dup_list, B.d_ctl + 7,
                                                     B.t_io);
     HC_CUDA(cudaGetLastError());
     return HC_OK;
@@ -1019,8 +1016,8 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
     ta.p1 = B.d_p1;
     ta.start = p->d_start;
     const hc::KernelRef k = hc::term_kernel(n, mixed, mixed ? p->s.lanes : 0);
-    auto smem_of = [&](const hc::KernelRef& kr) {
-      return (size_t)hc::block_smem_bytes(kr.lanes, p->extra, kr.acc_bytes);
+    auto smem_of = [&](const hc::KernelRef& kr, int threads = hc::kBlock) {
+      return (size_t)hc::block_smem_bytes(kr.lanes, p->extra, kr.acc_bytes, threads);
     };
     HC_CUDA(mark(ev.ek0, st));
     if ((rc = launch_generic(k, &ta, smem_of(k), items, st)) != HC_OK) return rc;
@@ -1030,12 +1027,15 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
       if ((rc = dedupe()) != HC_OK) return rc;
       hc::TermArgs td = ta;
       td.c = cd;
-      if ((rc = launch_generic(k, &td, smem_of(k), esc_groups, hs)) != HC_OK) return rc;
+      const int th = hc::retrack_threads(k.lanes);
+      if ((rc = launch_generic(k, &td, smem_of(k, th), esc_groups, hs, th)) != HC_OK) return rc;
       if ((rc = dedupe_again()) != HC_OK) return rc;
       hc::TermArgs te = ta;
       te.c = ce;
       const hc::KernelRef k64 = hc::term_kernel(n, false, 0);
-      if ((rc = launch_generic(k64, &te, smem_of(k64), esc_groups, hs)) != HC_OK) return rc;
+      const int th64 = hc::retrack_threads(k64.lanes);
+      if ((rc = launch_generic(k64, &te, smem_of(k64, th64), esc_groups, hs, th64)) != HC_OK)
+        return rc;
       HC_CUDA(mark(ev.ek2, hs));
       if (ev.capture) HC_CUDA(cudaEventRecord(ev.join, hs));
       HC_CUDA(cudaStreamWaitEvent(st, ev.capture ? ev.join : ev.ek2, 0));
@@ -1068,12 +1068,14 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
       // the rows split over the warp where that variant exists
       hc::DenseArgs dd = a;
       dd.c = cd;
-      if ((rc = launch_tracker(retrack_kernel(p->deg, n, true), dd, esc_groups, hs)) != HC_OK)
+      const hc::KernelRef kr = retrack_kernel(p->deg, n, true);
+      if ((rc = launch_tracker(kr, dd, esc_groups, hs, hc::retrack_threads(kr.lanes))) != HC_OK)
         return rc;
       if ((rc = dedupe_again()) != HC_OK) return rc;
       hc::DenseArgs e = a;
       e.c = ce;
-      if ((rc = launch_tracker(retrack_kernel(p->deg, n, false), e, esc_groups, hs)) != HC_OK)
+      const hc::KernelRef k64 = retrack_kernel(p->deg, n, false);
+      if ((rc = launch_tracker(k64, e, esc_groups, hs, hc::retrack_threads(k64.lanes))) != HC_OK)
         return rc;
       HC_CUDA(mark(ev.ek2, hs));
       if (ev.capture) HC_CUDA(cudaEventRecord(ev.join, hs));

@@ -20,10 +20,16 @@ constexpr int kBlock = 128;  // threads per block of the tracking kernels
 __host__ __device__ constexpr int group_smem_bytes(int L, int extra, int acc = 0) {
   return ((32 * (L + 2) + acc + (L + extra) * 16 + L * 16 + (L + extra) * 8 + 127) & ~127) + 16;
 }
-// Dynamic shared memory of one tracking block
-__host__ __device__ constexpr int block_smem_bytes(int L, int extra, int acc = 0) {
-  return (kBlock / L) * group_smem_bytes(L, extra, acc);
+// Dynamic shared memory of one tracking block of `threads` threads
+__host__ __device__ constexpr int block_smem_bytes(int L, int extra, int acc = 0,
+                                                   int threads = kBlock) {
+  return (threads / L) * group_smem_bytes(L, extra, acc);
 }
+// Threads per block of a launch: one warp for one-path-per-warp launches of
+// the re-tracking tiers (a hard path then holds only its own warp's
+// registers, not three idle warps' beside the other classes' launches),
+// kBlock otherwise.
+inline int retrack_threads(int lanes) { return lanes == 32 ? 32 : kBlock; }
 
 // Work distribution of a tracking launch: work item = (instance, path),
 // item = instance * paths + path; a lane group takes the next item with one
@@ -50,7 +56,7 @@ struct LaunchCommon {
   unsigned long long* dup_count;
   int start_hi;                 // mixed kernel: track every path with the FP64 state, FP64
                                 // residuals and FP64 tolerances from t = 0 (re-tracking of
-                                // FP32-tier failures)
+                                // colliding and failed paths)
   int spread;                   // first round of items round-robin over the blocks (one
                                 // per block before any second), then the queue: a short
                                 // list of FP64-heavy paths lands on as many SMs as it can

@@ -287,19 +287,20 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
   int dev = 0, sms = 0;
   NA_CUDA(cudaGetDevice(&dev));
   NA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  auto launch = [&](const hc::KernelRef& k, const hc::DenseArgs& args, int64_t max_items) {
-    const size_t smem = (size_t)hc::block_smem_bytes(k.lanes, k.extra);
+  auto launch = [&](const hc::KernelRef& k, const hc::DenseArgs& args, int64_t max_items,
+                    int threads = hc::kBlock) {
+    const size_t smem = (size_t)hc::block_smem_bytes(k.lanes, k.extra, 0, threads);
     int blocks = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k.fn, hc::kBlock, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k.fn, threads, smem) !=
         cudaSuccess)
       return cudaErrorUnknown;
     if (blocks < 1) blocks = 1;
-    const int64_t gpb = hc::kBlock / k.lanes;
+    const int64_t gpb = threads / k.lanes;
     int64_t grid = (int64_t)blocks * sms;
     const int64_t want = (max_items + gpb - 1) / gpb;
     if (want < grid) grid = want < 1 ? 1 : want;
     void* argv[] = {(void*)&args};
-    return cudaLaunchKernel(k.fn, dim3((unsigned)grid), dim3(hc::kBlock), argv, smem, st);
+    return cudaLaunchKernel(k.fn, dim3((unsigned)grid), dim3(threads), argv, smem, st);
   };
   const hc::KernelRef k = hc::dense_kernel(degree, n, mixed, 0);
   if (!k.fn) {
@@ -308,8 +309,8 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
   }
   NA_CUDA(launch(k, a, items));
   if (escalate) {
-    NA_CUDA(hc::launch_dedupe(items, paths, n, x32, status_out, 1e-6f, nullptr, nullptr, esc,
-                              ctl + 2, t_io, st));
+    NA_CUDA(hc::launch_dedupe(items, paths, n, x32, status_out, 1e-6f, nullptr, nullptr, dup,
+                              ctl + 7, t_io, st));
     hc::DenseArgs dd = a;
     dd.c.count_dev = ctl + 7;
     dd.c.items = dup;
@@ -318,7 +319,8 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
     dd.c.spread = 1;
     dd.c.dup_list = nullptr;
     dd.c.dup_count = nullptr;
-    NA_CUDA(launch(hc::retrack_kernel(degree, n, true), dd, items));
+    const hc::KernelRef kr = hc::retrack_kernel(degree, n, true);
+    NA_CUDA(launch(kr, dd, items, hc::retrack_threads(kr.lanes)));
     NA_CUDA(hc::launch_dedupe(items, paths, n, x32, status_out, 1e-6f, dup, ctl + 7, esc, ctl + 2,
                               t_io, st));
     hc::DenseArgs e = a;
@@ -331,7 +333,8 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
     e.c.spread = 1;
     e.c.dup_list = nullptr;
     e.c.dup_count = nullptr;
-    NA_CUDA(launch(hc::retrack_kernel(degree, n, false), e, items));
+    const hc::KernelRef k64 = hc::retrack_kernel(degree, n, false);
+    NA_CUDA(launch(k64, e, items, hc::retrack_threads(k64.lanes)));
   }
 #undef NA_CUDA
   return HC_OK;

@@ -229,7 +229,7 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
             // from the last accepted point (t = 1: refinement and exact
             // condition only).  Other failures of the FP32 tier (divergence,
             // non-finite state, failed refinement) are first re-tracked from
-            // t = 0 with FP64 residuals.
+            // t = 0 with FP64 residuals, like colliding paths.
             const bool to64 = base == ST_FAIL_STEP || base == ST_FAIL_MAXSTEPS ||
                               base == ST_SINGULAR || c.start_hi || !c.dup_list;
             if (c.t_io)

@@ -113,3 +113,22 @@ def test_poll_nonblocking_then_done(hc):
     assert code in (hc.HC_OK, hc.HC_PENDING)
     assert bt.poll(-1) == hc.HC_OK
     assert bt.result["finite"] == 4
+
+
+@pytest.mark.parametrize("n,d,ninst", [(8, 3, 16), (12, 2, 4)])
+def test_no_root_reported_twice(hc, n, d, ninst):
+    """Full batches of the bench's largest classes (mixed tiers, duplicate
+    detection and re-tracking on): within every instance the finite
+    endpoints are pairwise distinct, and the Bezout count is reached up to
+    the few paths that also fail in FP64 (a property at any size)."""
+    from paper_2112_03444_gb300 import inputs
+    seeds = [100 + k for k in range(ninst)]
+    base, coefs = inputs.dense_batch(n, d, seeds)
+    pr = hc.Problem(base, gamma=inputs.unit_gamma(seeds[0]))
+    b = pr.track(n_instances=ninst, coef=coefs).wait()
+    total = 0
+    for s in range(ninst):
+        fin = (b.status[s] & 0x7F) == hc.PATH_FINITE
+        total += int(fin.sum())
+        assert distinct(b.x[s][fin]) == int(fin.sum()), s
+    assert total >= ninst * d ** n - max(2, ninst * d ** n // 10000), total
