@@ -12,9 +12,11 @@
  *   - Sec. 3, Eqs. 2-4: predictor on dx/dt = -(dH/dx)^-1 dH/dt, with the
  *     4th-order Runge-Kutta method the paper names.
  *   - Sec. 3, Eqs. 5-6: Newton corrector at t + dt.
- *   - Sec. 6: per path, evaluation of H, dH/dx, dH/dt from homogenised term
- *     tuples, and a fused solve of the small dense complex system on the
- *     augmented matrix [A b] kept in registers, one matrix row per lane.
+ *   - Sec. 6: per path, evaluation of H, dH/dx, dH/dt from the terms of the
+ *     equations (each term's value and all its derivatives from one pass of
+ *     prefix and suffix products), and a fused solve of the small dense
+ *     complex system on the augmented matrix [A b] kept in registers, one
+ *     matrix row per lane.
  *
  * The problem statement follows Sec. 3: N polynomial equations in N unknowns
  * (square systems), a start system whose solutions are all known, and the

@@ -258,7 +258,7 @@ struct hc_problem {
   int* d_dslot = nullptr;
   float* d_dmult = nullptr;
   double* d_coef = nullptr;  // default coefficients [T][2]
-  // parameter homotopy (homogenised term tuples)
+  // parameter homotopy (term tables, see encode_terms)
   bool terms = false;
   int TT = 0;  // term slots per row
   int extra = 0;
@@ -491,12 +491,13 @@ bool encode_dense(hc_problem* p, std::vector<int>& emap, std::vector<int>& dterm
 }
 
 
-// Homogenised term tuples of a parameter homotopy (paper Sec. 6): for every
-// row i and entry e (dH_i/dx_j for e = j < n, dH_i/dt for e = n, H_i for
-// e = n + 1) a list of tuples (s, factor indices into V), V = [x | pad to L |
-// 1 | p(t) | dp].  x-derivatives by the power rule, the t-derivative by the
-// product rule over the parameter factors (dp/dt = p1 - p0).  Entries are
-// padded to a common tuple count per entry and a common factor count.
+// Term tables of a parameter homotopy (paper Sec. 6 evaluates the terms of
+// the equations per row): for every row i its terms, each a coefficient and
+// up to 8 factor positions in V = [x | pad to L | 1 | p(t) | dp | p0] (a
+// power x_j^a as a repeated factor), with the entry every factor's
+// derivative feeds (x_j -> j, a parameter -> n, i.e. dH/dt through dp).  Rows
+// are padded to the same number of term slots, and every slot to the largest
+// factor count of its terms over the rows (padding factor: the 1).
 bool encode_terms(hc_problem* p, std::vector<hc::TermRec>& rec, std::vector<double2>& s64) {
   const int n = p->n, P = p->P, L = hc::lanes_for(n);
   const int one = L, pbase = L + 1, dbase = L + 1 + P;

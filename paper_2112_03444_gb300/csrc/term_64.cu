@@ -1,4 +1,4 @@
-// Parameter-homotopy (term-tuple) tracking kernels, FP64, n = 1..24.
+// Parameter-homotopy (term table) tracking kernels, FP64, n = 1..24.
 // lanes = 0 selects the default group width; the mixed kernels also come
 // with one path per warp (lanes = 32) for the autotuner.
 #include "term_param.cuh"

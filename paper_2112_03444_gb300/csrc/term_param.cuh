@@ -29,9 +29,9 @@
 
 namespace hc {
 
-// The tuple tables and the V index positions (1 at LS, p(t) at LS + 1, dp at
-// LS + 1 + P) use the encoding's lane stride LS = a->ls, independent of the
-// kernel's group width L.
+// The term tables and the V index positions (1 at LS, p(t) at LS + 1, dp at
+// LS + 1 + P, p0 at LS + 1 + 2P) use the encoding's lane stride LS = a->ls,
+// independent of the kernel's group width L.
 template <int N, int L>
 struct TermEval {
   static constexpr int PARTS = 1;  // one row per lane, no replicas

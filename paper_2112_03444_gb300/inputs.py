@@ -14,8 +14,8 @@ Term-list format (shared by the C-ABI and the oracle):
                                   coefficient (-1 = no factor); maxpf may be 0
 
 A term's value is s_k * prod_l p_{param_kl} * x^{alpha_k}.  The paper's
-target systems F(x) (Sec. 3, Eq. 1) are sums of such terms; the homogenised
-term tuples of Sec. 6 are derived from this list by the library.
+target systems F(x) (Sec. 3, Eq. 1) are sums of such terms; the library
+derives its evaluation tables (Sec. 6) from this list.
 """
 from __future__ import annotations
 
