@@ -149,7 +149,7 @@ struct DenseTD {
       cx<R> a2[N];
 #pragma unroll
       for (int j = 0; j < N; ++j) a2[j] = czero<R>();
-#pragma unroll 2
+#pragma unroll 4
       for (int m = part; m < S::NQ; m += PARTS) {
         const cx<R> mu = Q[m];
         const cx<R>* Dm = D + (1 + N + m) * L;
