@@ -39,12 +39,11 @@ SM_COUNT = 152
 
 def source_sha() -> str:
     """sha256 (16 hex) of the sources that compile into the dominant tracking
-    kernel: its translation unit, the device headers and the C-ABI header."""
+    kernel: its translation unit and the device headers."""
     import glob
     import hashlib
     csrc = os.path.join(ROOT, "paper_2112_03444_gb300", "csrc")
-    files = sorted(glob.glob(os.path.join(csrc, "*.cuh")) +
-                   [os.path.join(csrc, "dense_c32.cu"), os.path.join(ROOT, "include", "hc.h")])
+    files = sorted(glob.glob(os.path.join(csrc, "*.cuh")) + [os.path.join(csrc, "dense_c32.cu")])
     h = hashlib.sha256()
     for f in sorted(files, key=lambda f: os.path.relpath(f, ROOT)):
         h.update(open(f, "rb").read())

@@ -60,7 +60,9 @@ enum {
   HC_PREC_FP64 = 0,   /* every step in complex FP64 (the plain reference form)         */
   HC_PREC_MIXED = 1   /* complex FP32 predictor and corrector; FP64 state x, FP64
                          residuals in the endgame (t > t_endgame) and the final
-                         Newton refinement; failed paths re-tracked in FP64         */
+                         Newton refinement; colliding endpoints (path jumps) and
+                         failed paths re-tracked with FP64 residuals, then in
+                         FP64                                                       */
 };
 
 /* Per-path status codes (hc_batch_desc.status_out).  HC_PATH_REAL is or-ed
@@ -118,7 +120,8 @@ typedef struct hc_settings {
   int32_t grow_after;     /* 3 */
   int32_t refine_iters;   /* 8 */
   int32_t precision;      /* HC_PREC_MIXED */
-  int32_t escalate;       /* 1: mixed-precision paths that fail are re-tracked in FP64 */
+  int32_t escalate;       /* 1: mixed-precision paths that fail or whose endpoints
+                             collide are re-tracked (FP64 residuals, then FP64)     */
   int32_t lanes;          /* mixed precision: 0 = default group width (next power of two
                              >= n, at least 4), 32 = one path per warp (n <= 16)   */
   int32_t max_newton_ir;  /* mixed precision: corrector iterations allowed in the
@@ -192,12 +195,12 @@ typedef struct hc_batch_desc {
 typedef struct hc_batch_result {
   int64_t paths;               /* n_instances * paths per instance            */
   int64_t finite, real, diverged, singular, failed;
-  int64_t escalated;           /* mixed-precision paths re-tracked in FP64      */
+  int64_t escalated;           /* mixed-precision re-tracks (both tiers)        */
   int64_t steps_accepted, steps_rejected, newton_iters;  /* all tiers        */
   int64_t esc_accepted, esc_rejected, esc_newton;        /* FP64 tier part   */
   double device_ms;            /* stream time from first copy to last copy      */
   double track_ms;             /* stream time of the tracking launch             */
-  double escalate_ms;          /* stream time of the FP64 re-tracking launch     */
+  double escalate_ms;          /* stream time of the re-tracking launches        */
 } hc_batch_result;
 
 /* Static description of an error code; never NULL. */
