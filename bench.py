@@ -68,6 +68,18 @@ def env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
 
 
+def max_over_ranks(value, world, device=None):
+    """The largest value over the ranks (the slowest replica's step time):
+    rank 0 reports whole-job throughput from it.  world <= 1: value."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload(rank=0):
     """Per size: (n, d, base TermSystem, coefficient array [16, T], gamma)."""
     from paper_2112_03444_gb300 import inputs
@@ -246,9 +258,8 @@ def run_gpu(args):
     torch.cuda.synchronize()
     ms = sum(step_ms) / len(step_ms)
     if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        dist.barrier()
+    ms = max_over_ranks(ms, world, dev)
 
     # ---- correctness of the measured run: Bezout count per system
     last = results[-1]
