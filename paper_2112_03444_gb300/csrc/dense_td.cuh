@@ -17,15 +17,19 @@
 //   F_i = c0 + sum_j x_j (b_j + sum_{k<=j} x_k (q_jk + sum_{l<=k} r_jkl x_l)),
 // one complex FMA per monomial.
 //
-// Data layout (per instance, lane stride L so that lane i reads D[..][i] and
-// the L lanes of a path read L consecutive complex numbers):
-//   D: [(N+1) slices][MP][L]; slice N entry 0 holds the constant c_i0.
+// Data layout (per instance, lane stride L so that the L lanes of a path read
+// consecutive addresses):
+//   D: [(N+1) slices][MPP/2 monomial pairs][L][2]: lane i reads the two
+//      coefficients of a pair with one 16-byte load (FP32); the constant,
+//      linear and quadratic monomials each start a new pair (dense_slot in
+//      kernels.cuh); slice N pair 0 holds the constant c_i0.
 //   E: [M][L] complex double, nested Horner order.
 #pragma once
 
 #include <type_traits>
 
 #include "hc_device.cuh"
+#include "kernels.cuh"
 
 namespace hc {
 
@@ -39,9 +43,13 @@ struct DenseShape {
     return 1 + N + k * N - k * (k - 1) / 2 + (l - k);
   }
   // quadratic monomials x_k x_l (k <= l), formed per evaluation in the
-  // group's shared memory behind the point (cubic systems only)
+  // group's shared memory behind the lane slots of the point (cubic systems
+  // only; padded to an even count like the table)
   static constexpr int NQ = N * (N + 1) / 2;
-  static constexpr int EXTRA = (DEG == 3) ? NQ : 0;
+  static constexpr int N2 = N + (N & 1);                    // linear monomials, padded
+  static constexpr int NQ2 = (DEG == 3) ? NQ + (NQ & 1) : 0;  // quadratic ones, padded
+  static constexpr int MPP = dense_mpp(N, DEG);             // padded monomials per slice
+  static constexpr int EXTRA = NQ2;
 };
 
 template <int N, int DEG, int L_GROUP>
@@ -97,20 +105,38 @@ struct DenseTD {
     return (m & 1) ? ((m + 1) * PARTS - 1 - part) : (m * PARTS + part);
   }
 
-  // The contraction indices run in loops that are not unrolled (x_k and the
-  // quadratic monomials are read from the group's shared memory); the rows j
-  // stay unrolled so that the accumulators live in registers.  The point is
-  // read from shared memory too (x is not needed in registers).
+  // Two consecutive complex numbers (16-byte aligned): one 16-byte load in
+  // FP32, two in FP64.
+  template <class R>
+  __device__ __forceinline__ static void ld2(const cx<R>* p, cx<R>& c0, cx<R>& c1) {
+    if constexpr (std::is_same<R, float>::value) {
+      const float4 f = *reinterpret_cast<const float4*>(p);
+      c0 = mk<float>(f.x, f.y);
+      c1 = mk<float>(f.z, f.w);
+    } else {
+      c0 = p[0];
+      c1 = p[1];
+    }
+  }
+
+  // The contraction indices run in loops that are not unrolled (pairs of
+  // point entries and quadratic monomials are read from the group's shared
+  // memory); the rows j stay unrolled so that the accumulators live in
+  // registers.  The point is read from shared memory too (x is not needed in
+  // registers).
   template <class R>
   __device__ __forceinline__ void eval(const cx<R> (&)[N], int i, R t, R omt, cx<R> (&row)[N + 1],
                                        cx<R>& H, cx<R>& Ht) const {
     const int r = i & (L - 1);                   // this lane's row
+    const int rr = r < N ? r : 0;
     const int part = (PARTS > 1) ? i / L : 0;    // and its share of the contraction
-    const cx<R>* D = dptr<R>() + (r < N ? r : 0);
+    const cx<R>* D = dptr<R>();
+    // the pair q of slice j, this lane's row
+    auto pair = [&](int j, int q) { return D + ((int64_t)(j * (S::MPP / 2) + q) * L + rr) * 2; };
     cx<R>* V = vptr<R>();
+    cx<R>* Q = V + L_GROUP;
     if constexpr (DEG == 3) {
       // x_k x_l for k <= l in graded order, the group's lanes sharing the work
-      cx<R>* Q = V + L;
 #pragma unroll 1
       for (int m = i; m < S::NQ; m += L_GROUP) {
         int k = 0, rem = m;
@@ -125,14 +151,18 @@ struct DenseTD {
     cx<R> a1[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) a1[j] = czero<R>();
-#pragma unroll 2
-    for (int k = part; k < N; k += PARTS) {
-      const cx<R> xk = V[k];
-      const cx<R>* Dk = D + (1 + k) * L;
+#pragma unroll 1
+    for (int q = part; q < S::N2 / 2; q += PARTS) {
+      cx<R> x0, x1;
+      ld2(V + 2 * q, x0, x1);
 #pragma unroll
-      for (int j = 0; j < N; ++j) a1[j] = cfma(Dk[j * S::MP * L], xk, a1[j]);
+      for (int j = 0; j < N; ++j) {
+        cx<R> c0, c1;
+        ld2(pair(j, 1 + q), c0, c1);
+        a1[j] = cfma(c1, x1, cfma(c0, x0, a1[j]));
+      }
     }
-    cx<R> F = D[(N * S::MP) * L];
+    cx<R> F = pair(N, 0)[0];
     if constexpr (DEG == 2) {
       if constexpr (PARTS > 1) {
 #pragma unroll
@@ -140,21 +170,24 @@ struct DenseTD {
       }
 #pragma unroll
       for (int j = 0; j < N; ++j) {
-        const cx<R> a0 = D[(j * S::MP) * L];
+        const cx<R> a0 = pair(j, 0)[0];
         row[j] = a0 + a1[j];
         F = cfma(V[j], a0 + R(0.5) * a1[j], F);
       }
     } else {
-      const cx<R>* Q = V + L;
       cx<R> a2[N];
 #pragma unroll
       for (int j = 0; j < N; ++j) a2[j] = czero<R>();
-#pragma unroll 4
-      for (int m = part; m < S::NQ; m += PARTS) {
-        const cx<R> mu = Q[m];
-        const cx<R>* Dm = D + (1 + N + m) * L;
+#pragma unroll 2
+      for (int q = part; q < S::NQ2 / 2; q += PARTS) {
+        cx<R> m0, m1;
+        ld2(Q + 2 * q, m0, m1);
 #pragma unroll
-        for (int j = 0; j < N; ++j) a2[j] = cfma(Dm[j * S::MP * L], mu, a2[j]);
+        for (int j = 0; j < N; ++j) {
+          cx<R> c0, c1;
+          ld2(pair(j, 1 + S::N2 / 2 + q), c0, c1);
+          a2[j] = cfma(c1, m1, cfma(c0, m0, a2[j]));
+        }
       }
       if constexpr (PARTS > 1) {
         // partial rows and the partial Euler sum, then one reduction each
@@ -167,20 +200,20 @@ struct DenseTD {
         F = F + part_sum(fp);
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-          const cx<R> a0 = D[(j * S::MP) * L];
+          const cx<R> a0 = pair(j, 0)[0];
           row[j] = a0 + a1[j];
           F = cfma(V[j], a0, F);
         }
       } else {
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-          const cx<R> a0 = D[(j * S::MP) * L];
+          const cx<R> a0 = pair(j, 0)[0];
           row[j] = a0 + a1[j] + a2[j];
           F = cfma(V[j], a0 + R(0.5) * a1[j] + R(1.0 / 3.0) * a2[j], F);
         }
       }
     }
-    const cx<R> xi = V[r < N ? r : 0];
+    const cx<R> xi = V[rr];
     // G_i = xi^d - 1, dG_i/dx_i = d xi^(d-1)
     const cx<R> xi2 = xi * xi;
     const cx<R> G = (DEG == 2 ? xi2 : xi2 * xi) - mk<R>(R(1), R(0));
@@ -278,7 +311,20 @@ struct DenseTD {
     }
   }
 
-  __device__ __forceinline__ void init(const Group&) const {}
+  // per path: the pad entries behind the point (odd N) and behind the
+  // quadratic monomials (odd count) are read by the pair loads as zeros
+  __device__ __forceinline__ void init(const Group& g) const {
+    if (g.gl == 0) {
+      if constexpr (N & 1) {
+        Vf[N] = czero<float>();
+        Vd[N] = czero<double>();
+      }
+      if constexpr (DEG == 3 && (S::NQ & 1)) {
+        Vf[L_GROUP + S::NQ] = czero<float>();
+        Vd[L_GROUP + S::NQ] = czero<double>();
+      }
+    }
+  }
 
   __device__ __forceinline__ cx<double> start(int64_t path, int i) const {
     int64_t k = path;

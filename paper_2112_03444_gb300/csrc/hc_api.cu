@@ -455,7 +455,7 @@ bool encode_dense(hc_problem* p, std::vector<int>& emap, std::vector<int>& dterm
     emap[k] = it->second * L + i;
     if (vars.empty()) {
       dterm.push_back(k);
-      dslot.push_back((n * MP + 0) * L + i);
+      dslot.push_back((int)hc::dense_slot(n, d, L, n, 0, i));
       dmult.push_back(1.0f);
       continue;
     }
@@ -473,7 +473,7 @@ bool encode_dense(hc_problem* p, std::vector<int>& emap, std::vector<int>& dterm
       }
       const int mp = graded_index(n, rest);
       dterm.push_back(k);
-      dslot.push_back((j * MP + mp) * L + i);
+      dslot.push_back((int)hc::dense_slot(n, d, L, j, mp, i));
       dmult.push_back((float)a);
     }
   }
@@ -482,7 +482,7 @@ bool encode_dense(hc_problem* p, std::vector<int>& emap, std::vector<int>& dterm
   p->M = M;
   p->MP = MP;
   p->L = L;
-  p->Dstride = (int64_t)(n + 1) * MP * L;
+  p->Dstride = (int64_t)(n + 1) * hc::dense_mpp(n, d) * L;
   p->Estride = (int64_t)M * L;
   int64_t paths = 1;
   for (int i = 0; i < n; ++i) paths *= d;

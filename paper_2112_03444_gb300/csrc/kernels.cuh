@@ -31,6 +31,25 @@ __host__ __device__ constexpr int block_smem_bytes(int L, int extra, int acc = 0
 // kBlock otherwise.
 inline int retrack_threads(int lanes) { return lanes == 32 ? 32 : kBlock; }
 
+// Dense coefficient tables D (see dense_td.cuh): per slice j (the partial
+// derivative dF_i/dx_j; slice n holds the constant term), the monomials of
+// degree < d are stored in pairs per lane, so that one 16-byte load brings
+// two FP32 coefficients.  The constant, the linear and the quadratic
+// monomials each start a new pair (each range padded to an even count).
+__host__ __device__ constexpr int dense_mpp(int n, int d) {  // padded monomials per slice
+  return 2 + (n + (n & 1)) + ((d == 3) ? (n * (n + 1) / 2 + ((n * (n + 1) / 2) & 1)) : 0);
+}
+// padded position of the monomial with graded index mp (0 constant, 1..n
+// linear, then the quadratic ones)
+__host__ __device__ constexpr int dense_mslot(int n, int mp) {
+  return mp == 0 ? 0 : (mp <= n ? 1 + mp : 2 + (n + (n & 1)) + (mp - 1 - n));
+}
+// entry of (slice j, monomial mp, row i) in an instance's table of lane stride L
+__host__ __device__ constexpr int64_t dense_slot(int n, int d, int L, int j, int mp, int i) {
+  return ((int64_t)(j * (dense_mpp(n, d) / 2) + (dense_mslot(n, mp) >> 1)) * L + i) * 2 +
+         (dense_mslot(n, mp) & 1);
+}
+
 // Work distribution of a tracking launch: work item = (instance, path),
 // item = instance * paths + path; a lane group takes the next item with one
 // atomicAdd on *queue (retire/refill: a group that finishes a path pulls the

@@ -140,7 +140,7 @@ __global__ void stage_canonical_kernel(int64_t n_inst, int n, int d, int M, int 
     const int g = unrank_graded(n, m, vars);
     E[inst * Es + (int64_t)nested_index(n, d, vars, g) * L + i] = c;
     if (g == 0) {
-      const int64_t slot = inst * Ds + (int64_t)(n * MP) * L + i;
+      const int64_t slot = inst * Ds + hc::dense_slot(n, d, L, n, 0, i);
       D64[slot] = c;
       D32[slot] = make_float2((float)c.x, (float)c.y);
       continue;
@@ -159,7 +159,7 @@ __global__ void stage_canonical_kernel(int64_t n_inst, int n, int d, int M, int 
         rest[nr++] = vars[q];
       }
       const int mp = rank_graded(n, rest, nr);
-      const int64_t slot = inst * Ds + (int64_t)(j * MP + mp) * L + i;
+      const int64_t slot = inst * Ds + hc::dense_slot(n, d, L, j, mp, i);
       const double2 v = make_double2(a * c.x, a * c.y);
       D64[slot] = v;
       D32[slot] = make_float2((float)v.x, (float)v.y);
@@ -199,7 +199,7 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
   int64_t paths = 1;
   for (int i = 0; i < n; ++i) paths *= degree;
   const int64_t items = (int64_t)n_instances * paths;
-  const int64_t Es = (int64_t)M * L, Ds = (int64_t)(n + 1) * MP * L;
+  const int64_t Es = (int64_t)M * L, Ds = (int64_t)(n + 1) * hc::dense_mpp(n, degree) * L;
 
   // scratch layout
   const size_t ctl_b = align256(sizeof(unsigned long long) * 16);
