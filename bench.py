@@ -270,9 +270,16 @@ def run_gpu(args):
         finite += int(per.sum())
     recovery = finite / total_paths
 
-    # ---- dominant kernel roofline: the largest class's tracking launch timed
-    # alone (inside the step the five classes overlap on the device)
-    dom = max(range(len(wl)), key=lambda i: last[i]["track_ms"])
+    # ---- dominant kernel roofline: the tracking launch of the class with the
+    # most algorithmic work in the timed step (from its device step
+    # counters), timed alone (inside the step the five classes overlap, so a
+    # launch's wall time there includes waiting for SM slots)
+    def class_flops(i):
+        r = last[i]
+        return flops(wl[i]["n"], wl[i]["d"],
+                     r["steps_accepted"] + r["steps_rejected"] - r["esc_accepted"] - r["esc_rejected"],
+                     r["newton_iters"] - r["esc_newton"])
+    dom = max(range(len(wl)), key=class_flops)
     dw, dpr, db = wl[dom], problems[dom], bufs[dom]
     dk_ms, dflop = [], []
     for _ in range(3):
