@@ -325,8 +325,11 @@ void pinned_slot_put(void* q) {
 // High-priority streams for the re-tracking launches (a few per device,
 // round-robin): when block slots free up they go to these small launches
 // before the pending blocks of other, normal-priority persistent launches.
+// High-priority streams for the re-tracking branch of hc_track_batch, handed
+// out round-robin: enough of them that concurrent batches (several classes,
+// the server's slots) rarely queue one batch's re-tracking behind another's.
 cudaStream_t retrack_stream(int device) {
-  constexpr int kPerDevice = 4, kMaxDev = 64;
+  constexpr int kPerDevice = 16, kMaxDev = 64;
   static std::mutex mu;
   static cudaStream_t streams[kMaxDev][kPerDevice] = {};
   static int next[kMaxDev] = {};
