@@ -322,11 +322,10 @@ void pinned_slot_put(void* q) {
   pp.free_slots.push_back(q);
 }
 
-// High-priority streams for the re-tracking launches (a few per device,
-// round-robin): when block slots free up they go to these small launches
-// before the pending blocks of other, normal-priority persistent launches.
 // High-priority streams for the re-tracking branch of hc_track_batch, handed
-// out round-robin: enough of them that concurrent batches (several classes,
+// out round-robin: when block slots free up they go to these small launches
+// before the pending blocks of other, normal-priority persistent launches,
+// and there are enough of them that concurrent batches (several classes,
 // the server's slots) rarely queue one batch's re-tracking behind another's.
 cudaStream_t retrack_stream(int device) {
   constexpr int kPerDevice = 16, kMaxDev = 64;
