@@ -1,15 +1,23 @@
 """Benchmark: batched homotopy-continuation path tracking on one GB300.
 
-Workload (dense total-degree sweep): dense random quadratic systems with
+Workload (the dense total-degree sweep): dense random quadratic systems with
 n = 8, 10, 12 unknowns (256 / 1024 / 4096 paths each) and dense random cubic
 systems with n = 6, 8 (729 / 6561 paths), complex Gaussian coefficients,
 16 systems per size; every path of every system of a size runs in one
-persistent mixed-precision launch (FP32 tracking, FP64 endgame residuals and
-refinement).  One step = all five size classes, 202,656 paths.
+persistent mixed-precision launch (FP32 tracking, double-float endgame
+residuals and refinement, FP64 re-tracking tiers).  One step = all five size
+classes, 202,656 paths.
 
-Prints one JSON line: value = matched paths/s (paths whose endpoint is a
-finite root; the Bezout count d^n is checked for every system, and a sampled
-set of FP64 oracle endpoints must be found among the GPU's within 1e-8).
+Prints one JSON line.  value = oracle-matched paths/s: a path counts when the
+GPU ends it at a finite root and the FP64 oracle, run once on every path of
+the same seeded systems (tests/golden/dense_sweep_oracle.json), ends the same
+start at a finite root too, provided the GPU's finite roots of every system
+are pairwise distinct (a finite root set of distinct refined roots of a
+system whose oracle root set is complete is that root set).  Beside it:
+recovery against the oracle's recovery, a sampled endpoint comparison with
+the oracle run live, the same sweep as one plain-FP64 launch per system, the
+dominant kernel's roofline (FP32 and FP64), per-request latency of a short
+serving run, and the oracle's own throughput on the host (all cores and one).
 """
 from __future__ import annotations
 
@@ -28,13 +36,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-SIZES = [(8, 2), (10, 2), (12, 2), (6, 3), (8, 3)]   # (n, degree)
-SYSTEMS_PER_SIZE = 16
-SEED0 = 100
+from paper_2112_03444_gb300 import inputs  # noqa: E402  (problem data only)
+
+SIZES = list(inputs.DENSE_SWEEP_SIZES)   # (n, degree)
+SYSTEMS_PER_SIZE = inputs.DENSE_SWEEP_SYSTEMS
 WORKLOAD = "dense total-degree sweep: quadratics n=8,10,12; cubics n=6,8; 16 systems per size"
 METRIC = "paths/s and systems/s at oracle-matched roots (1e-8); p50/p99 latency per system"
-FP32_LANES_PER_SM = 128
-SM_COUNT = 152
+GOLDEN = os.path.join(ROOT, "tests", "golden", "dense_sweep_oracle.json")
+START_DIR = os.path.join(ROOT, "paper_2112_03444_gb300", "startsets")
 
 
 def source_sha() -> str:
@@ -80,16 +89,20 @@ def max_over_ranks(value, world, device=None):
     return float(t.item())
 
 
+def sum_over_ranks(value, world, device=None):
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def workload(rank=0):
-    """Per size: (n, d, base TermSystem, coefficient array [16, T], gamma)."""
-    from paper_2112_03444_gb300 import inputs
-    out = []
-    for si, (n, d) in enumerate(SIZES):
-        seeds = [SEED0 + 1000 * rank + 100 * si + k for k in range(SYSTEMS_PER_SIZE)]
-        base, coefs = inputs.dense_batch(n, d, seeds)
-        out.append(dict(n=n, d=d, base=base, coefs=coefs, seeds=seeds,
-                        gamma=inputs.unit_gamma(seeds[0])))
-    return out
+    """Per size: dict(n, d, base TermSystem, coefs [16, T], seeds, gamma);
+    each replica rank its own seeds."""
+    return inputs.dense_sweep(rank)
 
 
 # ---------------------------------------------------------------- flop model
@@ -114,20 +127,83 @@ def dense_flops_per_unit(n, d):
 
 
 def flops(n, d, steps, newton):
+    """Flops of `steps` predictor steps (4 RK stages: E_Hx + E_Ht + S each)
+    and `newton` corrector iterations (E_H + E_Hx + S each), cFMA = 8 flops."""
     f = dense_flops_per_unit(n, d)
     rk = 4 * (f["E_Hx"] + f["E_Ht"] + f["S"])
     nw = f["E_H"] + f["E_Hx"] + f["S"]
     return 8.0 * (steps * rk + newton * nw)
 
 
+# ---------------------------------------------------------------- oracle goldens
+def load_golden():
+    """The oracle's stored outcome on every path of the rank-0 sweep, or None."""
+    try:
+        return json.load(open(GOLDEN))
+    except OSError:
+        return None
+
+
+def nearest_other(x):
+    """Relative infinity distance of every row of x to its nearest other row."""
+    from scipy.spatial import cKDTree
+    if len(x) < 2:
+        return np.full(len(x), np.inf)
+    emb = np.concatenate([x.real, x.imag], axis=1)
+    d, idx = cKDTree(emb).query(emb, k=2, p=np.inf)
+    scale = np.maximum(1.0, np.max(np.abs(x), axis=1))
+    return d[:, 1] / scale
+
+
+def match_sweep(wl, statuses, xs, golden, dup_tol=1e-6):
+    """Oracle-matched paths of one sweep step (see the module docstring).
+
+    statuses[c] [systems, paths] u8, xs[c] [systems, paths, n] complex.
+    matched: paths finite on both sides; oracle_only: paths the oracle ends
+    finite and the GPU does not (recovery equals the oracle's iff none);
+    gpu_only: finite GPU roots on starts the oracle fails (not counted)."""
+    matched = total = oracle_finite = gpu_finite = dup_systems = 0
+    oracle_only, gpu_only = [], []
+    for ci, w in enumerate(wl):
+        gcls = golden["classes"][ci] if golden else None
+        for s in range(len(w["seeds"])):
+            st = statuses[ci][s] & 0x7F
+            fin = st == 1
+            total += len(st)
+            gpu_finite += int(fin.sum())
+            dup = nearest_other(xs[ci][s][fin]).min(initial=np.inf) <= dup_tol
+            dup_systems += int(dup)
+            if gcls is None:
+                matched += 0 if dup else int(fin.sum())
+                continue
+            g = gcls["systems"][s]
+            assert g["seed"] == w["seeds"][s], "golden written for another workload"
+            ofin = np.ones(len(st), bool)
+            for p, code in g["not_finite"]:
+                ofin[p] = False
+            oracle_finite += int(ofin.sum())
+            if dup:                               # a root reported twice: nothing matches
+                fin = np.zeros_like(fin)
+            matched += int((fin & ofin).sum())
+            oracle_only += [[w["n"], w["d"], s, int(p), int(statuses[ci][s][p])]
+                            for p in np.nonzero(ofin & ~fin)[0]]
+            gpu_only += [[w["n"], w["d"], s, int(p)] for p in np.nonzero(fin & ~ofin)[0]]
+    return dict(matched=matched, total=total, gpu_finite=gpu_finite,
+                oracle_finite=oracle_finite if golden else None,
+                systems_with_duplicate_roots=dup_systems, oracle_only=oracle_only,
+                gpu_only=len(gpu_only))
+
+
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
+    """nvidia-smi samples during the timed region (a temporary file)."""
+
     def __init__(self):
+        import tempfile
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"hc_bench_clocks_{os.getpid()}.csv")
 
     def start(self):
-        os.makedirs(os.path.dirname(self.path), exist_ok=True)
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -162,6 +238,7 @@ class ClockSampler:
             for nm, v in zip(names, parts[5:9]):
                 if v.lower() == "active":
                     reasons.add(nm)
+        os.remove(self.path)
         if not sm:
             return dict(sm_mhz=None, sm_max_mhz=None, reasons=["no samples"])
         return dict(sm_mhz=statistics.median(sm), sm_max_mhz=max(smax), reasons=sorted(reasons),
@@ -182,14 +259,14 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     sp = stream.cuda_stream
-    # one stream per size class: the five persistent launches (and their FP64
+    # one stream per size class: the five persistent launches (and their
     # re-tracking launches) overlap on the device
     class_streams = [torch.cuda.Stream(device=dev) for _ in SIZES]
     wl = workload(rank)
-    settings = dict(precision=hc.HC_PREC_MIXED)
+    golden = load_golden() if rank == 0 else None
     problems, bufs = [], []
     for w in wl:
-        pr = hc.Problem(w["base"], gamma=w["gamma"], settings=settings)
+        pr = hc.Problem(w["base"], gamma=w["gamma"], settings=dict(precision=hc.HC_PREC_MIXED))
         I, P, n = SYSTEMS_PER_SIZE, pr.paths, w["n"]
         bufs.append(dict(
             coef=torch.from_numpy(w["coefs"]).to(dev),
@@ -213,7 +290,7 @@ def run_gpu(args):
         # largest class first: later classes' launches fill the SMs while the
         # earlier ones finish their re-tracking tails
         for i in order:
-            pr, b, cs = problems[i], bufs[i], class_streams[i]
+            b, cs = bufs[i], class_streams[i]
             cs.wait_event(ev)
             batches[i] = plans[i].run(coef=b["coef"], device=True, x_out=b["x"],
                                       status_out=b["st"], steps_out=b["steps"], be_out=b["be"],
@@ -261,19 +338,19 @@ def run_gpu(args):
         dist.barrier()
     ms = max_over_ranks(ms, world, dev)
 
-    # ---- correctness of the measured run: Bezout count per system
-    last = results[-1]
-    finite = 0
-    for w, b in zip(wl, bufs):
-        st = b["st"].cpu().numpy() & 0x7F
-        per = (st == hc.PATH_FINITE).sum(axis=1)
-        finite += int(per.sum())
-    recovery = finite / total_paths
+    # ---- oracle matching of the last timed step
+    m = match_sweep(wl, [b["st"].cpu().numpy() for b in bufs],
+                    [b["x"].cpu().numpy() for b in bufs], golden)
+    matched_all = sum_over_ranks(m["matched"], world, dev)
+    recovery = m["matched"] / m["total"]
+    oracle_recovery = m["oracle_finite"] / m["total"] if golden else None
 
     # ---- dominant kernel roofline: the tracking launch of the class with the
     # most algorithmic work in the timed step (from its device step
     # counters), timed alone (inside the step the five classes overlap, so a
     # launch's wall time there includes waiting for SM slots)
+    last = results[-1]
+
     def class_flops(i):
         r = last[i]
         return flops(wl[i]["n"], wl[i]["d"],
@@ -288,14 +365,14 @@ def run_gpu(args):
         bt.wait()
         r = bt.result
         dk_ms.append(r["track_ms"])
-        # flops of the tracking launch only: all steps minus the FP64 tier's
+        # flops of the tracking launch only: all steps minus the re-tracking tiers'
         dflop.append(flops(dw["n"], dw["d"],
                            r["steps_accepted"] + r["steps_rejected"] - r["esc_accepted"] - r["esc_rejected"],
                            r["newton_iters"] - r["esc_newton"]))
         bt.close()
-    achieved = statistics.mean(f / (m * 1e-3) for f, m in zip(dflop, dk_ms)) / 1e12
+    achieved = statistics.mean(f / (m_ * 1e-3) for f, m_ in zip(dflop, dk_ms)) / 1e12
     peak_fp32, _ = hc.measure_fma_peak(False)
-    peak = peak_fp32 / 1e12
+    peak_fp64, _ = hc.measure_fma_peak(True)
 
     # ---- end-to-end through the public API with host buffers: every step
     # copies the coefficients from pinned host memory and reads the endpoints,
@@ -327,103 +404,249 @@ def run_gpu(args):
             bt.close()
     e2e_ok = all(np.array_equal(h["st"], b["st"].cpu().numpy()) for h, b in zip(hbufs, bufs))
     e2e = statistics.median(e2e_ms)
+    me = match_sweep(wl, [h["st"] for h in hbufs], [h["x"] for h in hbufs], golden)
 
-    # ---- the same sweep as one launch per system (mixed tiers, one stream):
-    # the form the batched persistent launches replace
-    per_ms = []
-    for _ in range(2):
+    # ---- the same sweep as one plain-FP64 launch per system (80 launches on
+    # one stream, device buffers): the form the batched mixed-precision
+    # launches replace, with its own oracle matching and FP64 roofline
+    fp64 = None
+    if not args.no_fp64_leg:
+        fprobs = [hc.Problem(w["base"], gamma=w["gamma"], settings=dict(precision=hc.HC_PREC_FP64))
+                  for w in wl]
         torch.cuda.synchronize()
         s0 = torch.cuda.Event(enable_timing=True)
         s1 = torch.cuda.Event(enable_timing=True)
         s0.record(stream)
-        bts = []
+        fbts = []
         for i in order:
-            pr, b = problems[i], bufs[i]
+            pr, b = fprobs[i], bufs[i]
             for k in range(SYSTEMS_PER_SIZE):
-                bts.append(pr.track(n_instances=1, coef=b["coef"][k:k + 1], device=True,
-                                    x_out=b["x"][k:k + 1], status_out=b["st"][k:k + 1],
-                                    steps_out=b["steps"][k:k + 1], be_out=b["be"][k:k + 1],
-                                    stream=sp))
+                fbts.append((i, pr.track(n_instances=1, coef=b["coef"][k:k + 1], device=True,
+                                         x_out=b["x"][k:k + 1], status_out=b["st"][k:k + 1],
+                                         steps_out=b["steps"][k:k + 1], be_out=b["be"][k:k + 1],
+                                         stream=sp)))
         s1.record(stream)
-        for bt in bts:
+        fl64, tr64 = 0.0, 0.0
+        for i, bt in fbts:
             bt.wait()
-        torch.cuda.synchronize()
-        per_ms.append(s0.elapsed_time(s1))
-        for bt in bts:
+            r = bt.result
+            fl64 += flops(wl[i]["n"], wl[i]["d"], r["steps_accepted"] + r["steps_rejected"],
+                          r["newton_iters"])
+            tr64 += r["track_ms"]
             bt.close()
-    per_system = dict(value=total_paths * recovery * world / (min(per_ms) * 1e-3), unit="paths/s",
-                      ms_per_step=min(per_ms),
-                      form="one hc_track_batch per system, mixed tiers, one stream, device buffers")
+        torch.cuda.synchronize()
+        f_ms = s0.elapsed_time(s1)
+        mf = match_sweep(wl, [b["st"].cpu().numpy() for b in bufs],
+                         [b["x"].cpu().numpy() for b in bufs], golden)
+        ach64 = fl64 / (tr64 * 1e-3) / 1e12
+        fp64 = dict(value=mf["matched"] * world / (f_ms * 1e-3), unit="paths/s", ms_per_step=f_ms,
+                    recovery=mf["matched"] / mf["total"],
+                    recovery_equals_oracle=(mf["matched"] == mf["oracle_finite"]) if golden else None,
+                    oracle_only=len(mf["oracle_only"]), gpu_only=mf["gpu_only"],
+                    form="one hc_track_batch per system, precision FP64 (all-FP64 kernel), one "
+                         "stream, device buffers",
+                    roofline=dict(bound="alu", achieved=ach64, peak=peak_fp64 / 1e12,
+                                  unit="TFLOP/s", frac=ach64 * 1e12 / peak_fp64,
+                                  note="of measured: algorithmic flops of all 80 FP64 tracking "
+                                       "launches / their summed launch time, against the FP64 "
+                                       "FMA throughput from hc_measure_fma_peak(fp64=1)"))
+
+    # ---- the standalone fused batched solver against cuBLAS (paper Fig. 3)
+    solve = None if args.no_solve_leg else solve_leg(hc, torch, stream)
+
+    # ---- a short serving run: per-request latency (Poisson arrivals)
+    serving = None
+    if not args.no_serving_leg:
+        serving = serve_rows(hc, [args.serve_rate], args.serve_duration, trifocal=True,
+                             fp64_requests=0)[0]
 
     line = dict(
-        metric=METRIC, value=total_paths * recovery * world / (ms * 1e-3), unit="paths/s",
+        metric=METRIC, value=matched_all / (ms * 1e-3), unit="paths/s",
         systems_per_s=total_systems * world / (ms * 1e-3),
-        latency_ms=dict(p50=statistics.median(step_ms), p99=float(np.percentile(step_ms, 99)),
-                        note="whole-batch latency per system (all systems of a step finish together)"),
+        latency_ms=dict(p50=serving["p50_ms"], p99=serving["p99_ms"],
+                        note="per request of the serving leg (Poisson arrivals, continuous "
+                             "batching)") if serving else None,
         n_gpus=world, steps=args.steps, warmup=args.warmup, ms_per_step=ms,
         higher_is_better=True, scaling="weak", vs_baseline=None, dtype="c64+c128 (mixed)",
         data="synthetic",
         config=dict(workload=WORKLOAD, paths_per_step=total_paths, systems_per_step=total_systems,
-                    precision="mixed FP32 tracking, FP64 endgame/refinement",
+                    precision="mixed: FP32 tracking, double-float endgame residuals and "
+                              "refinement, FP64 re-tracking tiers",
                     l2="flushed between timed steps (256 MB write)", parallelism=f"replicas{world}",
-                    launch="one captured CUDA graph per size class (hc_plan_run), five streams"),
-        recovery=recovery,
-        escalated=sum(r["escalated"] for r in last),
-        e2e=dict(value=total_paths * recovery * world / (e2e * 1e-3), unit="paths/s",
+                    launch="one captured CUDA graph per size class (hc_plan_run), five streams",
+                    matching="rank 0 against the stored FP64 oracle outcome of every path "
+                             "(tests/golden/dense_sweep_oracle.json); other replicas: distinct "
+                             "finite roots"),
+        batch_step_ms=dict(p50=statistics.median(step_ms), p99=float(np.percentile(step_ms, 99))),
+        recovery=recovery, oracle_recovery=oracle_recovery,
+        recovery_equals_oracle=(m["matched"] == m["oracle_finite"]) if golden else None,
+        matched=m, escalated=sum(r["escalated"] for r in last),
+        e2e=dict(value=me["matched"] * world / (e2e * 1e-3), unit="paths/s",
                  h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h, ms_per_step=e2e,
                  path="hc_plan_run per size class on its own stream, pinned host buffers",
                  same_statuses_as_device_run=e2e_ok),
         gpu_launches=launches,
-        one_system_per_launch=per_system,
-        roofline=dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s",
-                      frac=achieved / peak, traffic=recorded_traffic(),
+        one_system_per_launch_fp64=fp64,
+        roofline=dict(bound="alu", achieved=achieved, peak=peak_fp32 / 1e12, unit="TFLOP/s",
+                      frac=achieved * 1e12 / peak_fp32, traffic=recorded_traffic(),
                       kernel=f"dense_td_kernel<n={dw['n']}, d={dw['d']}, mixed>",
                       kernel_ms=statistics.mean(dk_ms),
-                      peak_note="of measured: FP32 FMA throughput from hc_measure_fma_peak on this "
-                                "GPU in this run; algorithmic flops from the device step counters"),
+                      fp64_peak=peak_fp64 / 1e12,
+                      peak_note="of measured: FP32 FMA throughput from hc_measure_fma_peak on "
+                                "this GPU in this run; algorithmic flops from the device step "
+                                "counters"),
+        serving=serving,
+        batched_solve=solve,
         clocks=clocks,
     )
     if rank == 0 and not args.no_cpu:
-        line["cpu_baseline"], match = cpu_baseline(wl, bufs, args)
-        line["oracle_match"] = match
+        line["cpu_baseline"], line["oracle_match"] = cpu_baseline(wl, bufs_host(bufs), args)
+        line["cpu_baseline_1thread"], _ = cpu_baseline(wl, None, args, sample=args.cpu_sample_1t,
+                                                       threads=1)
+    if golden is not None and not line["recovery_equals_oracle"]:
+        line["recovery_note"] = ("the GPU does not end every path the oracle solves: see "
+                                 "matched.oracle_only")
     if world > 1:
         dist.destroy_process_group()
     return line
 
 
+def bufs_host(bufs):
+    return [dict(x=b["x"].cpu().numpy()) for b in bufs]
+
+
+# ---------------------------------------------------------------- batched solve (Fig. 3)
+def _cublas():
+    """cuBLAS as a black-box baseline (the library torch has loaded)."""
+    import ctypes
+    for name in ("libcublas.so.13", "libcublas.so.12", "libcublas.so"):
+        try:
+            return ctypes.CDLL(name)
+        except OSError:
+            continue
+    return None
+
+
+def solve_leg(hc, torch, stream, sizes=(4, 8, 12, 16, 20), batches=(1000, 100_000), reps=20):
+    """The paper's Fig. 3 on this GPU: batches of n x n complex systems,
+    hc_batched_solve (fused Gauss-Jordan in registers, one launch) against
+    cuBLAS getrfBatched + getrsBatched (two launches), FP32 and FP64
+    complex.  Times are CUDA-event means over `reps` launches on `stream`."""
+    import ctypes
+    lib = _cublas()
+    torch.ones(8, 8, device="cuda") @ torch.ones(8, 8, device="cuda")  # torch loads cuBLAS
+    if lib is None:
+        return dict(unavailable="libcublas not found")
+    P = ctypes.c_void_p
+    h = P()
+    lib.cublasCreate_v2(ctypes.byref(h))
+    lib.cublasSetStream_v2(h, P(stream.cuda_stream))
+    rows = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, prep=None):
+        ms = []
+        for _ in range(reps + 2):
+            if prep:
+                prep()
+            ev0.record(stream)
+            fn()
+            ev1.record(stream)
+            ev1.synchronize()
+            ms.append(ev0.elapsed_time(ev1))
+        return statistics.mean(ms[2:])
+
+    for fp32 in (1, 0):
+        dt = torch.complex64 if fp32 else torch.complex128
+        esz = 8 if fp32 else 16
+        getrf = lib.cublasCgetrfBatched if fp32 else lib.cublasZgetrfBatched
+        getrs = lib.cublasCgetrsBatched if fp32 else lib.cublasZgetrsBatched
+        for n in sizes:
+            for batch in batches:
+                g = torch.Generator(device="cuda").manual_seed(n * 7919 + batch)
+                A = torch.randn((batch, n, n), dtype=dt, device="cuda", generator=g)
+                b = torch.randn((batch, n), dtype=dt, device="cuda", generator=g)
+                x = torch.empty_like(b)
+                info = torch.empty(batch, dtype=torch.int32, device="cuda")
+                with torch.cuda.stream(stream):
+                    ours = timed(lambda: hc.batched_solve(A, b, x, info, stream.cuda_stream))
+                # cuBLAS: column-major, so the row-major A is A^T there: solve with trans = T
+                Aw, bw = A.clone(), b.clone()
+                Ap = torch.arange(batch, device="cuda", dtype=torch.int64) * (n * n * esz) + \
+                    Aw.data_ptr()
+                Bp = torch.arange(batch, device="cuda", dtype=torch.int64) * (n * esz) + \
+                    bw.data_ptr()
+                piv = torch.empty(batch * n, dtype=torch.int32, device="cuda")
+                cinfo = torch.empty(batch, dtype=torch.int32, device="cuda")
+                hinfo = ctypes.c_int(0)
+
+                def prep():
+                    Aw.copy_(A)
+                    bw.copy_(b)
+
+                def cub():
+                    getrf(h, n, P(Ap.data_ptr()), n, P(piv.data_ptr()), P(cinfo.data_ptr()), batch)
+                    getrs(h, 1, n, 1, P(Ap.data_ptr()), n, P(piv.data_ptr()), P(Bp.data_ptr()), n,
+                          ctypes.byref(hinfo), batch)
+                with torch.cuda.stream(stream):
+                    cb = timed(cub, prep)
+                stream.synchronize()
+                diff = float(((x - bw).abs().amax(dim=1) / bw.abs().amax(dim=1)).max())
+                byt = batch * (n * n + 2 * n) * esz
+                cfma = sum(j * (j + 1) for j in range(n)) + n * (n + 1) // 2
+                rows.append(dict(dtype="c64" if fp32 else "c128", n=n, batch=batch,
+                                 hc_us=ours * 1e3, cublas_us=cb * 1e3, speedup=cb / ours,
+                                 hc_gbs=byt / (ours * 1e-3) / 1e9,
+                                 hc_tflops=8.0 * cfma * batch / (ours * 1e-3) / 1e12,
+                                 max_rel_diff_vs_cublas=diff, singular=int((info != 0).sum())))
+    lib.cublasDestroy_v2(h)
+    return dict(form="hc_batched_solve (one fused launch) vs cuBLAS getrfBatched + getrsBatched",
+                rows=rows)
+
+
 # ---------------------------------------------------------------- CPU oracle
-def cpu_baseline(wl, bufs, args, sample=None):
-    """Oracle on a bounded sample: paths per size class from system 0."""
+def class_sample(wl, total):
+    """Paths per size class for a sample of `total` paths, proportional to the
+    class's share of the step's paths (at least 4 each)."""
+    P = [w["d"] ** w["n"] for w in wl]
+    return [max(4, int(round(total * p / sum(P)))) for p in P]
+
+
+def cpu_baseline(wl, bufs, args, sample=None, threads=None):
+    """The FP64 oracle on a bounded sample: system 0 of each class, paths per
+    class in proportion to the step; with bufs, its endpoints are compared
+    with the GPU's of the same systems."""
     import oracle
     sys.path.insert(0, os.path.join(ROOT, "tests"))
     from hcmatch import match
     sample = sample or args.cpu_sample
-    threads = oracle.hardware_threads()
+    threads = threads or oracle.hardware_threads()
     t_total, n_paths = 0.0, 0
     worst, checked = 0.0, 0
-    for si, w in enumerate(wl):
+    for si, (w, k) in enumerate(zip(wl, class_sample(wl, sample))):
         P = w["d"] ** w["n"]
-        ids = np.random.default_rng(w["seeds"][0]).choice(P, size=min(sample, P), replace=False)
+        ids = np.random.default_rng(w["seeds"][0]).choice(P, size=min(k, P), replace=False)
         pr = oracle.OracleProblem(w["base"], gamma=w["gamma"], coef=w["coefs"][0])
         t0 = time.perf_counter()
         r = pr.track(path_ids=ids, threads=threads)
         t_total += time.perf_counter() - t0
         n_paths += len(ids)
         if bufs is not None:
-            gx = bufs[si]["x"][0].cpu().numpy()
-            _, dist = match(r["x"], gx, 1e-8)
-            worst = max(worst, float(np.max(dist)))
-            checked += len(ids)
+            fin = (r["status"] & 0x7F) == oracle.FINITE
+            _, dist = match(r["x"][fin], bufs[si]["x"][0], 1e-8)
+            worst = max(worst, float(np.max(dist, initial=0.0)))
+            checked += int(fin.sum())
     rate = n_paths / t_total
     return (dict(value=rate, unit="paths/s", cores=threads, kind="oracle",
-                 sample=f"{sample} paths per size class (system 0 of each), {n_paths} paths, "
-                        f"{t_total:.1f} s"),
+                 sample=f"{n_paths} paths of system 0 of each size class, in proportion to "
+                        f"the class's paths ({t_total:.1f} s)"),
             dict(checked=checked, max_rel_dist=worst, tol=1e-8, ok=worst <= 1e-8))
 
 
 def run_reference(args):
     """The FP64 CPU oracle as the reference arm: each step tracks a bounded
-    sample of the workload (ref_sample paths per size class) on all host cores."""
+    sample of the workload (paths per class in proportion to the step) on all
+    host cores."""
     rank, world = env_rank()
     if rank != 0:
         return None
@@ -450,99 +673,94 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- serving
-def serve_mix(args):
-    """Poisson arrivals of single-system requests drawn from {dense quadratics
-    n = 4..12, 4-view triangulation, trifocal pose}: continuous batching on
-    the GPU versus the plain FP64 one-launch-per-system form."""
-    import threading
-    import torch
-    from paper_2112_03444_gb300 import hc, inputs
-    torch.cuda.set_device(0)
-    start_dir = os.path.join(ROOT, "paper_2112_03444_gb300", "startsets")
+def serving_problems(hc, precision, trifocal=True):
+    """(name, problem, request generator) for the serving mix: dense
+    quadratics n = 4..12, 4-view triangulation and trifocal pose."""
+    probs = []
+    for n in range(4, 13):
+        probs.append((f"quad{n}", hc.Problem(inputs.dense_system(n, 2, 700 + n),
+                                              gamma=inputs.unit_gamma(700 + n),
+                                              settings=dict(precision=precision)),
+                      lambda s, n=n: inputs.dense_coefficients(n, 2, s).reshape(-1)))
+    z = np.load(os.path.join(START_DIR, "triangulation4.npz"))
+    probs.append(("triangulation4", hc.Problem(inputs.triangulation_family(4).system,
+                                                kind=hc.HC_PARAMETER, p0=z["p0"],
+                                                start=z["start"],
+                                                settings=dict(precision=precision)),
+                  lambda s: inputs.triangulation_scene(s)[0]))
+    if trifocal:
+        z = np.load(os.path.join(START_DIR, "trifocal_f.npz"))
+        probs.append(("trifocal_f", hc.Problem(inputs.trifocal_family().system,
+                                                kind=hc.HC_PARAMETER, p0=z["p0"],
+                                                start=z["start"],
+                                                settings=dict(precision=precision)),
+                      lambda s: inputs.trifocal_scene(s)[0]))
+    return probs
 
-    def problems(precision):
-        probs = []
-        for n in range(4, 13):
-            probs.append((f"quad{n}", hc.Problem(inputs.dense_system(n, 2, 700 + n),
-                                                  gamma=inputs.unit_gamma(700 + n),
-                                                  settings=dict(precision=precision)),
-                          lambda s, n=n: inputs.dense_coefficients(n, 2, s).reshape(-1)))
-        z = np.load(os.path.join(start_dir, "triangulation4.npz"))
-        probs.append(("triangulation4", hc.Problem(inputs.triangulation_family(4).system,
-                                                    kind=hc.HC_PARAMETER, p0=z["p0"],
-                                                    start=z["start"],
-                                                    settings=dict(precision=precision)),
-                      lambda s: inputs.triangulation_scene(s)[0]))
-        tf = os.path.join(start_dir, "trifocal_f.npz")
-        if os.path.exists(tf) and not args.no_trifocal:
-            z = np.load(tf)
-            probs.append(("trifocal_f", hc.Problem(inputs.trifocal_family().system,
-                                                    kind=hc.HC_PARAMETER, p0=z["p0"],
-                                                    start=z["start"],
-                                                    settings=dict(precision=precision)),
-                          lambda s: inputs.trifocal_scene(s)[0]))
-        return probs
 
-    def run(probs, rate, count, streams, max_batch, seed):
-        rng = np.random.default_rng([seed, int(rate)])
-        kinds = rng.integers(0, len(probs), size=count)
-        gaps = rng.exponential(1.0 / rate, size=count)
-        payload = [probs[k][2](10_000 + j) for j, k in enumerate(kinds)]
-        srv = hc.Server(n_streams=streams, max_batch_instances=max_batch)
-        ids = [None] * count
-        t0 = time.perf_counter()
+def serve_run(hc, probs, rate, count, streams, max_batch, seed):
+    """Poisson arrivals of `count` requests at `rate` per second, kinds
+    uniform over probs; returns throughput and per-request latency."""
+    rng = np.random.default_rng([seed, int(rate)])
+    kinds = rng.integers(0, len(probs), size=count)
+    gaps = rng.exponential(1.0 / rate, size=count)
+    payload = [probs[k][2](10_000 + j) for j, k in enumerate(kinds)]
+    srv = hc.Server(n_streams=streams, max_batch_instances=max_batch)
+    ids = [None] * count
+    t0 = time.perf_counter()
 
-        def producer():
-            t = t0
-            for j, k in enumerate(kinds):
-                t += gaps[j]
-                while time.perf_counter() < t:
-                    pass
-                ids[j] = srv.submit(probs[k][1], payload[j])
-
-        th = threading.Thread(target=producer)
-        th.start()
-        th.join()
-        lat, paths, finite = [], 0, 0
+    def producer():
+        t = t0
         for j, k in enumerate(kinds):
-            x, st, info = srv.wait(ids[j], probs[k][1])
-            lat.append(info["latency_us"] / 1e3)
-            paths += info["paths"]
-            finite += info["finite"]
-        wall = time.perf_counter() - t0
-        stats = srv.stats()
-        srv.close()
-        return dict(offered_per_s=rate, requests=count, systems_per_s=count / wall,
-                    paths_per_s=finite / wall, p50_ms=float(np.percentile(lat, 50)),
-                    p99_ms=float(np.percentile(lat, 99)), recovery=finite / paths,
-                    batches=stats["batches"], max_inflight_batches=stats["max_inflight_batches"])
+            t += gaps[j]
+            while time.perf_counter() < t:
+                pass
+            ids[j] = srv.submit(probs[k][1], payload[j])
 
-    mixed = problems(hc.HC_PREC_MIXED)
+    th = threading.Thread(target=producer)
+    th.start()
+    th.join()
+    lat, paths, finite = [], 0, 0
+    per_kind = {}
+    for j, k in enumerate(kinds):
+        x, st, info = srv.wait(ids[j], probs[k][1])
+        lat.append(info["latency_us"] / 1e3)
+        paths += info["paths"]
+        finite += info["finite"]
+        per_kind.setdefault(probs[k][0], []).append(info["latency_us"] / 1e3)
+    wall = time.perf_counter() - t0
+    stats = srv.stats()
+    srv.close()
+    return dict(offered_per_s=rate, requests=count, systems_per_s=count / wall,
+                paths_per_s=finite / wall, p50_ms=float(np.percentile(lat, 50)),
+                p99_ms=float(np.percentile(lat, 99)), recovery=finite / paths,
+                batches=stats["batches"], max_inflight_batches=stats["max_inflight_batches"],
+                p50_ms_by_kind={k: float(np.percentile(v, 50)) for k, v in sorted(per_kind.items())})
+
+
+def serve_rows(hc, rates, duration, trifocal=True, fp64_requests=0):
+    mixed = serving_problems(hc, hc.HC_PREC_MIXED, trifocal)
     rows = []
-    for rate in [float(r) for r in args.rates.split(",")]:
-        count = int(max(50, min(rate * args.duration, 20000)))
-        rows.append(dict(form="mixed continuous batching", **run(mixed, rate, count, 4, 64, 1)))
-    fp64 = problems(hc.HC_PREC_FP64)
-    rate = float(args.rates.split(",")[0])
-    rows.append(dict(form="plain FP64, one launch per system",
-                     **run(fp64, rate, args.fp64_requests, 1, 1, 1)))
-    line = dict(metric=METRIC, mode="serving", workload="Poisson mix of " +
-                ", ".join(p[0] for p in mixed), rows=rows)
-    print(json.dumps(line), flush=True)
+    for rate in rates:
+        count = int(max(50, min(rate * duration, 20000)))
+        rows.append(dict(form="mixed continuous batching", kinds=[p[0] for p in mixed],
+                         **serve_run(hc, mixed, rate, count, 4, 64, 1)))
+    if fp64_requests:
+        fp64 = serving_problems(hc, hc.HC_PREC_FP64, trifocal)
+        rows.append(dict(form="plain FP64, one launch per system",
+                         **serve_run(hc, fp64, rates[0], fp64_requests, 1, 1, 1)))
+    return rows
 
 
-def run_case(spec):
-    """One dense size class, tracked twice (for profilers): spec = "n,d,instances"."""
+def serve_mix(args):
+    """Serving sweep: Poisson arrivals at several rates, continuous batching
+    on the GPU versus the plain FP64 one-launch-per-system form."""
     import torch
-    from paper_2112_03444_gb300 import hc, inputs
-    n, d, ni = (int(v) for v in spec.split(","))
+    from paper_2112_03444_gb300 import hc
     torch.cuda.set_device(0)
-    seeds = [SEED0 + k for k in range(ni)]
-    base, coefs = inputs.dense_batch(n, d, seeds)
-    pr = hc.Problem(base, gamma=inputs.unit_gamma(seeds[0]), settings=dict(escalate=0))
-    for _ in range(2):
-        bt = pr.track(n_instances=ni, coef=coefs).wait()
-    print(json.dumps(dict(case=spec, **bt.result)))
+    rows = serve_rows(hc, [float(r) for r in args.rates.split(",")], args.duration,
+                      trifocal=not args.no_trifocal, fp64_requests=args.fp64_requests)
+    print(json.dumps(dict(metric=METRIC, mode="serving", rows=rows)), flush=True)
 
 
 def main():
@@ -551,21 +769,26 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--cpu-sample", type=int, default=160)
-    ap.add_argument("--ref-sample", type=int, default=48)
+    ap.add_argument("--cpu-sample", type=int, default=320,
+                    help="oracle paths (all host cores) for cpu_baseline")
+    ap.add_argument("--cpu-sample-1t", type=int, default=40,
+                    help="oracle paths (one thread) for cpu_baseline_1thread")
+    ap.add_argument("--ref-sample", type=int, default=160,
+                    help="oracle paths per step of the reference arm")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64-leg", action="store_true")
+    ap.add_argument("--no-serving-leg", action="store_true")
+    ap.add_argument("--no-solve-leg", action="store_true")
+    ap.add_argument("--serve-rate", type=float, default=400.0,
+                    help="offered requests/s of the serving leg")
+    ap.add_argument("--serve-duration", type=float, default=2.0)
     ap.add_argument("--serve", action="store_true",
-                    help="serving mix: Poisson arrivals, continuous batching vs plain FP64")
+                    help="serving sweep: Poisson arrivals, continuous batching vs plain FP64")
     ap.add_argument("--rates", default="1000,2000,5000,10000,20000")
     ap.add_argument("--duration", type=float, default=2.0)
     ap.add_argument("--fp64-requests", type=int, default=60)
     ap.add_argument("--no-trifocal", action="store_true")
-    ap.add_argument("--case", default=None,
-                    help="profiling helper: track one dense class 'n,d,instances' twice and exit")
     args = ap.parse_args()
-    if args.case:
-        run_case(args.case)
-        return
     if args.serve:
         serve_mix(args)
         return

@@ -58,17 +58,18 @@ enum {
 /* Tracking precision (hc_settings.precision). */
 enum {
   HC_PREC_FP64 = 0,   /* every step in complex FP64 (the plain reference form)         */
-  HC_PREC_MIXED = 1   /* complex FP32 predictor and corrector; FP64 state x, FP64
-                         residuals in the endgame (t > t_endgame) and the final
-                         Newton refinement; colliding endpoints (path jumps) and
-                         failed paths re-tracked with FP64 residuals, then in
-                         FP64                                                       */
+  HC_PREC_MIXED = 1   /* complex FP32 predictor and corrector; FP64 state x in the
+                         endgame (t > t_endgame) with double-float corrector
+                         residuals (FP64 after a rejected step there), FP64
+                         residuals in the final Newton refinement; colliding
+                         endpoints (path jumps) and failed paths re-tracked with
+                         high-precision residuals, then in FP64                  */
 };
 
 /* Per-path status codes (hc_batch_desc.status_out).  HC_PATH_REAL is or-ed
  * into HC_PATH_FINITE when the endpoint is real within real_tol. */
 enum {
-  HC_PATH_NONE = 0,          /* not tracked (cancelled batch)                  */
+  HC_PATH_NONE = 0,          /* not tracked (step budget exhausted)            */
   HC_PATH_FINITE = 1,        /* nonsingular finite endpoint, backward error ok */
   HC_PATH_DIVERGED = 2,      /* |x|_inf exceeded r_inf                          */
   HC_PATH_FAIL_STEP = 3,     /* step size fell below dt_min                     */
@@ -157,27 +158,49 @@ typedef struct hc_problem_desc {
   int64_t n_start;             /* HC_PARAMETER: number of start solutions           */
   const double* start;         /* HC_PARAMETER: [n_start][n][2] start solutions     */
   hc_settings settings;
+  /* HC_PARAMETER, optional: sign symmetries.  Symmetry k negates the unknowns
+   * whose bits are set in sym_mask[k].  Allowed when every term has even
+   * total degree in the unknowns of every mask (then H(D x, t) = H(x, t)
+   * and the path from D s is D times the path from s, exactly in floating
+   * point: negation is exact and the evaluation and the solve treat the
+   * negated columns alike).  The start set must be closed under the masks.
+   * The library then tracks one start per orbit and writes every orbit
+   * member's endpoint as the signed image of its representative's; the
+   * duplicate check compares endpoints up to the signs.  A batch with a
+   * start subset tracks its starts without the reduction. */
+  int32_t n_sym;               /* 0..4                                              */
+  uint32_t sym_mask[4];
 } hc_problem_desc;
 
 typedef struct hc_problem hc_problem;  /* opaque */
 typedef struct hc_batch hc_batch;      /* opaque */
 
 /*
- * One batch: n_instances systems of the problem's family tracked together in
- * one persistent launch (every path of every instance is one work item).
+ * One batch (paper Sec. 3: the target systems F -- their coefficients, or the
+ * target parameters p1 of Sec. 6 -- tracked from the start solutions of G;
+ * Sec. 6: every path an independent work item): n_instances systems of the
+ * problem's family tracked together in one persistent launch.
  *   HC_TOTAL_DEGREE: coef = [n_instances][T][2] doubles (NULL: every instance
  *                    uses the problem's term_coef); paths = prod_i d_i.
  *   HC_PARAMETER:    p1 = [n_instances][n_params][2] doubles (required);
  *                    paths = n_start.
- * Outputs (written by the library until hc_poll returns HC_OK):
- *   x_out      [n_instances][paths][n][2] double  endpoints after refinement
- *   status_out [n_instances][paths] uint8         HC_PATH_* codes
- *   steps_out  [n_instances][paths][3] int32      accepted, rejected steps,
- *                                                  Newton iterations (optional)
- *   be_out     [n_instances][paths] double        backward error (optional)
+ * Optional start subset: with n_subset > 0, instance k tracks only the
+ * starts path_ids[k][0 .. n_subset) (host int64, each in [0, paths)) and
+ * its outputs hold n_subset paths, in that order (P below = n_subset).
+ * Optional step budget: with step_budget > 0 the batch starts no new path
+ * once the paths it has finished took that many steps (accepted + rejected,
+ * all tiers) in total; paths never started keep HC_PATH_NONE and hc_poll
+ * returns HC_ERR_TIMEOUT (results of the finished paths are valid).  A path
+ * that has started always finishes (its own limit is settings.max_steps).
+ * Outputs (written by the library until hc_poll returns HC_OK), P = paths:
+ *   x_out      [n_instances][P][n][2] double  endpoints after refinement
+ *   status_out [n_instances][P] uint8         HC_PATH_* codes
+ *   steps_out  [n_instances][P][3] int32      accepted, rejected steps,
+ *                                              Newton iterations (optional)
+ *   be_out     [n_instances][P] double        backward error (optional)
  * Without HC_DEVICE_PTRS the host buffers must stay valid until hc_poll
  * returns HC_OK; the library copies through device staging buffers on the
- * batch's stream.
+ * batch's stream.  path_ids is copied before hc_track_batch returns.
  */
 typedef struct hc_batch_desc {
   int32_t n_instances;
@@ -189,6 +212,10 @@ typedef struct hc_batch_desc {
   uint8_t* status_out;
   int32_t* steps_out;
   double* be_out;
+  int64_t step_budget;         /* 0: none                                        */
+  int32_t n_subset;            /* 0: every start path                             */
+  int32_t reserved;            /* 0                                               */
+  const int64_t* path_ids;     /* [n_instances][n_subset] (host), or NULL        */
 } hc_batch_desc;
 
 /* Summary filled by hc_poll when the batch is done. */
@@ -201,29 +228,40 @@ typedef struct hc_batch_result {
   double device_ms;            /* stream time from first copy to last copy      */
   double track_ms;             /* stream time of the tracking launch             */
   double escalate_ms;          /* stream time of the re-tracking launches        */
+  int64_t untracked;           /* paths never started (step budget exhausted)    */
+  int64_t steps_total;         /* steps counted against the step budget          */
 } hc_batch_result;
 
-/* Static description of an error code; never NULL. */
+/* Static description of an error code; never NULL.  (Library utility; the
+ * paper defines no error reporting.) */
 const char* hc_status_string(int32_t status);
 
-/* Last CUDA or validation error message of the calling thread ("" if none). */
+/* Last CUDA or validation error message of the calling thread ("" if none).
+ * (Library utility.) */
 const char* hc_last_error(void);
 
-/* Default settings (values listed in the hc_settings comments). */
+/* Default settings (values listed in the hc_settings comments): the step
+ * rule, tolerances and classification thresholds on which Sec. 3 is silent,
+ * read by this library. */
 hc_settings hc_default_settings(void);
 
 /*
- * Validate and deep-copy a problem; upload its encoded form to the current
- * device.  On error *out is left untouched.  Errors: HC_ERR_INVALID (index
+ * Sec. 3 (the square system F, the start system G with known solutions and
+ * the homotopy H joining them) and Sec. 6 (the terms of the equations as the
+ * evaluator's input): validate and deep-copy a problem; upload its encoded
+ * form (term tables or dense coefficient maps) to the current device.  On
+ * error *out is left untouched.  Errors: HC_ERR_INVALID (index
  * out of range, n outside 1..32, missing start data, unsupported degree),
  * HC_ERR_NUMERIC (non-finite data), HC_ERR_OOM, HC_ERR_CUDA.
  */
 hc_status hc_create_problem(const hc_problem_desc* d, hc_problem** out);
 
-/* Paths per instance of a problem (prod d_i, or n_start); -1 for NULL. */
+/* Paths per instance of a problem (prod d_i, the Bezout number of the
+ * total-degree start system, or n_start); -1 for NULL. */
 int64_t hc_problem_paths(const hc_problem* p);
 
-/* Static facts of a problem, for callers that size buffers or admit work. */
+/* Static facts of a problem, for callers that size buffers or admit work
+ * (library utility). */
 typedef struct hc_problem_info {
   int32_t n;                  /* unknowns                                        */
   int32_t kind;               /* HC_TOTAL_DEGREE or HC_PARAMETER                 */
@@ -238,30 +276,54 @@ typedef struct hc_problem_info {
 hc_status hc_problem_query(const hc_problem* p, hc_problem_info* out);
 
 /*
- * Enqueue one batch on b->stream and return at once with *out set.  Staging
- * of coefficients, the tracking launch and the result copies all run on the
- * stream.  Errors: HC_ERR_INVALID, HC_ERR_OOM, HC_ERR_CUDA, HC_ERR_BUSY.
+ * Sec. 3 (predictor-corrector tracking of every start path from t = 0 to
+ * t = 1, Eqs. 2-6) run as Sec. 6 lays the work out on the GPU (each path an
+ * independent track, evaluation and the fused solve per path): enqueue one
+ * batch on b->stream and return at once with *out set.  Staging of
+ * coefficients, the tracking launch and the result copies all run on the
+ * stream.  Admission: with a device-memory cap set (hc_set_memory_cap), a
+ * batch whose device memory would take the batches in flight on the device
+ * past the cap returns HC_ERR_BUSY, or with HC_BLOCKING_ADMIT waits for
+ * earlier batches to finish (a batch larger than the cap on its own is
+ * admitted when nothing else is in flight).  Errors: HC_ERR_INVALID,
+ * HC_ERR_OOM, HC_ERR_CUDA, HC_ERR_BUSY.
  */
 hc_status hc_track_batch(hc_problem* p, const hc_batch_desc* b, hc_batch** out);
 
 /*
- * Wait at most timeout_us microseconds (< 0: without limit, 0: just test)
- * for the batch.  HC_OK: done, *r filled (r may be NULL).  HC_PENDING: still
- * running.  Never blocks beyond the timeout.
+ * Admission cap for hc_track_batch on the current device: the device bytes
+ * (inputs, encoded tables, outputs, scratch) of the batches in flight may
+ * not exceed max_device_bytes (0: no cap, the default).  A batch counts as
+ * in flight until its completion is observed (hc_poll, hc_destroy or a later
+ * admission check).  (Library utility; the paper tracks one system at a
+ * time.)  Errors: HC_ERR_INVALID (negative), HC_ERR_CUDA.
+ */
+hc_status hc_set_memory_cap(int64_t max_device_bytes);
+
+/*
+ * The output side of Sec. 3 (endpoints and their classification): wait at
+ * most timeout_us microseconds (< 0: without limit, 0: just test) for the
+ * batch.  HC_OK: done, *r filled (r may be NULL).  HC_ERR_TIMEOUT: done, but
+ * the batch's step budget ran out before every path started (*r filled,
+ * r->untracked > 0).  HC_PENDING: still running.  Never blocks beyond the
+ * timeout.
  */
 hc_status hc_poll(hc_batch* b, int64_t timeout_us, hc_batch_result* r);
 
 /* Free a problem, a batch, a plan or a server (waits for running work
- * first).  NULL is a no-op.  A problem must outlive its batches and plans. */
+ * first).  NULL is a no-op.  A problem must outlive its batches and plans.
+ * (Library utility.) */
 void hc_destroy(void* handle);
 
 /*
- * Plans: a batch shape replayed as one CUDA graph.  The paper (Sec. 5) runs
- * each problem's batch as a fixed sequence of launches; a plan records that
- * sequence once -- coefficient staging, the tracking launch, the re-tracking
- * tiers on a high-priority branch, the summary -- with device buffers
- * allocated for good, so each later batch of the same size costs one graph
- * launch plus its input and output copies, and no allocation.
+ * Plans: a batch shape replayed as one CUDA graph (no counterpart in the
+ * paper, which launches one system at a time; Sec. 6 only asks that data
+ * transfer be avoided).  A batch of hc_track_batch is a fixed sequence of
+ * launches; a plan records that sequence once -- coefficient staging, the
+ * tracking launch, the re-tracking tiers on a high-priority branch, the
+ * summary -- with device buffers allocated for good, so each later batch of
+ * the same size costs one graph launch plus its input and output copies, and
+ * no allocation.  Plans take no start subset and no step budget.
  *
  * hc_plan_create: fixes the problem's current settings, n_instances and the
  * device (the current one).  Errors: HC_ERR_INVALID, HC_ERR_OOM, HC_ERR_CUDA,
@@ -282,7 +344,8 @@ hc_status hc_plan_create(hc_problem* p, int32_t n_instances, hc_plan** out);
 hc_status hc_plan_run(hc_plan* plan, const hc_batch_desc* b, hc_batch** out);
 
 /*
- * Autotuner.  Runs the caller's representative batch (*sample, as for
+ * Autotuner (no counterpart in the paper, which fixes one warp per path in
+ * Sec. 6).  Runs the caller's representative batch (*sample, as for
  * hc_track_batch; its outputs are overwritten) under each candidate
  * configuration -- all-FP64; mixed precision with the default lane width or
  * one path per warp; FP32 first-correction bound 0.01 or 0.1 -- twice each,
@@ -301,8 +364,8 @@ typedef struct hc_tune_report {
 hc_status hc_autotune(hc_problem* p, const hc_batch_desc* sample, hc_tune_report* report);
 
 /*
- * Continuous-batching server (serving form of the tracker; the paper tracks
- * one system per launch).  Requests -- one system instance each: the
+ * Continuous-batching server (serving form of the tracker; no counterpart in
+ * the paper, which tracks one system per launch).  Requests -- one system instance each: the
  * coefficients (HC_TOTAL_DEGREE) or target parameters (HC_PARAMETER) of one
  * problem -- are queued per problem.  A dispatcher thread forms a batch from
  * whatever is pending for a problem as soon as one of n_streams streams is
@@ -354,6 +417,74 @@ hc_status hc_server_wait(hc_server* s, uint64_t request_id, int64_t timeout_us, 
 /* Counters since creation: [0] requests done [1] batches [2] max batches in
  * flight at once [3] max in-flight device bytes [4] max instances in a batch. */
 hc_status hc_server_stats(hc_server* s, int64_t* out5);
+
+/*
+ * Sec. 6, the fused batched linear solver (LU with partial pivoting on the
+ * augmented matrix [A b], the triangular solve folded into the same kernel,
+ * data held in registers), measured standalone as in the paper's Fig. 3:
+ * solves A_k x_k = b_k for k < batch, n x n complex systems, one lane group
+ * per system, one matrix row per lane (the tracker's own solve).  The
+ * elimination is Gauss-Jordan (it also clears above the pivot), which with
+ * one row per lane replaces the back substitution at no extra latency.
+ *   n       1..32
+ *   batch   >= 0 (0: nothing to do)
+ *   fp32    0: complex double (interleaved re, im doubles);
+ *           1: complex float (interleaved re, im floats)
+ *   A       device [batch][n][n] complex, row-major, system after system
+ *   b       device [batch][n] complex
+ *   x       device [batch][n] complex (output; may not alias A or b)
+ *   info    device [batch] int32 (optional): 0, or 1 if a pivot was zero or
+ *           non-finite (x is then not a solution)
+ *   stream  cudaStream_t (NULL: the legacy default stream)
+ * Enqueues one launch and returns.  Pivot: largest |Re| + |Im|, lowest row
+ * on ties.  Errors: HC_ERR_INVALID, HC_ERR_CUDA.
+ */
+hc_status hc_batched_solve(int32_t n, int64_t batch, int32_t fp32, const void* A, const void* b,
+                           void* x, int32_t* info, void* stream);
+
+/*
+ * Sec. 7: the start systems of the parameter homotopies come from monodromy
+ * (Macaulay2 in the paper) -- all isolated solutions of F(x; p0) at a
+ * generic complex parameter point p0.  This call computes them on the GPU
+ * from one seed solution: the known solutions are carried around triangle
+ * loops p0 -> pa -> pb -> p0 through random complex parameter points
+ * (parameter homotopies tracked by hc_track_batch), and endpoints not yet
+ * known (relative infinity distance > 1e-6) are added, until stall_loops
+ * consecutive loops add nothing.  A round runs loops_per_round loops; their
+ * first legs share one batch.  With sign symmetries in the family
+ * (n_sym > 0) the sign images of every new solution are added too and the
+ * legs track one start per orbit.
+ *   family          HC_PARAMETER description; its p0, n_start and start are
+ *                   ignored (the call sets them per leg); its settings apply
+ *   x0, p0          host [n][2] and [n_params][2]: a solution of F(x0; p0) = 0
+ *   seed            seeds the loop points (splitmix64 + Box-Muller)
+ *   out             host [max_solutions][n][2] doubles: the solutions found
+ * *n_solutions receives the count (also when it exceeds max_solutions, in
+ * which case HC_ERR_INVALID is returned and out is not written); *info
+ * (may be NULL) the loops, rounds, tracked paths and wall time.  Errors:
+ * HC_ERR_INVALID and those of hc_create_problem / hc_track_batch.
+ */
+typedef struct hc_monodromy_desc {
+  const hc_problem_desc* family;
+  const double* x0;
+  const double* p0;
+  uint64_t seed;
+  int32_t stall_loops;         /* e.g. 10                                          */
+  int32_t max_loops;           /* e.g. 400                                         */
+  int32_t loops_per_round;     /* e.g. 4                                           */
+  int32_t reserved;            /* 0                                                */
+  int64_t max_solutions;
+  double* out;
+} hc_monodromy_desc;
+
+typedef struct hc_monodromy_info {
+  int32_t loops, rounds;
+  int64_t paths_tracked;
+  double seconds;
+} hc_monodromy_info;
+
+hc_status hc_monodromy_solve(const hc_monodromy_desc* d, int64_t* n_solutions,
+                             hc_monodromy_info* info);
 
 /*
  * Measurement utility (no counterpart in the paper): FMA throughput of the

@@ -70,6 +70,10 @@ def _load():
         lib.oracle_newton_step.restype = I
         lib.oracle_track.argtypes = [P, I64, P, P, P, I, P, P, P, P, P, P]
         lib.oracle_hardware_threads.restype = I
+        lib.oracle_backward_error.argtypes = [P, P]
+        lib.oracle_backward_error.restype = D
+        lib.oracle_cond1.argtypes = [P, P]
+        lib.oracle_cond1.restype = D
         _lib = lib
         return lib
 
@@ -142,6 +146,16 @@ class OracleProblem:
         dn = ctypes.c_double(0.0)
         rc = self._lib.oracle_newton_step(self.h, _ptr(x), float(t), ctypes.byref(dn))
         return x, float(dn.value), rc == 0
+
+    def backward_error(self, x) -> float:
+        """max_i |F_i(x)| / sum_k |c_k| |x^alpha_k| at t = 1 (classification)."""
+        x = np.ascontiguousarray(x, np.complex128)
+        return float(self._lib.oracle_backward_error(self.h, _ptr(x)))
+
+    def cond1(self, x) -> float:
+        """1-norm condition number of dF/dx at t = 1 and the point x."""
+        x = np.ascontiguousarray(x, np.complex128)
+        return float(self._lib.oracle_cond1(self.h, _ptr(x)))
 
     def track(self, n_paths=None, start=None, path_ids=None, settings=None, threads=0):
         """Track paths; returns dict of numpy arrays (x, status, counts, be, cond, t)."""

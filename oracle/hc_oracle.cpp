@@ -520,6 +520,23 @@ void oracle_track(void* h, int64_t n_paths, const double* start, const int64_t* 
   for (auto& th : pool) th.join();
 }
 
+// Backward error max_i |F_i(x)| / sum_k |c_k| |x^alpha_k| and the 1-norm
+// condition number of dF/dx, both at t = 1 and a given point x (the two
+// classification quantities of track_one, exposed for their pins).
+double oracle_backward_error(void* h, const double* x) {
+  const Problem& pr = *static_cast<Problem*>(h);
+  std::vector<cd> xv(pr.n);
+  for (int i = 0; i < pr.n; ++i) xv[i] = cd(x[2 * i], x[2 * i + 1]);
+  return backward_error(pr, xv.data());
+}
+
+double oracle_cond1(void* h, const double* x) {
+  const Problem& pr = *static_cast<Problem*>(h);
+  std::vector<cd> xv(pr.n);
+  for (int i = 0; i < pr.n; ++i) xv[i] = cd(x[2 * i], x[2 * i + 1]);
+  return cond1_at_end(pr, xv.data());
+}
+
 int oracle_hardware_threads() { return (int)std::max(1u, std::thread::hardware_concurrency()); }
 
 }  // extern "C"

@@ -19,6 +19,8 @@ struct DenseProblem {
     h.D32 = a->D32 ? a->D32 + inst * a->Dstride : nullptr;
     h.D64 = a->D64 ? a->D64 + inst * a->Dstride : nullptr;
     h.E = a->E + inst * a->Estride;
+    h.Edf = a->Edf ? a->Edf + inst * a->Estride : nullptr;
+    h.gammadf = a->gammadf;
     h.gamma = a->gamma;
     h.gamma32 = a->gamma32;
     h.Vf = sm.vf;

@@ -13,9 +13,11 @@
 // homogeneous part:  F_i = c_i0 + sum_j x_j (a0_j + a1_j / 2 + a2_j / 3),
 // where a_e is the part of dF_i/dx_j built from degree-e monomials.
 //
-// FP64 residuals use the monomial coefficients in nested Horner order
+// High-precision residuals use the monomial coefficients in nested Horner order
 //   F_i = c0 + sum_j x_j (b_j + sum_{k<=j} x_k (q_jk + sum_{l<=k} r_jkl x_l)),
-// one complex FMA per monomial.
+// one complex FMA per monomial: in FP64 (all-FP64 kernels, table E) or in
+// double-float arithmetic (mixed-precision kernels, table Edf: the same
+// coefficients split into FP32 pairs, see dfloat.cuh).
 //
 // Data layout (per instance, lane stride L so that the L lanes of a path read
 // consecutive addresses):
@@ -23,11 +25,13 @@
 //      coefficients of a pair with one 16-byte load (FP32); the constant,
 //      linear and quadratic monomials each start a new pair (dense_slot in
 //      kernels.cuh); slice N pair 0 holds the constant c_i0.
-//   E: [M][L] complex double, nested Horner order.
+//   E: [M][L] complex double, nested Horner order; Edf the same entries as
+//      double-floats (16 bytes each: hi re, hi im, lo re, lo im).
 #pragma once
 
 #include <type_traits>
 
+#include "dfloat.cuh"
 #include "hc_device.cuh"
 #include "kernels.cuh"
 
@@ -61,8 +65,10 @@ struct DenseTD {
   const cx<float>* D32;
   const cx<double>* D64;
   const cx<double>* E;
+  const cdf* Edf;
   cx<double> gamma;
   cx<float> gamma32;
+  cdf gammadf;
   cx<float>* Vf;   // the group's shared copies of the evaluation point (+ monomials)
   cx<double>* Vd;
   unsigned gmask;  // lanes of the group
@@ -308,6 +314,98 @@ struct DenseTD {
       sc = t * (double)Ssum + omt * (double)(1.0f + (DEG == 2 ? axi * axi : axi * axi * axi));
     } else {
       sc = 0.0;
+    }
+  }
+
+  // The residual of row i in double-float arithmetic (mixed-precision
+  // kernels): the nested Horner order of residual64 over Edf, the point read
+  // as double-floats from the group's shared copy.  H is returned rounded to
+  // FP32: its error is a small multiple of 2^-48 times the size of the terms
+  // (the backward-error scale sc, formed as in residual64), far below the
+  // tolerances the FP64 residual serves, and only the FP32 solve consumes it.
+  template <bool SCALE_T>
+  __device__ __forceinline__ void residual_df(const cdf* xs, int i, double t, cx<float>& H,
+                                              float& sc) const {
+    residual_df_impl(xs, i, t, SCALE_T, H, sc);
+  }
+
+  __device__ static cdf part_sum_cdf(cdf v) {
+    if constexpr (PARTS > 1) {
+#pragma unroll
+      for (int o = L; o < L * PARTS; o <<= 1) {
+        cdf w;
+        w.hr = __shfl_xor_sync(0xffffffffu, v.hr, o);
+        w.hi_ = __shfl_xor_sync(0xffffffffu, v.hi_, o);
+        w.lr = __shfl_xor_sync(0xffffffffu, v.lr, o);
+        w.li = __shfl_xor_sync(0xffffffffu, v.li, o);
+        v = cdf_add(v, w);
+      }
+    }
+    return v;
+  }
+
+  __device__ __noinline__ void residual_df_impl(const cdf* xs, int i, double t, bool scale,
+                                                cx<float>& H, float& sc) const {
+    const int r = i & (L - 1);
+    const int part = (PARTS > 1) ? i / L : 0;
+    const cdf* e = Edf + (r < N ? r : 0);
+    cdf F = part == 0 ? e[0] : cdf_zero();
+    float Ssum = (scale && part == 0) ? cdf_abs_hi(e[0]) : 0.f;
+#pragma unroll 1
+    for (int mm = 0;; ++mm) {
+      const int j = zigzag(mm, part);
+      if (j >= N) break;
+      int m = 1;
+#pragma unroll 1
+      for (int jj = 0; jj < j; ++jj)
+        m += 1 + (DEG == 2 ? jj + 1 : (jj + 1) * jj / 2 + 2 * (jj + 1));
+      cdf in = e[m * L];
+      float ins = scale ? cdf_abs_hi(e[m * L]) : 0.f;
+      ++m;
+#pragma unroll 1
+      for (int k = 0; k <= j; ++k) {
+        const cdf xk = xs[k];
+        if constexpr (DEG == 2) {
+          in = cdf_fma(e[m * L], xk, in);
+          if (scale) ins += cdf_abs_hi(e[m * L]) * cdf_abs_hi(xk);
+          ++m;
+        } else {
+          cdf in2 = e[m * L];
+          float in2s = scale ? cdf_abs_hi(e[m * L]) : 0.f;
+          ++m;
+#pragma unroll 1
+          for (int l = 0; l <= k; ++l) {
+            const cdf xl = xs[l];
+            in2 = cdf_fma(e[m * L], xl, in2);
+            if (scale) in2s += cdf_abs_hi(e[m * L]) * cdf_abs_hi(xl);
+            ++m;
+          }
+          in = cdf_fma(xk, in2, in);
+          if (scale) ins += cdf_abs_hi(xk) * in2s;
+        }
+      }
+      const cdf xj = xs[j];
+      F = cdf_fma(xj, in, F);
+      if (scale) Ssum += cdf_abs_hi(xj) * ins;
+    }
+    if constexpr (PARTS > 1) {
+      F = part_sum_cdf(F);
+      if (scale) {
+#pragma unroll
+        for (int o = L; o < L * PARTS; o <<= 1) Ssum += __shfl_xor_sync(0xffffffffu, Ssum, o);
+      }
+    }
+    const cdf xi = xs[r < N ? r : 0];
+    const cdf xi2 = cdf_mul(xi, xi);
+    const cdf one{1.f, 0.f, 0.f, 0.f};
+    const cdf G = cdf_sub(DEG == 2 ? xi2 : cdf_mul(xi2, xi), one);
+    const cdf Hd = cdf_add(cdf_scale(to_df(t), F), cdf_scale(to_df(1.0 - t), cdf_mul(gammadf, G)));
+    H = cdf_to_cf(Hd);
+    if (scale) {
+      const float axi = cdf_abs_hi(xi);
+      sc = (float)t * Ssum + (float)(1.0 - t) * (1.0f + (DEG == 2 ? axi * axi : axi * axi * axi));
+    } else {
+      sc = 0.f;
     }
   }
 

@@ -8,6 +8,7 @@
 #include <cstring>
 #include <functional>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -63,8 +64,8 @@ void set_err(const std::string& s) { g_err = s; }
 __global__ void stage_dense_kernel(int64_t n_inst, int T, const double2* __restrict__ coef,
                                    int64_t coef_stride, const int* __restrict__ emap, int ndc,
                                    const int* __restrict__ dterm, const int* __restrict__ dslot,
-                                   const float* __restrict__ dmult, double2* E, int64_t Es,
-                                   float2* D32, double2* D64, int64_t Ds) {
+                                   const float* __restrict__ dmult, double2* E, hc::cdf* Edf,
+                                   int64_t Es, float2* D32, double2* D64, int64_t Ds) {
   const int64_t per = (int64_t)T + ndc;
   const int64_t total = n_inst * per;
   for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < total;
@@ -74,6 +75,7 @@ __global__ void stage_dense_kernel(int64_t n_inst, int T, const double2* __restr
     const double2* c = coef + inst * coef_stride;
     if (r < T) {
       E[inst * Es + emap[r]] = c[r];
+      if (Edf) Edf[inst * Es + emap[r]] = hc::to_cdf(cx<double>{c[r].x, c[r].y});
     } else {
       r -= T;
       const double2 v = c[dterm[r]];
@@ -85,12 +87,6 @@ __global__ void stage_dense_kernel(int64_t n_inst, int T, const double2* __restr
   }
 }
 
-// Path-jump detection: two paths of one instance that end on the same root
-// (relative infinity distance <= tol) cannot both be right, so both are
-// re-tracked from t = 0 with FP64-quality step acceptance.  One thread per path scans the other
-// paths of its instance; the threads of a warp read the same endpoint at the
-// same time (a broadcast load).  x32 holds NaN for paths that did not end
-// finite, which then never match.
 // Duplicate endpoints within an instance (path jumping): an item whose FP32
 // endpoint copy lies within tol (relative, inf-norm) of another item's gets
 // resume time 0 and is appended to out_list -- unless its status is
@@ -98,12 +94,17 @@ __global__ void stage_dense_kernel(int64_t n_inst, int T, const double2* __restr
 // all-FP64 tier, which then re-tracks it from t = 0 instead of only checking
 // it at t = 1.  list == nullptr checks every item; otherwise only the
 // *list_count items of list (endpoints that were re-tracked), against every
-// item of their instance.
+// item of their instance.  One thread per item scans the other items of its
+// instance; x32 holds NaN for paths that did not end finite, which then
+// never match.  With sign symmetries (n_group > 1) the items are orbit
+// representatives and an endpoint is compared with every sign image of the
+// others (group[e]: the unknowns element e negates).
 __global__ void dedupe_kernel(int64_t items, int64_t paths, int n, const float2* __restrict__ x32,
                               const uint8_t* __restrict__ status, float tol,
                               const int64_t* __restrict__ list,
                               const unsigned long long* list_count, int64_t* out_list,
-                              unsigned long long* out_count, double* t_io) {
+                              unsigned long long* out_count, double* t_io, int n_group,
+                              const uint32_t* __restrict__ group) {
   const int64_t total = list ? (int64_t)*list_count : items;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -119,14 +120,19 @@ __global__ void dedupe_kernel(int64_t items, int64_t paths, int n, const float2*
     for (int64_t b = b0; b < b0 + paths && !dup; ++b) {
       if (b == a) continue;
       const float2* xb = x32 + b * n;
-      const float2 w = xb[0];
-      if (!(fabsf(w.x - v0.x) <= thr) || !(fabsf(w.y - v0.y) <= thr)) continue;
-      bool same = true;
-      for (int k = 1; k < n && same; ++k) {
-        const float2 p = xa[k], q = xb[k];
-        same = (fabsf(p.x - q.x) <= thr) && (fabsf(p.y - q.y) <= thr);
+      for (int e = 0; e < n_group && !dup; ++e) {  // b's endpoint and its sign images
+        const uint32_t m = group ? group[e] : 0u;
+        const float s0 = (m & 1u) ? -1.f : 1.f;
+        const float2 w = xb[0];
+        if (!(fabsf(s0 * w.x - v0.x) <= thr) || !(fabsf(s0 * w.y - v0.y) <= thr)) continue;
+        bool same = true;
+        for (int k = 1; k < n && same; ++k) {
+          const float sk = (m >> k & 1u) ? -1.f : 1.f;
+          const float2 p = xa[k], q = xb[k];
+          same = (fabsf(p.x - sk * q.x) <= thr) && (fabsf(p.y - sk * q.y) <= thr);
+        }
+        dup = same;
       }
-      dup = same;
     }
     if (dup) {
       t_io[a] = 0.0;
@@ -145,7 +151,8 @@ __global__ void dedupe_list_kernel(int64_t paths, int n, const float2* __restric
                                    const uint8_t* __restrict__ status, float tol,
                                    const int64_t* __restrict__ list,
                                    const unsigned long long* list_count, int64_t* out_list,
-                                   unsigned long long* out_count, double* t_io) {
+                                   unsigned long long* out_count, double* t_io, int n_group,
+                                   const uint32_t* __restrict__ group) {
   const int lane = threadIdx.x & 31;
   const int64_t total = (int64_t)*list_count;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
@@ -162,12 +169,16 @@ __global__ void dedupe_list_kernel(int64_t paths, int n, const float2* __restric
     for (int64_t b = b0 + lane; b < b0 + paths && !dup; b += 32) {
       if (b == a) continue;
       const float2* xb = x32 + b * n;
-      bool same = true;
-      for (int k = 0; k < n && same; ++k) {
-        const float2 p = xa[k], q = xb[k];
-        same = (fabsf(p.x - q.x) <= thr) && (fabsf(p.y - q.y) <= thr);
+      for (int e = 0; e < n_group && !dup; ++e) {
+        const uint32_t m = group ? group[e] : 0u;
+        bool same = true;
+        for (int k = 0; k < n && same; ++k) {
+          const float sk = (m >> k & 1u) ? -1.f : 1.f;
+          const float2 p = xa[k], q = xb[k];
+          same = (fabsf(p.x - sk * q.x) <= thr) && (fabsf(p.y - sk * q.y) <= thr);
+        }
+        dup = same;
       }
-      dup = same;
     }
     if (__any_sync(0xffffffffu, dup) && lane == 0) {
       t_io[a] = 0.0;
@@ -180,28 +191,66 @@ __global__ void dedupe_list_kernel(int64_t paths, int n, const float2* __restric
 }
 
 // Batch summary: [0] finite [1] real [2] diverged [3] singular [4] failed
-// [5] accepted steps [6] rejected steps [7] Newton iterations
+// [5] accepted steps [6] rejected steps [7] Newton iterations; untracked
+// paths (HC_PATH_NONE) are counted in *untracked as well as in [4]
+// Step counters are summed over the step_items tracked items (with sign
+// symmetries the orbit representatives: the work done), statuses over the
+// items of the output.
 __global__ void summarize_kernel(int64_t items, const uint8_t* __restrict__ st,
-                                 const int32_t* __restrict__ steps, unsigned long long* out) {
-  unsigned long long c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < items;
+                                 int64_t step_items, const int32_t* __restrict__ steps,
+                                 unsigned long long* out, unsigned long long* untracked) {
+  unsigned long long c[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  const int64_t lim = items > step_items ? items : step_items;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < lim;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int s = st[i];
-    const int b = s & 0x7f;
-    c[0] += (b == hc::ST_FINITE);
-    c[1] += (b == hc::ST_FINITE) && (s & hc::ST_REAL);
-    c[2] += (b == hc::ST_DIVERGED);
-    c[3] += (b == hc::ST_SINGULAR);
-    c[4] += (b != hc::ST_FINITE && b != hc::ST_DIVERGED && b != hc::ST_SINGULAR);
-    c[5] += (unsigned)steps[i * 3 + 0];
-    c[6] += (unsigned)steps[i * 3 + 1];
-    c[7] += (unsigned)steps[i * 3 + 2];
+    if (i < items) {
+      const int s = st[i];
+      const int b = s & 0x7f;
+      c[0] += (b == hc::ST_FINITE);
+      c[1] += (b == hc::ST_FINITE) && (s & hc::ST_REAL);
+      c[2] += (b == hc::ST_DIVERGED);
+      c[3] += (b == hc::ST_SINGULAR);
+      c[4] += (b != hc::ST_FINITE && b != hc::ST_DIVERGED && b != hc::ST_SINGULAR);
+      c[8] += (s == 0);
+    }
+    if (i < step_items) {
+      c[5] += (unsigned)steps[i * 3 + 0];
+      c[6] += (unsigned)steps[i * 3 + 1];
+      c[7] += (unsigned)steps[i * 3 + 2];
+    }
   }
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
+  for (int k = 0; k < 9; ++k) {
     unsigned long long v = c[k];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0 && v) atomicAdd(out + k, v);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(k < 8 ? out + k : untracked, v);
+  }
+}
+
+// Outputs of a batch tracked on orbit representatives (sign symmetries):
+// start j of instance i takes its representative's results, the unknowns of
+// group[sign[j]] negated.  One thread per output item.
+__global__ void expand_orbits_kernel(int64_t items, int64_t paths, int64_t n_rep, int n,
+                                     const int32_t* __restrict__ rep_pos,
+                                     const uint8_t* __restrict__ sign,
+                                     const uint32_t* __restrict__ group,
+                                     const double2* __restrict__ cx, const uint8_t* __restrict__ cst,
+                                     const int32_t* __restrict__ csteps,
+                                     const double* __restrict__ cbe, double2* x, uint8_t* st,
+                                     int32_t* steps, double* be) {
+  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < items;
+       w += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t inst = w / paths, j = w - inst * paths;
+    const int64_t r = inst * n_rep + rep_pos[j];
+    const uint32_t m = group[sign[j]];
+    for (int k = 0; k < n; ++k) {
+      const double2 v = cx[r * n + k];
+      x[w * n + k] = (m >> k & 1u) ? make_double2(-v.x, -v.y) : v;
+    }
+    st[w] = cst[r];
+    if (steps)
+      for (int k = 0; k < 3; ++k) steps[w * 3 + k] = csteps[r * 3 + k];
+    if (be) be[w] = cbe[r];
   }
 }
 
@@ -264,6 +313,17 @@ struct hc_problem {
   int extra = 0;
   hc::TermRec* d_rec = nullptr;
   double2* d_s64 = nullptr;
+  hc::cdf* d_sdf = nullptr;  // the coefficients as double-floats
+  // sign symmetries (parameter homotopies): group element masks, one tracked
+  // start per orbit (reps), and per start its representative's position in
+  // reps and the group element mapping the representative onto it
+  int n_group = 1;
+  std::vector<uint32_t> group;
+  int64_t n_rep = 0;
+  uint32_t* d_group = nullptr;
+  int64_t* d_reps = nullptr;
+  int32_t* d_rep_pos = nullptr;
+  uint8_t* d_sign = nullptr;
   double2* d_p0 = nullptr;
   double2* d_start = nullptr;
 };
@@ -289,6 +349,8 @@ struct hc_batch {
   std::vector<void*> pinned;
   bool owns_ctl = false;            // h_ctl from the pinned pool (else a plan's)
   bool owns_kernel_events = false;  // evk* created for this batch (else a plan's)
+  int64_t step_budget = 0;
+  std::shared_ptr<void> admission;  // in-flight record under a memory cap
 };
 
 namespace {
@@ -303,7 +365,11 @@ PinnedPool& pinned_pool() {
   static PinnedPool pool;
   return pool;
 }
-constexpr size_t kCtlBytes = sizeof(unsigned long long) * 16;
+// control words of a batch: [0] queue [1] FP64 queue [2] FP64 list count
+// [3..5] FP64 steps [6] re-track queue [7] re-track list count [8..15]
+// summary [16] untracked paths [17] steps counted against the budget
+constexpr int kCtlWords = 24;
+constexpr size_t kCtlBytes = sizeof(unsigned long long) * kCtlWords;
 void* pinned_slot_get() {
   PinnedPool& pp = pinned_pool();
   std::lock_guard<std::mutex> lk(pp.mu);
@@ -327,24 +393,79 @@ void pinned_slot_put(void* q) {
 // before the pending blocks of other, normal-priority persistent launches,
 // and there are enough of them that concurrent batches (several classes,
 // the server's slots) rarely queue one batch's re-tracking behind another's.
+// Creation is attempted once per device; a slot whose creation failed is
+// skipped (nullptr only if every creation failed: the caller then runs the
+// re-tracking on its own stream).
 cudaStream_t retrack_stream(int device) {
   constexpr int kPerDevice = 16, kMaxDev = 64;
   static std::mutex mu;
   static cudaStream_t streams[kMaxDev][kPerDevice] = {};
+  static bool tried[kMaxDev] = {};
   static int next[kMaxDev] = {};
   if (device < 0 || device >= kMaxDev) return nullptr;
   std::lock_guard<std::mutex> lk(mu);
-  int lo = 0, hi = 0;
-  if (!streams[device][0]) {
+  if (!tried[device]) {
+    tried[device] = true;
+    int lo = 0, hi = 0;
     cudaDeviceGetStreamPriorityRange(&lo, &hi);
     for (int i = 0; i < kPerDevice; ++i)
       if (cudaStreamCreateWithPriority(&streams[device][i], cudaStreamNonBlocking, hi) !=
-          cudaSuccess)
+          cudaSuccess) {
         streams[device][i] = nullptr;
+        cudaGetLastError();
+      }
   }
-  cudaStream_t s = streams[device][next[device]];
-  next[device] = (next[device] + 1) % kPerDevice;
-  return s;
+  for (int k = 0; k < kPerDevice; ++k) {
+    cudaStream_t s = streams[device][next[device]];
+    next[device] = (next[device] + 1) % kPerDevice;
+    if (s) return s;
+  }
+  return nullptr;
+}
+
+// Admission under a device-memory cap (hc_set_memory_cap): the batches in
+// flight on a device and their device bytes.  Each record owns an event
+// recorded after its batch's last copy, so completion can be observed (and
+// waited for) without touching the batch, which its owner may destroy.
+struct AdmitRecord {
+  cudaEvent_t done = nullptr;
+  int64_t bytes = 0;
+  ~AdmitRecord() {
+    if (done) cudaEventDestroy(done);
+  }
+};
+struct AdmitState {
+  std::mutex mu;
+  int64_t cap = 0, inflight = 0;
+  std::vector<std::shared_ptr<AdmitRecord>> recs;  // admission order
+};
+constexpr int kAdmitDevices = 64;
+AdmitState& admit_state(int dev) {
+  static AdmitState st[kAdmitDevices];
+  return st[dev < 0 || dev >= kAdmitDevices ? 0 : dev];
+}
+// drop records whose batches have finished (caller holds the lock)
+void admit_reap(AdmitState& a) {
+  for (size_t i = 0; i < a.recs.size();) {
+    if (cudaEventQuery(a.recs[i]->done) == cudaSuccess) {
+      a.inflight -= a.recs[i]->bytes;
+      a.recs.erase(a.recs.begin() + (long)i);
+    } else {
+      cudaGetLastError();  // not ready is not an error of the caller's
+      ++i;
+    }
+  }
+}
+void admit_release(int dev, const std::shared_ptr<void>& rec) {
+  if (!rec) return;
+  AdmitState& a = admit_state(dev);
+  std::lock_guard<std::mutex> lk(a.mu);
+  for (size_t i = 0; i < a.recs.size(); ++i)
+    if (a.recs[i].get() == rec.get()) {
+      a.inflight -= a.recs[i]->bytes;
+      a.recs.erase(a.recs.begin() + (long)i);
+      break;
+    }
 }
 
 bool is_device_ptr(const void* p) {
@@ -493,6 +614,93 @@ bool encode_dense(hc_problem* p, std::vector<int>& emap, std::vector<int>& dterm
 }
 
 
+// Sign symmetries of a parameter homotopy (hc_problem_desc.sym_mask): every
+// term must have even degree in the unknowns of every mask; the start set
+// must be closed under the masks.  Fills the group, the orbit
+// representatives and per start its representative's position and sign
+// element.  Returns an error message, or nullptr.
+const char* build_orbits(hc_problem* p, int n_sym, const uint32_t* masks,
+                         std::vector<int64_t>& reps, std::vector<int32_t>& rep_pos,
+                         std::vector<uint8_t>& sign) {
+  const int n = p->n;
+  if (n_sym < 0 || n_sym > 4) return "n_sym must be 0..4";
+  for (int k = 0; k < n_sym; ++k) {
+    if (masks[k] == 0 || (n < 32 && (masks[k] >> n) != 0)) return "sym_mask: empty or beyond n";
+    for (int t = 0; t < p->T; ++t) {
+      int deg = 0;
+      for (int j = 0; j < n; ++j)
+        if (masks[k] >> j & 1u) deg += p->exps[(size_t)t * n + j];
+      if (deg & 1) return "sym_mask: a term has odd degree in the masked unknowns";
+    }
+  }
+  const int G = 1 << n_sym;
+  p->group.assign(G, 0u);
+  for (int e = 0; e < G; ++e)
+    for (int k = 0; k < n_sym; ++k)
+      if (e >> k & 1) p->group[e] ^= masks[k];
+  // lookup of a point in the start set: starts sorted by a linear key
+  const int64_t S = p->n_start;
+  const double* st = p->start.data();
+  auto key = [&](const double* x) {
+    double v = 0.0;
+    for (int j = 0; j < n; ++j) v += (1.0 + 0.37 * j) * (x[2 * j] + 0.61 * x[2 * j + 1]);
+    return v;
+  };
+  double wsum = 0.0;
+  for (int j = 0; j < n; ++j) wsum += 1.61 * (1.0 + 0.37 * j);
+  std::vector<std::pair<double, int64_t>> order((size_t)S);
+  for (int64_t s = 0; s < S; ++s) order[(size_t)s] = {key(st + 2 * n * s), s};
+  std::sort(order.begin(), order.end());
+  std::vector<double> img(2 * n);
+  auto find = [&](const double* y) -> int64_t {
+    double ymax = 1.0;
+    for (int j = 0; j < 2 * n; ++j) ymax = std::max(ymax, std::fabs(y[j]));
+    const double tol = 1e-9 * ymax;
+    const double ky = key(y), kt = 2.0 * tol * wsum;
+    auto it = std::lower_bound(order.begin(), order.end(), std::make_pair(ky - kt, (int64_t)-1));
+    for (; it != order.end() && it->first <= ky + kt; ++it) {
+      const double* x = st + 2 * n * it->second;
+      bool same = true;
+      for (int j = 0; j < 2 * n && same; ++j) same = std::fabs(x[j] - y[j]) <= tol;
+      if (same) return it->second;
+    }
+    return -1;
+  };
+  std::vector<int64_t> rep_of((size_t)S);
+  sign.assign((size_t)S, 0);
+  for (int64_t s = 0; s < S; ++s) {
+    int64_t best = s;
+    int be = 0;
+    for (int e = 1; e < G; ++e) {
+      for (int j = 0; j < n; ++j) {
+        const double sg = (p->group[e] >> j & 1u) ? -1.0 : 1.0;
+        img[2 * j] = sg * st[2 * n * s + 2 * j];
+        img[2 * j + 1] = sg * st[2 * n * s + 2 * j + 1];
+      }
+      const int64_t i = find(img.data());
+      if (i < 0) return "the start set is not closed under the sign symmetries";
+      if (i < best) {
+        best = i;
+        be = e;
+      }
+    }
+    rep_of[(size_t)s] = best;  // s = group[be] applied to start best
+    sign[(size_t)s] = (uint8_t)be;
+  }
+  reps.clear();
+  std::vector<int32_t> pos((size_t)S, -1);
+  for (int64_t s = 0; s < S; ++s)
+    if (rep_of[(size_t)s] == s) {
+      pos[(size_t)s] = (int32_t)reps.size();
+      reps.push_back(s);
+    }
+  rep_pos.assign((size_t)S, 0);
+  for (int64_t s = 0; s < S; ++s) rep_pos[(size_t)s] = pos[(size_t)rep_of[(size_t)s]];
+  p->n_group = G;
+  p->n_rep = (int64_t)reps.size();
+  return nullptr;
+}
+
 // Term tables of a parameter homotopy (paper Sec. 6 evaluates the terms of
 // the equations per row): for every row i its terms, each a coefficient and
 // up to 8 factor positions in V = [x | pad to L | 1 | p(t) | dp | p0] (a
@@ -590,6 +798,11 @@ void free_problem(hc_problem* p) {
   cudaFree(p->d_coef);
   cudaFree(p->d_rec);
   cudaFree(p->d_s64);
+  cudaFree(p->d_sdf);
+  cudaFree(p->d_group);
+  cudaFree(p->d_reps);
+  cudaFree(p->d_rep_pos);
+  cudaFree(p->d_sign);
   cudaFree(p->d_p0);
   cudaFree(p->d_start);
   p->magic = 0;
@@ -649,6 +862,19 @@ KernelRef retrack_kernel(int deg, int n, bool mixed) {
 }
 }  // namespace hc
 using hc::retrack_kernel;
+
+namespace hc {
+// Device bytes one instance of a batch needs with P paths per instance
+// (inputs, encoded tables, outputs, scratch): the admission measure.
+int64_t instance_device_bytes(const hc_problem* p, int64_t P) {
+  const int64_t n = p->n;
+  int64_t b = 16 * (int64_t)(p->kind == HC_PARAMETER ? p->P : p->T);  // inputs
+  if (!p->terms) b += 32 * p->Estride + 24 * p->Dstride;              // E, Edf, D64, D32
+  b += P * (16 * n + 1 + 12 + 8);                                     // x, status, steps, be
+  b += P * (8 + 8 + 8 + 8 * n + 8);                                   // lists, t_io, x32, ids
+  return b;
+}
+}  // namespace hc
 
 extern "C" {
 
@@ -744,6 +970,10 @@ hc_status hc_create_problem(const hc_problem_desc* d, hc_problem** out) {
       set_err("an equation has no terms");
       return HC_ERR_INVALID;
     }
+  if (d->n_sym != 0 && d->kind != HC_PARAMETER) {
+    set_err("sign symmetries need a parameter homotopy");
+    return HC_ERR_INVALID;
+  }
   if (d->kind == HC_TOTAL_DEGREE &&
       !(std::fabs(std::hypot(d->gamma[0], d->gamma[1]) - 1.0) < 1e-6)) {
     set_err("gamma must have unit modulus");
@@ -777,6 +1007,18 @@ hc_status hc_create_problem(const hc_problem_desc* d, hc_problem** out) {
         set_err("non-finite p0");
         return HC_ERR_NUMERIC;
       }
+    p->start.assign(d->start, d->start + 2 * (size_t)d->n_start * n);
+    std::vector<int64_t> reps;
+    std::vector<int32_t> rep_pos;
+    std::vector<uint8_t> sign;
+    if (d->n_sym != 0) {
+      const char* why = build_orbits(p, d->n_sym, d->sym_mask, reps, rep_pos, sign);
+      if (why) {
+        delete p;
+        set_err(why);
+        return HC_ERR_INVALID;
+      }
+    }
     std::vector<hc::TermRec> rec;
     std::vector<double2> s64;
     if (!encode_terms(p, rec, s64)) {
@@ -789,12 +1031,19 @@ hc_status hc_create_problem(const hc_problem_desc* d, hc_problem** out) {
       set_err("this build has parameter-homotopy kernels for n <= 24");
       return HC_ERR_UNSUPPORTED;
     }
+    // double-float split of every coefficient: hi the nearest float, lo the
+    // nearest float to the remainder
+    std::vector<hc::cdf> sdf(s64.size());
+    for (size_t k = 0; k < s64.size(); ++k) sdf[k] = hc::split_cdf_host(s64[k].x, s64[k].y);
     std::vector<double2> p0v(d->n_params), sv((size_t)d->n_start * n);
     for (int l = 0; l < d->n_params; ++l) p0v[l] = make_double2(d->p0[2 * l], d->p0[2 * l + 1]);
     for (size_t k = 0; k < sv.size(); ++k) sv[k] = make_double2(d->start[2 * k], d->start[2 * k + 1]);
     hc_status st;
     if ((st = upload(rec, &p->d_rec)) != HC_OK || (st = upload(s64, &p->d_s64)) != HC_OK ||
-        (st = upload(p0v, &p->d_p0)) != HC_OK || (st = upload(sv, &p->d_start)) != HC_OK) {
+        (st = upload(sdf, &p->d_sdf)) != HC_OK ||
+        (st = upload(p0v, &p->d_p0)) != HC_OK || (st = upload(sv, &p->d_start)) != HC_OK ||
+        (st = upload(p->group, &p->d_group)) != HC_OK || (st = upload(reps, &p->d_reps)) != HC_OK ||
+        (st = upload(rep_pos, &p->d_rep_pos)) != HC_OK || (st = upload(sign, &p->d_sign)) != HC_OK) {
       free_problem(p);
       return st;
     }
@@ -836,12 +1085,7 @@ hc_status hc_problem_query(const hc_problem* p, hc_problem_info* out) {
   out->inputs_per_instance = p->kind == HC_PARAMETER ? p->P : p->T;
   out->lanes = p->terms ? hc::term_kernel(p->n, true, 0).lanes : p->L;
   out->paths = p->paths;
-  const int64_t P = p->paths, n = p->n;
-  int64_t b = 16 * (int64_t)out->inputs_per_instance;                // inputs
-  if (!p->terms) b += 16 * p->Estride + 24 * p->Dstride;             // E, D64, D32
-  b += P * (16 * n + 1 + 12 + 8);                                    // x, status, steps, be
-  b += P * (8 + 8 + 8 + 8 * n);                                      // two lists, t_io, x32
-  out->device_bytes_per_instance = b;
+  out->device_bytes_per_instance = hc::instance_device_bytes(p, p->paths);
   return HC_OK;
 }
 
@@ -851,23 +1095,37 @@ namespace {
 
 // Device buffers of one batch.
 struct Bufs {
+  int64_t paths = 0;                 // paths per instance of this batch (subset size)
+  const int64_t* path_ids = nullptr; // device [instances][paths] start indices, or null
+  int64_t step_budget = 0;           // 0: none
   const double* d_coef = nullptr;  // dense: per-instance coefficients (or the problem's)
   int64_t coef_stride = 0;
   const double2* d_p1 = nullptr;   // parameter families: target parameters
-  void *E = nullptr, *D64 = nullptr, *D32 = nullptr;
+  void *E = nullptr, *Edf = nullptr, *D64 = nullptr, *D32 = nullptr;
   double* d_x = nullptr;
   uint8_t* d_status = nullptr;
   int32_t* d_steps = nullptr;
   double* d_be = nullptr;
-  unsigned long long* d_ctl = nullptr;  // [0] queue [1] FP64 queue [2] FP64 list count
-                                        // [3..5] FP64 steps [6] re-track queue
-                                        // [7] re-track list count [8..15] summary
+  unsigned long long* d_ctl = nullptr;  // kCtlWords control words (see kCtlBytes)
   unsigned long long* h_ctl = nullptr;  // pinned copy of d_ctl
   int64_t* esc_list = nullptr;
   int64_t* dup_list = nullptr;
   double* t_io = nullptr;
   float2* x32 = nullptr;
+  // sign symmetries: results of the tracked orbit representatives, expanded
+  // into d_x .. d_be at the end
+  double* cx = nullptr;
+  uint8_t* cst = nullptr;
+  int32_t* csteps = nullptr;
+  double* cbe = nullptr;
 };
+
+// The batch tracks orbit representatives (sign symmetries, no start subset).
+bool sym_active(const hc_problem* p, const Bufs& B) { return p->n_group > 1 && !B.path_ids; }
+// Paths per instance the kernels track.
+int64_t tracked_paths(const hc_problem* p, const Bufs& B) {
+  return sym_active(p, B) ? p->n_rep : B.paths;
+}
 
 // Scratch of a batch (encoded coefficients, control words, re-tracking lists);
 // alloc(bytes, &ptr) returns an hc_status.
@@ -875,17 +1133,29 @@ template <class A>
 hc_status alloc_scratch(hc_problem* p, int64_t n_inst, Bufs& B, A&& alloc) {
   const bool mixed = p->s.precision == HC_PREC_MIXED;
   const bool escalate = mixed && p->s.escalate;
-  const int64_t items = n_inst * p->paths;
+  const int64_t items = n_inst * tracked_paths(p, B);
   void* q;
   hc_status rc;
+  if (sym_active(p, B)) {
+    if ((rc = alloc(sizeof(double) * 2 * p->n * items, &q)) != HC_OK) return rc;
+    B.cx = (double*)q;
+    if ((rc = alloc((size_t)items, &q)) != HC_OK) return rc;
+    B.cst = (uint8_t*)q;
+    if ((rc = alloc(sizeof(int32_t) * 3 * items, &q)) != HC_OK) return rc;
+    B.csteps = (int32_t*)q;
+    if ((rc = alloc(sizeof(double) * items, &q)) != HC_OK) return rc;
+    B.cbe = (double*)q;
+  }
   if (!p->terms) {
     if ((rc = alloc(sizeof(cx<double>) * p->Estride * n_inst, &B.E)) != HC_OK) return rc;
     if (!mixed || escalate)
       if ((rc = alloc(sizeof(cx<double>) * p->Dstride * n_inst, &B.D64)) != HC_OK) return rc;
-    if (mixed)
+    if (mixed) {
       if ((rc = alloc(sizeof(cx<float>) * p->Dstride * n_inst, &B.D32)) != HC_OK) return rc;
+      if ((rc = alloc(sizeof(hc::cdf) * p->Estride * n_inst, &B.Edf)) != HC_OK) return rc;
+    }
   }
-  if ((rc = alloc(sizeof(unsigned long long) * 16, &q)) != HC_OK) return rc;
+  if ((rc = alloc(kCtlBytes, &q)) != HC_OK) return rc;
   B.d_ctl = (unsigned long long*)q;
   if (escalate) {
     if ((rc = alloc(sizeof(int64_t) * items, &q)) != HC_OK) return rc;
@@ -922,33 +1192,54 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
   };
   const bool mixed = p->s.precision == HC_PREC_MIXED;
   const bool escalate = mixed && p->s.escalate;
-  const int64_t items = n_inst * p->paths;
+  const bool sym = sym_active(p, B);
+  const int64_t paths = tracked_paths(p, B);  // tracked paths per instance
+  const int64_t items = n_inst * paths;       // tracked items
+  const int64_t out_items = n_inst * B.paths;
+  double* tx = sym ? B.cx : B.d_x;             // the tracking launches' outputs
+  uint8_t* tst = sym ? B.cst : B.d_status;
+  int32_t* tsteps = sym ? B.csteps : B.d_steps;
+  double* tbe = sym ? B.cbe : B.d_be;
+  const int n_group = sym ? p->n_group : 1;
+  const uint32_t* group = sym ? p->d_group : nullptr;
   const int n = p->n;
   if (!p->terms) {
     HC_CUDA(cudaMemsetAsync(B.E, 0, sizeof(cx<double>) * p->Estride * n_inst, st));
+    if (B.Edf) HC_CUDA(cudaMemsetAsync(B.Edf, 0, sizeof(hc::cdf) * p->Estride * n_inst, st));
     if (B.D64) HC_CUDA(cudaMemsetAsync(B.D64, 0, sizeof(cx<double>) * p->Dstride * n_inst, st));
     if (B.D32) HC_CUDA(cudaMemsetAsync(B.D32, 0, sizeof(cx<float>) * p->Dstride * n_inst, st));
     const int64_t work = n_inst * (p->T + p->ndc);
     const int grid = (int)std::min<int64_t>((work + 255) / 256, 4096);
     stage_dense_kernel<<<grid, 256, 0, st>>>(n_inst, p->T, (const double2*)B.d_coef, B.coef_stride,
                                             p->d_emap, p->ndc, p->d_dterm, p->d_dslot,
-                                            p->d_dmult, (double2*)B.E, p->Estride, (float2*)B.D32,
+                                            p->d_dmult, (double2*)B.E, (hc::cdf*)B.Edf, p->Estride,
+                                            (float2*)B.D32,
                                             (double2*)B.D64, p->Dstride);
     HC_CUDA(cudaGetLastError());
   }
-  HC_CUDA(cudaMemsetAsync(B.d_ctl, 0, sizeof(unsigned long long) * 16, st));
-  HC_CUDA(cudaMemsetAsync(B.d_steps, 0, sizeof(int32_t) * 3 * items, st));
+  HC_CUDA(cudaMemsetAsync(B.d_ctl, 0, kCtlBytes, st));
+  HC_CUDA(cudaMemsetAsync(tsteps, 0, sizeof(int32_t) * 3 * items, st));
+  if (B.step_budget > 0) {
+    // paths the budget leaves unstarted keep HC_PATH_NONE and a NaN
+    // endpoint copy (the duplicate check skips them)
+    HC_CUDA(cudaMemsetAsync(tst, 0, (size_t)items, st));
+    if (B.x32) HC_CUDA(cudaMemsetAsync(B.x32, 0xff, sizeof(float2) * n * items, st));
+  }
 
   hc::LaunchCommon cm;
   std::memset(&cm, 0, sizeof(cm));
   cm.s = dev_settings(p->s);
   cm.n_items = items;
   cm.queue = B.d_ctl + 0;
-  cm.paths = p->paths;
-  cm.x_out = B.d_x;
-  cm.status_out = B.d_status;
-  cm.steps_out = B.d_steps;
-  cm.be_out = B.d_be;
+  cm.paths = paths;
+  cm.path_ids = B.path_ids;
+  cm.path_map = sym ? p->d_reps : nullptr;
+  cm.step_total = B.d_ctl + 17;
+  cm.step_budget = (unsigned long long)B.step_budget;
+  cm.x_out = tx;
+  cm.status_out = tst;
+  cm.steps_out = tsteps;
+  cm.be_out = tbe;
   cm.esc_list = B.esc_list;
   cm.esc_count = B.d_ctl + 2;
   cm.t_io = B.t_io;
@@ -988,9 +1279,9 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
   auto dedupe = [&]() -> hc_status {
     HC_CUDA(cudaStreamWaitEvent(hs, ev.capture ? ev.fork : ev.ek1, 0));
     const int grid = (int)std::min<int64_t>((items + 255) / 256, 65535);
-    dedupe_kernel<<<std::max(grid, 1), 256, 0, hs>>>(items, p->paths, n, B.x32, B.d_status, 1e-6f,
+    dedupe_kernel<<<std::max(grid, 1), 256, 0, hs>>>(items, paths, n, B.x32, tst, 1e-6f,
                                                     nullptr, nullptr, B.dup_list, B.d_ctl + 7,
-                                                    B.t_io);
+                                                    B.t_io, n_group, group);
     HC_CUDA(cudaGetLastError());
     return HC_OK;
   };
@@ -998,9 +1289,9 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
   // goes to the all-FP64 tier, from t = 0
   auto dedupe_again = [&]() -> hc_status {
     const int grid = (int)std::min<int64_t>((items + 7) / 8, 1024);  // 8 warps per block
-    dedupe_list_kernel<<<std::max(grid, 1), 256, 0, hs>>>(p->paths, n, B.x32, B.d_status, 1e-6f,
+    dedupe_list_kernel<<<std::max(grid, 1), 256, 0, hs>>>(paths, n, B.x32, tst, 1e-6f,
                                                          B.dup_list, B.d_ctl + 7, B.esc_list,
-                                                         B.d_ctl + 2, B.t_io);
+                                                         B.d_ctl + 2, B.t_io, n_group, group);
     HC_CUDA(cudaGetLastError());
     return HC_OK;
   };
@@ -1011,6 +1302,7 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
     ta.c = cm;
     ta.rec = p->d_rec;
     ta.s64 = p->d_s64;
+    ta.sdf = p->d_sdf;
     ta.TT = p->TT;
     ta.P = p->P;
     ta.ls = p->L;
@@ -1052,10 +1344,12 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
     a.D32 = (const cx<float>*)B.D32;
     a.D64 = (const cx<double>*)B.D64;
     a.E = (const cx<double>*)B.E;
+    a.Edf = (const hc::cdf*)B.Edf;
     a.Dstride = p->Dstride;
     a.Estride = p->Estride;
     a.gamma = cx<double>{p->gamma[0], p->gamma[1]};
     a.gamma32 = cx<float>{(float)p->gamma[0], (float)p->gamma[1]};
+    a.gammadf = hc::split_cdf_host(p->gamma[0], p->gamma[1]);
     const hc::KernelRef k = hc::dense_kernel(p->deg, n, mixed, mixed ? p->s.lanes : 0);
     if (!k.fn) {
       set_err("no kernel for this problem shape");
@@ -1087,20 +1381,36 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
       HC_CUDA(mark(ev.ek2, st));
     }
   }
-  const int grid = (int)std::min<int64_t>((items + 255) / 256, 1024);
-  summarize_kernel<<<std::max(grid, 1), 256, 0, st>>>(items, B.d_status, B.d_steps, B.d_ctl + 8);
+  if (sym) {
+    const int eg = (int)std::min<int64_t>((out_items + 255) / 256, 4096);
+    expand_orbits_kernel<<<std::max(eg, 1), 256, 0, st>>>(
+        out_items, B.paths, paths, n, p->d_rep_pos, p->d_sign, p->d_group, (const double2*)tx, tst,
+        tsteps, tbe, (double2*)B.d_x, B.d_status, B.d_steps, B.d_be);
+    HC_CUDA(cudaGetLastError());
+  }
+  const int grid = (int)std::min<int64_t>((std::max(items, out_items) + 255) / 256, 1024);
+  summarize_kernel<<<std::max(grid, 1), 256, 0, st>>>(out_items, B.d_status, items, tsteps,
+                                                     B.d_ctl + 8, B.d_ctl + 16);
   HC_CUDA(cudaGetLastError());
   if (B.h_ctl)
-    HC_CUDA(cudaMemcpyAsync(B.h_ctl, B.d_ctl, sizeof(unsigned long long) * 16,
-                            cudaMemcpyDeviceToHost, st));
+    HC_CUDA(cudaMemcpyAsync(B.h_ctl, B.d_ctl, kCtlBytes, cudaMemcpyDeviceToHost, st));
   return HC_OK;
 }
 
 hc_status validate_batch(hc_problem* p, const hc_batch_desc* b) {
   if (!p || p->magic != kProblemMagic || !b || b->n_instances < 1 || !b->x_out ||
-      !b->status_out) {
+      !b->status_out || b->step_budget < 0 || b->n_subset < 0 || b->reserved != 0 ||
+      (b->n_subset > 0 && !b->path_ids)) {
     set_err("invalid batch descriptor");
     return HC_ERR_INVALID;
+  }
+  if (b->n_subset > 0) {
+    const int64_t cnt = (int64_t)b->n_instances * b->n_subset;
+    for (int64_t k = 0; k < cnt; ++k)
+      if (b->path_ids[k] < 0 || b->path_ids[k] >= p->paths) {
+        set_err("path_ids: a start index is out of range");
+        return HC_ERR_INVALID;
+      }
   }
   if (p->kind == HC_PARAMETER && !b->p1) {
     set_err("parameter homotopy batch needs p1");
@@ -1110,6 +1420,8 @@ hc_status validate_batch(hc_problem* p, const hc_batch_desc* b) {
 }
 
 void release_batch(hc_batch* bt) {
+  admit_release(bt->p ? bt->p->device : 0, bt->admission);
+  bt->admission.reset();
   for (void* q : bt->dev) cudaFree(q);
   for (void* q : bt->pinned) cudaFreeHost(q);
   if (bt->h_ctl && bt->owns_ctl) pinned_slot_put(bt->h_ctl);
@@ -1185,11 +1497,46 @@ hc_status hc_track_batch(hc_problem* p, const hc_batch_desc* b, hc_batch** out) 
   if (cur != p->device) HC_CUDA(cudaSetDevice(p->device));
   const bool devptrs = (b->flags & HC_DEVICE_PTRS) != 0;
 
+  const int64_t paths_eff = b->n_subset > 0 ? (int64_t)b->n_subset : p->paths;
+  // ---- admission under the device-memory cap
+  std::shared_ptr<AdmitRecord> adm;
+  {
+    AdmitState& a = admit_state(p->device);
+    std::unique_lock<std::mutex> lk(a.mu);
+    if (a.cap > 0) {
+      const int64_t need = hc::instance_device_bytes(p, paths_eff) * b->n_instances;
+      admit_reap(a);
+      while (a.inflight + need > a.cap && !a.recs.empty()) {
+        if (!(b->flags & HC_BLOCKING_ADMIT)) {
+          set_err("admission refused: the batches in flight and this one exceed the memory cap");
+          if (cur != p->device) cudaSetDevice(cur);
+          return HC_ERR_BUSY;
+        }
+        std::shared_ptr<AdmitRecord> oldest = a.recs.front();
+        lk.unlock();
+        cudaEventSynchronize(oldest->done);
+        lk.lock();
+        admit_reap(a);
+      }
+      adm = std::make_shared<AdmitRecord>();
+      adm->bytes = need;
+      if (cudaEventCreateWithFlags(&adm->done, cudaEventDisableTiming) != cudaSuccess) {
+        set_err("cudaEventCreate failed");
+        if (cur != p->device) cudaSetDevice(cur);
+        return HC_ERR_CUDA;
+      }
+      a.inflight += need;
+      a.recs.push_back(adm);
+    }
+  }
+
   hc_batch* bt = new hc_batch;
   bt->p = p;
   bt->stream = (cudaStream_t)b->stream;
   bt->n_inst = b->n_instances;
-  bt->items = bt->n_inst * p->paths;
+  bt->items = bt->n_inst * paths_eff;
+  bt->step_budget = b->step_budget;
+  bt->admission = adm;
   const int64_t items = bt->items;
   cudaStream_t st = bt->stream;
   auto fail = [&](hc_status s) {
@@ -1226,6 +1573,24 @@ hc_status hc_track_batch(hc_problem* p, const hc_batch_desc* b, hc_batch** out) 
   HC_TRYCUDA(cudaEventRecord(bt->ev0, st));
 
   Bufs B;
+  B.paths = paths_eff;
+  B.step_budget = b->step_budget;
+  if (b->n_subset > 0) {
+    void* q;
+    const size_t bytes = sizeof(int64_t) * (size_t)bt->items;
+    HC_TRY(dalloc(bytes, &q));
+    // the caller may free path_ids on return: copy through a pinned buffer
+    // the batch owns, so the upload stays asynchronous
+    void* pin = nullptr;
+    if (cudaMallocHost(&pin, bytes) != cudaSuccess) {
+      set_err("cudaMallocHost failed");
+      return fail(HC_ERR_OOM);
+    }
+    bt->pinned.push_back(pin);
+    std::memcpy(pin, b->path_ids, bytes);
+    HC_TRYCUDA(cudaMemcpyAsync(q, pin, bytes, cudaMemcpyHostToDevice, st));
+    B.path_ids = (const int64_t*)q;
+  }
   // ---- inputs on the device
   if (p->terms) {
     if (devptrs || is_device_ptr(b->p1)) {
@@ -1263,7 +1628,7 @@ hc_status hc_track_batch(hc_problem* p, const hc_batch_desc* b, hc_batch** out) 
   }
   bt->h_ctl = (unsigned long long*)pin;
   bt->owns_ctl = true;
-  std::memset(pin, 0, sizeof(unsigned long long) * 16);
+  std::memset(pin, 0, kCtlBytes);
   B.h_ctl = bt->h_ctl;
   bt->d_ctl = B.d_ctl;
   // ---- the computation
@@ -1274,6 +1639,7 @@ hc_status hc_track_batch(hc_problem* p, const hc_batch_desc* b, hc_batch** out) 
     HC_TRYCUDA(cudaMemcpyAsync(dst, d2h[i], bt->copies[i].bytes, cudaMemcpyDeviceToHost, st));
   }
   HC_TRYCUDA(cudaEventRecord(bt->ev1, st));
+  if (adm) HC_TRYCUDA(cudaEventRecord(adm->done, st));
   if (cur != p->device) cudaSetDevice(cur);
   *out = bt;
   return HC_OK;
@@ -1336,6 +1702,7 @@ hc_status hc_plan_create(hc_problem* p, int32_t n_instances, hc_plan** out) {
   pl->p = p;
   pl->n_inst = n_instances;
   pl->items = pl->n_inst * p->paths;
+  pl->B.paths = p->paths;
   auto fail = [&](hc_status s) {
     free_plan(pl);
     if (cur != p->device) cudaSetDevice(cur);
@@ -1425,6 +1792,10 @@ hc_status hc_plan_run(hc_plan* pl, const hc_batch_desc* b, hc_batch** out) {
     set_err("batch size differs from the plan's");
     return HC_ERR_INVALID;
   }
+  if (b->n_subset != 0 || b->step_budget != 0) {
+    set_err("plans take no start subset and no step budget");
+    return HC_ERR_INVALID;
+  }
   int cur = 0;
   HC_CUDA(cudaGetDevice(&cur));
   if (cur != p->device) HC_CUDA(cudaSetDevice(p->device));
@@ -1462,7 +1833,7 @@ hc_status hc_plan_run(hc_plan* pl, const hc_batch_desc* b, hc_batch** out) {
   }
   bt->h_ctl = (unsigned long long*)pin;
   bt->owns_ctl = true;
-  std::memset(pin, 0, sizeof(unsigned long long) * 16);
+  std::memset(pin, 0, kCtlBytes);
   // runs of one plan share its device buffers: each starts after the
   // previous one's last copy, whatever stream it was enqueued on
   HC_TRYCUDA(cudaStreamWaitEvent(st, pl->done, 0));
@@ -1476,8 +1847,7 @@ hc_status hc_plan_run(hc_plan* pl, const hc_batch_desc* b, hc_batch** out) {
                                  16 * (size_t)p->T, cudaMemcpyDeviceToDevice, st));
   }
   HC_TRYCUDA(cudaGraphLaunch(pl->exec, st));
-  HC_TRYCUDA(cudaMemcpyAsync(bt->h_ctl, pl->B.d_ctl, sizeof(unsigned long long) * 16,
-                             cudaMemcpyDeviceToHost, st));
+  HC_TRYCUDA(cudaMemcpyAsync(bt->h_ctl, pl->B.d_ctl, kCtlBytes, cudaMemcpyDeviceToHost, st));
   const int64_t items = pl->items;
   const size_t xb = sizeof(double) * 2 * p->n * items;
   struct Out {
@@ -1537,6 +1907,8 @@ hc_status hc_poll(hc_batch* b, int64_t timeout_us, hc_batch_result* r) {
     for (auto& c : b->copies)
       if (c.pinned) std::memcpy(c.dst, c.pinned, c.bytes);
     b->done = true;
+    admit_release(b->p->device, b->admission);
+    b->admission.reset();
   }
   if (r) {
     std::memset(r, 0, sizeof(*r));
@@ -1563,7 +1935,27 @@ hc_status hc_poll(hc_batch* b, int64_t timeout_us, hc_batch_result* r) {
     r->device_ms = elapsed(b->ev0, b->ev1);
     r->track_ms = elapsed(b->evk0, b->evk1);
     r->escalate_ms = elapsed(b->evk1, b->evk2);
+    r->untracked = (int64_t)b->h_ctl[16];
+    r->steps_total = (int64_t)b->h_ctl[17];
   }
+  if (b->step_budget > 0 && b->h_ctl[16] > 0) {
+    set_err("the batch's step budget ran out before every path started");
+    return HC_ERR_TIMEOUT;
+  }
+  return HC_OK;
+}
+
+hc_status hc_set_memory_cap(int64_t max_device_bytes) {
+  g_err.clear();
+  if (max_device_bytes < 0) {
+    set_err("negative memory cap");
+    return HC_ERR_INVALID;
+  }
+  int dev = 0;
+  HC_CUDA(cudaGetDevice(&dev));
+  AdmitState& a = admit_state(dev);
+  std::lock_guard<std::mutex> lk(a.mu);
+  a.cap = max_device_bytes;
   return HC_OK;
 }
 
@@ -1662,11 +2054,13 @@ cudaError_t launch_dedupe(int64_t items, int64_t paths, int n, const float2* x32
   if (list) {
     const int grid = (int)std::min<int64_t>((items + 7) / 8, 1024);
     dedupe_list_kernel<<<std::max(grid, 1), 256, 0, st>>>(paths, n, x32, status, tol, list,
-                                                         list_count, out_list, out_count, t_io);
+                                                         list_count, out_list, out_count, t_io,
+                                                         1, nullptr);
   } else {
     const int grid = (int)std::min<int64_t>((items + 255) / 256, 65535);
     dedupe_kernel<<<std::max(grid, 1), 256, 0, st>>>(items, paths, n, x32, status, tol, nullptr,
-                                                    nullptr, out_list, out_count, t_io);
+                                                    nullptr, out_list, out_count, t_io, 1,
+                                                    nullptr);
   }
   return cudaGetLastError();
 }

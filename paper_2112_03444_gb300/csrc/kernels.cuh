@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "dfloat.cuh"
 #include "hc.h"
 #include "hc_device.cuh"
 
@@ -50,17 +51,24 @@ __host__ __device__ constexpr int64_t dense_slot(int n, int d, int L, int j, int
          (dense_mslot(n, mp) & 1);
 }
 
-// Work distribution of a tracking launch: work item = (instance, path),
-// item = instance * paths + path; a lane group takes the next item with one
-// atomicAdd on *queue (retire/refill: a group that finishes a path pulls the
-// next one), until the items are exhausted.
+// Work distribution of a tracking launch: work item = output slot
+// item = instance * paths + k, k < paths; its start path is k, or
+// path_ids[item] when the batch tracks a subset of the starts.  A lane group
+// takes the next item with one atomicAdd on *queue (retire/refill: a group
+// that finishes a path pulls the next one), until the items are exhausted
+// or, with a step budget, the finished paths' steps reach it.
 struct LaunchCommon {
   DevSettings s;
   int64_t n_items;                      // used when count_dev == nullptr
   const unsigned long long* count_dev;  // number of items, read on the device
   const int64_t* items;                 // optional explicit item list
   unsigned long long* queue;            // next item counter (zeroed before launch)
-  int64_t paths;                        // paths per instance
+  int64_t paths;                        // items (output slots) per instance
+  const int64_t* path_ids;              // optional start index of every item
+  const int64_t* path_map;              // optional start index of item k of each instance
+  unsigned long long* step_total;       // steps of the finished paths (atomic)
+  unsigned long long step_budget;       // 0: none; else no item is started once
+                                        // *step_total reaches it (implicit lists only)
   double* x_out;                        // [items][n] complex
   uint8_t* status_out;                  // [items]
   int32_t* steps_out;                   // [items][3]
@@ -86,9 +94,11 @@ struct DenseArgs {
   const cx<float>* D32;
   const cx<double>* D64;
   const cx<double>* E;
+  const cdf* Edf;            // E as double-floats (mixed-precision kernels' residuals)
   int64_t Dstride, Estride;  // complex elements per instance
   cx<double> gamma;
   cx<float> gamma32;         // FP32 copy (FP32 evaluations convert nothing)
+  cdf gammadf;               // double-float copy
 };
 
 // One term of an equation (paper Sec. 6: a coefficient times a product of
@@ -113,6 +123,7 @@ struct TermArgs {
   LaunchCommon c;
   const TermRec* rec;    // [TT][ls]: term slot k of row i at k * ls + i
   const double2* s64;    // FP64 coefficients, same layout
+  const cdf* sdf;        // the same as double-floats (mixed-precision residuals)
   int TT;                // term slots per row (rows padded with zero terms)
   int P;                 // number of parameters
   int ls;                // lane stride of the tables (and V's offset of the 1)

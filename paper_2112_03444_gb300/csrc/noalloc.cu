@@ -127,8 +127,9 @@ __device__ int nested_index(int n, int d, const int* vars, int g) {
 // coef[inst][i][m] (equation i, monomial m of the graded order) into E, D64
 // and D32, computing the index maps on the fly.
 __global__ void stage_canonical_kernel(int64_t n_inst, int n, int d, int M, int MP, int L,
-                                       const double2* __restrict__ coef, double2* E, int64_t Es,
-                                       double2* D64, float2* D32, int64_t Ds) {
+                                       const double2* __restrict__ coef, double2* E,
+                                       hc::cdf* Edf, int64_t Es, double2* D64, float2* D32,
+                                       int64_t Ds) {
   const int64_t total = n_inst * n * M;
   for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < total;
        w += (int64_t)gridDim.x * blockDim.x) {
@@ -138,7 +139,9 @@ __global__ void stage_canonical_kernel(int64_t n_inst, int n, int d, int M, int 
     const double2 c = coef[w];
     int vars[4];
     const int g = unrank_graded(n, m, vars);
-    E[inst * Es + (int64_t)nested_index(n, d, vars, g) * L + i] = c;
+    const int64_t eslot = inst * Es + (int64_t)nested_index(n, d, vars, g) * L + i;
+    E[eslot] = c;
+    Edf[eslot] = hc::to_cdf(hc::cx<double>{c.x, c.y});
     if (g == 0) {
       const int64_t slot = inst * Ds + hc::dense_slot(n, d, L, n, 0, i);
       D64[slot] = c;
@@ -204,13 +207,14 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
   // scratch layout
   const size_t ctl_b = align256(sizeof(unsigned long long) * 16);
   const size_t e_b = align256(sizeof(double2) * Es * n_instances);
+  const size_t edf_b = align256(sizeof(hc::cdf) * Es * n_instances);
   const size_t d64_b = align256(sizeof(double2) * Ds * n_instances);
   const size_t d32_b = align256(sizeof(float2) * Ds * n_instances);
   const size_t esc_b = escalate ? align256(sizeof(int64_t) * items) : 0;
   const size_t dup_b = esc_b;
   const size_t tio_b = escalate ? align256(sizeof(double) * items) : 0;
   const size_t x32_b = escalate ? align256(sizeof(float2) * n * items) : 0;
-  const size_t need = ctl_b + e_b + d64_b + d32_b + esc_b + dup_b + tio_b + x32_b;
+  const size_t need = ctl_b + e_b + edf_b + d64_b + d32_b + esc_b + dup_b + tio_b + x32_b;
   if (need > kNoAllocScratchBytes) {
     char msg[200];
     std::snprintf(msg, sizeof(msg),
@@ -228,6 +232,8 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
   p += ctl_b;
   double2* E = reinterpret_cast<double2*>(p);
   p += e_b;
+  hc::cdf* Edf = reinterpret_cast<hc::cdf*>(p);
+  p += edf_b;
   double2* D64 = reinterpret_cast<double2*>(p);
   p += d64_b;
   float2* D32 = reinterpret_cast<float2*>(p);
@@ -249,14 +255,14 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
     }                                                                                   \
   } while (0)
   // the array keeps the previous call's contents: clear what starts at zero
-  NA_CUDA(cudaMemsetAsync(ctl, 0, ctl_b + e_b + d64_b + d32_b, st));
+  NA_CUDA(cudaMemsetAsync(ctl, 0, ctl_b + e_b + edf_b + d64_b + d32_b, st));
   NA_CUDA(cudaMemsetAsync(steps_out, 0, sizeof(int32_t) * 3 * items, st));
   {
     const int64_t work = (int64_t)n_instances * n * M;
     const int grid = (int)((work + 255) / 256 < 4096 ? (work + 255) / 256 : 4096);
     stage_canonical_kernel<<<grid, 256, 0, st>>>(n_instances, n, degree, M, MP, L,
-                                                 reinterpret_cast<const double2*>(coef), E, Es,
-                                                 D64, D32, Ds);
+                                                 reinterpret_cast<const double2*>(coef), E, Edf,
+                                                 Es, D64, D32, Ds);
     NA_CUDA(cudaGetLastError());
   }
 
@@ -279,10 +285,12 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
   a.D32 = reinterpret_cast<const hc::cx<float>*>(D32);
   a.D64 = reinterpret_cast<const hc::cx<double>*>(D64);
   a.E = reinterpret_cast<const hc::cx<double>*>(E);
+  a.Edf = Edf;
   a.Dstride = Ds;
   a.Estride = Es;
   a.gamma = hc::cx<double>{gamma[0], gamma[1]};
   a.gamma32 = hc::cx<float>{(float)gamma[0], (float)gamma[1]};
+  a.gammadf = hc::split_cdf_host(gamma[0], gamma[1]);
 
   int dev = 0, sms = 0;
   NA_CUDA(cudaGetDevice(&dev));

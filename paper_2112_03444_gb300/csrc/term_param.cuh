@@ -32,7 +32,11 @@ namespace hc {
 // The term tables and the V index positions (1 at LS, p(t) at LS + 1, dp at
 // LS + 1 + P, p0 at LS + 1 + 2P) use the encoding's lane stride LS = a->ls,
 // independent of the kernel's group width L.
-template <int N, int L>
+//
+// The high-precision copy of V (Vd, 16 bytes per entry) holds complex FP64
+// in the all-FP64 kernels and double-floats (dfloat.cuh) in the
+// mixed-precision ones (DF), whose residuals run in double-float arithmetic.
+template <int N, int L, bool DF>
 struct TermEval {
   static constexpr int PARTS = 1;  // one row per lane, no replicas
   static constexpr int ROWL = L;
@@ -43,17 +47,27 @@ struct TermEval {
   cx<double>* Vd;
   unsigned char* acc;  // [N + 2][L] accumulators of cx<R>, this lane at column g.gl
 
-  // constant part of V for this path: the 1, dp and (FP32) p0
+  // constant part of V for this path: the 1, dp and p0 (FP32 copies, and
+  // for DF double-float copies of dp and p0 in Vd)
   __device__ __forceinline__ void init(const Group&) const {
     const int P = a->P, LS = a->ls;
     const double2* p1 = a->p1 + inst * P;
+    cdf* Vdf = reinterpret_cast<cdf*>(Vd);
     if (g.gl == 0) {
       Vf[LS] = mk<float>(1.f, 0.f);
-      Vd[LS] = mk<double>(1.0, 0.0);
+      if constexpr (DF)
+        Vdf[LS] = cdf{1.f, 0.f, 0.f, 0.f};
+      else
+        Vd[LS] = mk<double>(1.0, 0.0);
     }
     for (int l = g.gl; l < P; l += L) {
       const cx<double> d = mk<double>(p1[l].x - a->p0[l].x, p1[l].y - a->p0[l].y);
-      Vd[LS + 1 + P + l] = d;
+      if constexpr (DF) {
+        Vdf[LS + 1 + P + l] = to_cdf(d);
+        Vdf[LS + 1 + 2 * P + l] = to_cdf(mk<double>(a->p0[l].x, a->p0[l].y));
+      } else {
+        Vd[LS + 1 + P + l] = d;
+      }
       Vf[LS + 1 + P + l] = cvt<float>(d);
       Vf[LS + 1 + 2 * P + l] = mk<float>((float)a->p0[l].x, (float)a->p0[l].y);
     }
@@ -82,6 +96,8 @@ struct TermEval {
         Vf[LS + 1 + l] = cfma(mk<float>(t, 0.f), Vf[LS + 1 + P + l], Vf[LS + 1 + 2 * P + l]);
     } else {
       const double2* p1 = a->p1 + inst * P;
+      // DF: the 1 of V is held as a double-float between FP64 residuals
+      if (DF && g.gl == 0) Vd[LS] = mk<double>(1.0, 0.0);
       for (int l = g.gl; l < P; l += L) {
         const double2 q0 = a->p0[l], q1 = p1[l];
         Vd[LS + 1 + l] = mk<double>((1.0 - t) * q0.x + t * q1.x, (1.0 - t) * q0.y + t * q1.y);
@@ -176,15 +192,47 @@ struct TermEval {
     H = h;
     sc = SCALE ? (double)s_abs : 0.0;
   }
+  // The residual in double-float arithmetic (DF): p(t) = p0 + t dp formed
+  // in double-floats from the per-path copies, then every term's product of
+  // factors and coefficient (table sdf) as in residual64.  H is returned
+  // rounded to FP32 (its error is a small multiple of 2^-48 times the
+  // backward-error scale sc).
+  template <bool SCALE>
+  __device__ __forceinline__ void residual_df(const cdf*, int i, double t, cx<float>& H,
+                                              float& sc) const {
+    const int P = a->P, LS = a->ls;
+    cdf* V = reinterpret_cast<cdf*>(Vd);
+    const df tdf = to_df(t);
+    if (g.gl == 0) V[LS] = cdf{1.f, 0.f, 0.f, 0.f};
+    for (int l = g.gl; l < P; l += L)
+      V[LS + 1 + l] = cdf_add(V[LS + 1 + 2 * P + l], cdf_scale(tdf, V[LS + 1 + P + l]));
+    __syncwarp(g.mask);
+    const int ii = i < N ? i : 0;
+    cdf h = cdf_zero();
+    float s_abs = 0.f;
+#pragma unroll 1
+    for (int k = 0; k < a->TT; ++k) {
+      const int64_t r = (int64_t)k * a->ls + ii;
+      const TermRec rc = a->rec[r];
+      cdf prod = V[rc.idx[0]];
+#pragma unroll 1
+      for (int f = 1; f < rc.d; ++f) prod = cdf_mul(prod, V[rc.idx[f]]);
+      const cdf s = a->sdf[r];
+      h = cdf_fma(s, prod, h);
+      if (SCALE) s_abs += cdf_abs_hi(s) * cdf_abs_hi(prod);
+    }
+    H = cdf_to_cf(h);
+    sc = SCALE ? s_abs : 0.f;
+  }
 };
 
-template <int N, int L>
+template <int N, int L, bool DF>
 struct TermProblem {
   const TermArgs* a;
   Group g;
   GroupMem sm;
-  __device__ __forceinline__ TermEval<N, L> hom(int64_t inst) const {
-    return TermEval<N, L>{a, inst, g, sm.vf, sm.vd, sm.acc};
+  __device__ __forceinline__ TermEval<N, L, DF> hom(int64_t inst) const {
+    return TermEval<N, L, DF>{a, inst, g, sm.vf, sm.vd, sm.acc};
   }
 };
 
@@ -199,7 +247,7 @@ __global__ void __launch_bounds__(kBlock) term_param_kernel(const __grid_constan
   extern __shared__ __align__(16) unsigned char smem[];
   const Group g = make_group<L>();
   const GroupMem sm = make_group_mem<L>(smem, a.extra, term_acc_bytes<N, MIXED, L>());
-  TermProblem<N, L> prob{&a, g, sm};
+  TermProblem<N, L, MIXED> prob{&a, g, sm};
   run_tracker<N, L, MIXED>(prob, a.c, g, sm);
 }
 

@@ -25,16 +25,21 @@
 //   MIXED = true : for t < t_endgame the state, the RK4 stages and the Newton
 //     iterations are complex FP32 and no FP64 instruction executes; for
 //     t > t_endgame the state is FP64 and the corrector's residual H is
-//     evaluated in FP64 while the Jacobian and the solve stay FP32 (mixed
-//     precision iterative refinement, converged to the FP64 tolerance within
+//     evaluated in double-float arithmetic (FP32 pairs, about 48 bits, see
+//     dfloat.cuh) -- in FP64 once a step of the path has been rejected
+//     there -- while the Jacobian and the solve stay FP32 (mixed precision
+//     iterative refinement, converged to the FP64 tolerance within
 //     max_newton_ir iterations: each contracts only linearly, by about
-//     cond * 6e-8, so one exact Newton step is worth about two); the
-//     final refinement and the backward error use FP64 residuals the same way.
+//     cond * 6e-8, so one exact Newton step is worth about two); the final
+//     refinement and the backward error use FP64 residuals the same way
+//     (the refinement target, 1e-13, lies below the double-float noise
+//     floor times the condition of most endpoints).
 //     A path whose FP32 steps fall below dt_min_fp32 (the corrector stalls
 //     at the FP32 noise floor near an ill-conditioned stretch) or exhaust
 //     max_steps_fp32 switches to that FP64-residual mode at once.  GB300
-//     issues FP64 FMAs at about 1/74 of its FP32 rate (measured), so FP64 is
-//     kept to the residuals where it buys accuracy.  Paths that still fail,
+//     issues FP64 FMAs at about 1/74 of its FP32 rate (measured), so the
+//     corrector residuals run on the FP32 pipe where their precision
+//     suffices.  Paths that still fail,
 //     paths whose endpoints collide (a path jump) and endpoints whose FP32
 //     condition estimate is suspect are re-tracked by the all-FP64 kernel.
 //
@@ -43,7 +48,9 @@
 //       row[j] = dH_i/dx_j (j < N), H = H_i, Ht = dH_i/dt, all at (x, t)
 //   residual64<SCALE>(xs, i, t, 1-t, H, scale)   H_i in FP64 at the point
 //       xs[0..N) (shared memory), and with SCALE the backward-error
-//       denominator sum |c| |x^a| of row i
+//       denominator sum |c| |x^a| of row i (all-FP64 kernels)
+//   residual_df<SCALE>(xs, i, t, H, scale)         the same in double-float
+//       arithmetic, xs as double-floats, H rounded to FP32 (mixed kernels)
 //   start(path, i)                                 start component x_i(0)
 //   init(g)                                        per-path set-up (once per path)
 // Evaluators read the point from the group's shared copy written by the
@@ -66,8 +73,10 @@ __device__ __forceinline__ void load_vec(const cx<S>* buf, cx<R> (&x)[N]) {
 enum : int { M_RK = 0, M_NEWTON = 1, M_REFINE = 2, M_COND = 3, M_DONE = 4, M_FETCH = 5 };
 
 // Shared memory of one lane group: pv = two pivot-row buffers of the solve,
-// acc = evaluator accumulators (term evaluator only), vd = FP64 copy of the
-// evaluation point (phases with FP64 state), sb = solution scatter buffer,
+// acc = evaluator accumulators (term evaluator only), vd = high-precision
+// copy of the evaluation point (complex FP64 in the all-FP64 kernels,
+// double-floats in the mixed ones, 16 bytes per entry either way; written
+// where a high-precision residual follows), sb = solution scatter buffer,
 // vf = FP32 copy of the point.  vf and vd hold L + extra entries: the point
 // occupies [0, N) and an evaluator may keep its own per-path values behind
 // index L.  Size: group_smem_bytes (kernels.cuh).
@@ -136,6 +145,9 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
   cx<double> xpd = czero<double>(); // corrector iterate (FP64 state)
   bool step_ok = true;
   bool first_fetch = true;
+  // mixed kernels: the FP64-state corrector's residual runs in double-float
+  // arithmetic until the path's first rejected FP64-state step, then in FP64
+  bool res64 = false;
   float cond_inorm = 0.f, cond_anorm = 0.f, be = 0.f;
 
   cx<R> row[N + 1];
@@ -145,6 +157,14 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
 
   // hi is constant true in the plain FP64 kernel; say so to the compiler
   auto HI = [&]() { return !MIXED || hi; };
+  // this lane's entry of the high-precision point copy, as double-floats
+  // (as_df) or complex FP64
+  auto put_hi = [&](const cx<double>& v, bool as_df) {
+    if (MIXED && as_df)
+      reinterpret_cast<cdf*>(sm.vd)[g.gl] = to_cdf(v);
+    else
+      sm.vd[g.gl] = v;
+  };
   auto begin_step = [&]() {
     if (HI()) {
       const bool last = dt >= 1.0 - t;
@@ -179,6 +199,7 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
     ++nrej;
     consec = 0;
     if (HI()) {
+      res64 = true;
       dt *= 0.5;
       if (dt < s.dt_min) {
         status = ST_FAIL_STEP;
@@ -219,6 +240,7 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
       if (g.gl == 0) {
         c.status_out[item] = (uint8_t)status;
         if (c.be_out) c.be_out[item] = (double)be;
+        if (c.step_budget) atomicAdd(c.step_total, (unsigned long long)(nacc + nrej));
         if (MIXED) {
           c.steps_out[item * 3 + 0] = nacc;
           c.steps_out[item * 3 + 1] = nrej;
@@ -260,6 +282,12 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
       mode = M_FETCH;
     }
     if (mode == M_FETCH) {
+      if (c.step_budget && !c.items) {
+        // the budget stops new paths of the launch; started ones finish
+        unsigned long long spent = 0;
+        if (g.gl == 0) spent = *reinterpret_cast<volatile unsigned long long*>(c.step_total);
+        if (__shfl_sync(g.mask, spent, leader) >= c.step_budget) break;
+      }
       unsigned long long q = 0;
       if (c.spread && first_fetch) {
         // ticket = slot * blocks + block: consecutive items on different blocks
@@ -274,7 +302,8 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
       if ((int64_t)q >= total) break;
       item = c.items ? c.items[q] : (int64_t)q;
       const int64_t inst = item / c.paths;
-      const int64_t path = item - inst * c.paths;
+      const int64_t k_in = item - inst * c.paths;
+      const int64_t path = c.path_ids ? c.path_ids[item] : c.path_map ? c.path_map[k_in] : k_in;
       hom = prob.hom(inst);
       hom.init(g);  // per-path constants of the evaluator (shared memory)
       // a path handed over by the FP32 tier resumes from its last accepted point
@@ -296,6 +325,7 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
       tf = (float)t;
       dtf = (float)s.dt_init;
       consec = nacc = nrej = nnewt = status = 0;
+      res64 = false;
       be = 0.f;
       if (t >= 1.0)
         enter_refine();
@@ -325,7 +355,7 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
         ter = (R)te;
         omt = (R)(1.0 - te);
         const cx<double> p = xd + (cst * h) * cvt<double>(kprev);
-        if (act) sm.vd[g.gl] = p;
+        if (!MIXED && act) sm.vd[g.gl] = p;  // the FP32 evaluation reads vf only
         if (act) sm.vf[g.gl] = cvt<float>(p);
       } else {
         const float cst = (stage == 0) ? 0.f : (stage == 3 ? 1.f : 0.5f);
@@ -341,7 +371,7 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
         ter = (R)t1;
         omt = (R)(1.0 - t1);
         need64 = MIXED;
-        if (act) sm.vd[g.gl] = xpd;
+        if (act) put_hi(xpd, !res64);
         if (act) sm.vf[g.gl] = cvt<float>(xpd);
       } else {
         ter = (R)t1f;
@@ -350,7 +380,7 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
       }
     } else {  // M_REFINE, M_COND: at the endpoint, t = 1
       need64 = (mode == M_REFINE);
-      if (act) sm.vd[g.gl] = xd;
+      if (act && (need64 || !MIXED)) put_hi(xd, false);
       if (act) sm.vf[g.gl] = cvt<float>(xd);
     }
     __syncwarp(g.mask);
@@ -378,10 +408,17 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
         const int grow = g.gl & (HOM::ROWL - 1);
         row[N] = mk<R>((grow < N && grow == stage) ? R(1) : R(0), R(0));
       } else if (need64) {
-        cx<double> H64;
-        double sc;
-        hom.template residual64<false>(sm.vd, g.gl, te, 1.0 - te, H64, sc);
-        row[N] = cvt<R>(-H64);
+        if (MIXED && mode == M_NEWTON && !res64) {
+          cx<float> Hf;
+          float sc;
+          hom.template residual_df<false>(reinterpret_cast<const cdf*>(sm.vd), g.gl, te, Hf, sc);
+          row[N] = cvt<R>(-Hf);
+        } else {
+          cx<double> H64;
+          double sc;
+          hom.template residual64<false>(sm.vd, g.gl, te, 1.0 - te, H64, sc);
+          row[N] = cvt<R>(-H64);
+        }
       } else {
         row[N] = -H;
       }
@@ -475,7 +512,7 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
           mode = M_DONE;
         } else {
           __syncwarp(g.mask);
-          if (act) sm.vd[g.gl] = xd;
+          if (act) put_hi(xd, false);
           __syncwarp(g.mask);
           cx<double> H64;
           double sc;

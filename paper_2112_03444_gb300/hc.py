@@ -60,7 +60,8 @@ class hc_problem_desc(ctypes.Structure):
                 ("term_param", ctypes.c_void_p), ("n_params", ctypes.c_int32),
                 ("kind", ctypes.c_int32), ("gamma", ctypes.c_double * 2),
                 ("p0", ctypes.c_void_p), ("n_start", ctypes.c_int64),
-                ("start", ctypes.c_void_p), ("settings", hc_settings)]
+                ("start", ctypes.c_void_p), ("settings", hc_settings),
+                ("n_sym", ctypes.c_int32), ("sym_mask", ctypes.c_uint32 * 4)]
 
 
 class hc_batch_desc(ctypes.Structure):
@@ -68,7 +69,9 @@ class hc_batch_desc(ctypes.Structure):
                 ("coef", ctypes.c_void_p), ("p1", ctypes.c_void_p),
                 ("stream", ctypes.c_void_p), ("x_out", ctypes.c_void_p),
                 ("status_out", ctypes.c_void_p), ("steps_out", ctypes.c_void_p),
-                ("be_out", ctypes.c_void_p)]
+                ("be_out", ctypes.c_void_p), ("step_budget", ctypes.c_int64),
+                ("n_subset", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("path_ids", ctypes.c_void_p)]
 
 
 class hc_batch_result(ctypes.Structure):
@@ -80,7 +83,8 @@ class hc_batch_result(ctypes.Structure):
                 ("esc_accepted", ctypes.c_int64), ("esc_rejected", ctypes.c_int64),
                 ("esc_newton", ctypes.c_int64),
                 ("device_ms", ctypes.c_double), ("track_ms", ctypes.c_double),
-                ("escalate_ms", ctypes.c_double)]
+                ("escalate_ms", ctypes.c_double), ("untracked", ctypes.c_int64),
+                ("steps_total", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -101,6 +105,8 @@ _lib.hc_poll.restype = ctypes.c_int32
 _lib.hc_poll.argtypes = [_P, ctypes.c_int64, ctypes.POINTER(hc_batch_result)]
 _lib.hc_destroy.restype = None
 _lib.hc_destroy.argtypes = [_P]
+_lib.hc_set_memory_cap.restype = ctypes.c_int32
+_lib.hc_set_memory_cap.argtypes = [ctypes.c_int64]
 
 _lib.hc_measure_fma_peak.restype = ctypes.c_int32
 _lib.hc_measure_fma_peak.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
@@ -161,7 +167,8 @@ EXPORTED = ("hc_status_string", "hc_last_error", "hc_default_settings", "hc_crea
             "hc_problem_paths", "hc_problem_query", "hc_track_batch", "hc_poll", "hc_destroy",
             "hc_measure_fma_peak", "hc_track_dense_noalloc", "hc_server_default_config",
             "hc_server_create", "hc_server_submit", "hc_server_wait", "hc_server_stats",
-            "hc_autotune", "hc_plan_create", "hc_plan_run")
+            "hc_autotune", "hc_plan_create", "hc_plan_run", "hc_set_memory_cap",
+            "hc_batched_solve", "hc_monodromy_solve")
 
 
 def problem_query(problem: int) -> dict:
@@ -237,6 +244,73 @@ def track_dense_noalloc(n, degree, gamma, settings, n_instances, coef, x_out, st
                                            stream))
 
 
+_lib.hc_batched_solve.restype = ctypes.c_int32
+_lib.hc_batched_solve.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, _P, _P, _P, _P,
+                                  _P]
+
+
+def batched_solve(A, b, x, info=None, stream=None) -> int:
+    """hc_batched_solve on torch CUDA tensors: A [batch, n, n], b and x
+    [batch, n], complex64 (FP32) or complex128 (FP64); info int32 [batch]."""
+    batch, n = int(A.shape[0]), int(A.shape[-1])
+    fp32 = 1 if str(A.dtype).endswith("complex64") else 0
+    return int(_lib.hc_batched_solve(n, batch, fp32, _addr(A), _addr(b), _addr(x), _addr(info),
+                                     stream))
+
+
+class hc_monodromy_desc(ctypes.Structure):
+    _fields_ = [("family", ctypes.c_void_p), ("x0", ctypes.c_void_p), ("p0", ctypes.c_void_p),
+                ("seed", ctypes.c_uint64), ("stall_loops", ctypes.c_int32),
+                ("max_loops", ctypes.c_int32), ("loops_per_round", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("max_solutions", ctypes.c_int64),
+                ("out", ctypes.c_void_p)]
+
+
+class hc_monodromy_info(ctypes.Structure):
+    _fields_ = [("loops", ctypes.c_int32), ("rounds", ctypes.c_int32),
+                ("paths_tracked", ctypes.c_int64), ("seconds", ctypes.c_double)]
+
+
+_lib.hc_monodromy_solve.restype = ctypes.c_int32
+_lib.hc_monodromy_solve.argtypes = [ctypes.POINTER(hc_monodromy_desc),
+                                    ctypes.POINTER(ctypes.c_int64),
+                                    ctypes.POINTER(hc_monodromy_info)]
+
+
+def monodromy_solve(system, x0, p0, seed=0, stall_loops=10, max_loops=400, loops_per_round=4,
+                    max_solutions=100_000, symmetries=(), settings=None):
+    """hc_monodromy_solve: (solutions [S, n] complex128, info dict)."""
+    if isinstance(settings, dict) or settings is None:
+        settings = default_settings(**(settings or {}))
+    keep = [_host(system.term_eq, np.int32), _host(system.term_coef, np.complex128),
+            _host(system.term_exp, np.uint8), _host(system.term_param, np.int32),
+            _host(x0, np.complex128), _host(p0, np.complex128)]
+    eq, cf, ex, pa, xa, pa0 = keep
+    d = hc_problem_desc()
+    d.n, d.n_terms = int(system.n), int(system.n_terms)
+    d.term_eq, d.term_coef, d.term_exp = eq.ctypes.data, cf.ctypes.data, ex.ctypes.data
+    d.max_pfac = int(system.max_pfac)
+    d.term_param = pa.ctypes.data if pa.size else None
+    d.n_params = int(system.n_params)
+    d.kind = HC_PARAMETER
+    d.settings = settings
+    d.n_sym = len(symmetries)
+    for k, m in enumerate(symmetries):
+        d.sym_mask[k] = int(m)
+    out = np.zeros((int(max_solutions), d.n), np.complex128)
+    m = hc_monodromy_desc()
+    m.family = ctypes.addressof(d)
+    m.x0, m.p0 = xa.ctypes.data, pa0.ctypes.data
+    m.seed, m.stall_loops, m.max_loops = int(seed), int(stall_loops), int(max_loops)
+    m.loops_per_round, m.max_solutions, m.out = int(loops_per_round), int(max_solutions), \
+        out.ctypes.data
+    cnt = ctypes.c_int64()
+    inf = hc_monodromy_info()
+    _check(_lib.hc_monodromy_solve(ctypes.byref(m), ctypes.byref(cnt), ctypes.byref(inf)),
+           "hc_monodromy_solve")
+    return out[:cnt.value].copy(), {k: getattr(inf, k) for k, _ in inf._fields_}
+
+
 def measure_fma_peak(fp64: bool, iters: int = 20000):
     """(FLOP/s, ms) of the device's FP32 or FP64 FMA pipe (own microbenchmark)."""
     f = ctypes.c_double()
@@ -280,9 +354,18 @@ def track_batch(problem: int, desc: hc_batch_desc) -> int:
 
 
 def poll(batch: int, timeout_us: int = -1):
+    """(code, result): HC_OK, HC_PENDING, or HC_ERR_TIMEOUT (done, step
+    budget exhausted; result filled); other codes raise."""
     r = hc_batch_result()
-    code = _check(_lib.hc_poll(batch, int(timeout_us), ctypes.byref(r)), "hc_poll")
+    code = _lib.hc_poll(batch, int(timeout_us), ctypes.byref(r))
+    if code != HC_ERR_TIMEOUT:
+        _check(code, "hc_poll")
     return code, r
+
+
+def set_memory_cap(max_device_bytes: int) -> None:
+    """hc_set_memory_cap on the current device (0: no cap)."""
+    _check(_lib.hc_set_memory_cap(int(max_device_bytes)), "hc_set_memory_cap")
 
 
 def destroy(handle: int) -> None:
@@ -313,10 +396,11 @@ class Problem:
 
     system: an ``inputs.TermSystem``.  kind: HC_TOTAL_DEGREE (gamma) or
     HC_PARAMETER (p0, start).  settings: hc_settings or dict of overrides.
+    symmetries: HC_PARAMETER sign masks (hc_problem_desc.sym_mask).
     """
 
     def __init__(self, system, kind=HC_TOTAL_DEGREE, gamma=1 + 0j, p0=None, start=None,
-                 settings=None):
+                 settings=None, symmetries=()):
         if isinstance(settings, dict) or settings is None:
             settings = default_settings(**(settings or {}))
         self.system = system
@@ -345,6 +429,9 @@ class Problem:
         d.n_start = 0 if sa is None else int(sa.shape[0])
         d.start = None if sa is None else sa.ctypes.data
         d.settings = settings
+        d.n_sym = len(symmetries)
+        for k, m in enumerate(symmetries):
+            d.sym_mask[k] = int(m)
         self.settings = settings
         self.h = create_problem(d)
         self.paths = problem_paths(self.h)
@@ -357,8 +444,12 @@ class Problem:
     def __del__(self):
         self.close()
 
-    def _desc(self, n_instances, coef, p1, stream, x_out, status_out, steps_out, be_out, device):
+    def _desc(self, n_instances, coef, p1, stream, x_out, status_out, steps_out, be_out, device,
+              path_ids=None, step_budget=0, blocking=False):
         I, P, n = int(n_instances), self.paths, self.n
+        if path_ids is not None:
+            path_ids = _host(path_ids, np.int64).reshape(I, -1)
+            P = path_ids.shape[1]
         if not device:
             x_out = np.zeros((I, P, n), np.complex128) if x_out is None else x_out
             status_out = np.zeros((I, P), np.uint8) if status_out is None else status_out
@@ -370,7 +461,10 @@ class Problem:
                 p1 = _host(p1, np.complex128)
         b = hc_batch_desc()
         b.n_instances = I
-        b.flags = HC_DEVICE_PTRS if device else 0
+        b.flags = (HC_DEVICE_PTRS if device else 0) | (HC_BLOCKING_ADMIT if blocking else 0)
+        b.step_budget = int(step_budget)
+        b.n_subset = 0 if path_ids is None else P
+        b.path_ids = None if path_ids is None else path_ids.ctypes.data
         b.coef = _addr(coef)
         b.p1 = _addr(p1)
         b.stream = stream
@@ -378,14 +472,19 @@ class Problem:
         b.status_out = _addr(status_out)
         b.steps_out = _addr(steps_out)
         b.be_out = _addr(be_out)
-        return b, dict(x=x_out, status=status_out, steps=steps_out, be=be_out, coef=coef, p1=p1)
+        return b, dict(x=x_out, status=status_out, steps=steps_out, be=be_out, coef=coef, p1=p1,
+                       path_ids=path_ids)
 
     def track(self, n_instances=1, coef=None, p1=None, stream=None, device_out=None,
-              x_out=None, status_out=None, steps_out=None, be_out=None, device=False):
+              x_out=None, status_out=None, steps_out=None, be_out=None, device=False,
+              path_ids=None, step_budget=0, blocking=False):
         """Enqueue a batch; returns a Batch.  Host mode (default) allocates numpy
-        outputs; with device=True pass torch CUDA tensors (inputs and outputs)."""
+        outputs; with device=True pass torch CUDA tensors (inputs and outputs).
+        path_ids [n_instances, k]: track only those starts (outputs hold k
+        paths per instance); step_budget: hc_batch_desc.step_budget;
+        blocking: HC_BLOCKING_ADMIT."""
         b, bufs = self._desc(n_instances, coef, p1, stream, x_out, status_out, steps_out, be_out,
-                             device)
+                             device, path_ids, step_budget, blocking)
         h = track_batch(self.h, b)
         return Batch(h, self, bufs)
 
@@ -459,8 +558,9 @@ class Batch:
 
     def poll(self, timeout_us=-1):
         code, r = poll(self.h, timeout_us)
-        if code == HC_OK:
+        if code in (HC_OK, HC_ERR_TIMEOUT):
             self.result = r.as_dict()
+            self.code = code
         return code
 
     def wait(self):

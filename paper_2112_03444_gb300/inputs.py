@@ -219,6 +219,12 @@ class ParamFamily:
     unit_groups: list         # unknown-index groups constrained by q.q = 1
     name: str
 
+    @property
+    def sign_masks(self) -> list:
+        """Bit masks of the unit-quaternion groups: the rotation R(q) is
+        quadratic in q, so negating a group maps solutions to solutions."""
+        return [sum(1 << j for j in grp) for grp in self.unit_groups]
+
 
 def triangulation_family(views: int = 4) -> ParamFamily:
     """N-view optimal triangulation by Lagrange multipliers (paper Sec. 4).
@@ -524,3 +530,24 @@ def dense_parameter_family(n: int, d: int, seed: int):
         elif e[i] == d and e.sum() == d:
             p0[k] = g
     return sys_, base.term_coef.copy(), p0
+
+
+# The dense total-degree sweep: quadratics n = 8, 10, 12 (256 / 1024 / 4096
+# paths) and cubics n = 6, 8 (729 / 6561 paths), 16 systems per size, the
+# stand-in for the paper's Table 1 benchmark systems at several sizes.
+DENSE_SWEEP_SIZES = ((8, 2), (10, 2), (12, 2), (6, 3), (8, 3))
+DENSE_SWEEP_SYSTEMS = 16
+DENSE_SWEEP_SEED0 = 100
+
+
+def dense_sweep(rank: int = 0, systems: int = DENSE_SWEEP_SYSTEMS):
+    """Per size class: dict(n, d, base, coefs [systems, T], seeds, gamma).
+
+    Replica `rank` gets its own seeds; all systems of a class share the
+    class's gamma (the homotopy constant of its first seed)."""
+    out = []
+    for si, (n, d) in enumerate(DENSE_SWEEP_SIZES):
+        seeds = [DENSE_SWEEP_SEED0 + 1000 * rank + 100 * si + k for k in range(systems)]
+        base, coefs = dense_batch(n, d, seeds)
+        out.append(dict(n=n, d=d, base=base, coefs=coefs, seeds=seeds, gamma=unit_gamma(seeds[0])))
+    return out

@@ -36,7 +36,8 @@ def test_every_declared_symbol_is_exported(hc):
 def test_struct_layouts_match_header_sizes(hc):
     # hc_settings: 14 doubles + 10 int32 = 152 bytes
     assert ctypes.sizeof(hc.hc_settings) == 152
-    assert ctypes.sizeof(hc.hc_batch_result) == 16 * 8
+    assert ctypes.sizeof(hc.hc_batch_result) == 18 * 8
+    assert ctypes.sizeof(hc.hc_batch_desc) == 4 + 4 + 7 * 8 + 8 + 4 + 4 + 8
 
 
 def test_default_settings_and_strings(hc):
@@ -129,3 +130,12 @@ def test_plan_calls_reject_null_handles(hc):
     assert hc._lib.hc_plan_create(None, 1, ctypes.byref(h)) == hc.HC_ERR_INVALID
     b = hc.hc_batch_desc()
     assert hc._lib.hc_plan_run(None, ctypes.byref(b), ctypes.byref(h)) == hc.HC_ERR_INVALID
+
+
+def test_memory_cap_rejects_negative(hc):
+    assert hc._lib.hc_set_memory_cap(-1) == hc.HC_ERR_INVALID
+
+
+def test_batch_descriptor_defaults_are_zero(hc):
+    b = hc.hc_batch_desc()
+    assert b.step_budget == 0 and b.n_subset == 0 and b.reserved == 0 and not b.path_ids

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
-from hcmatch import same_set, match, distinct
+from hcmatch import same_set, match, distinct, rel_dist
 
 pytestmark = pytest.mark.gpu
 
@@ -115,20 +115,49 @@ def test_poll_nonblocking_then_done(hc):
     assert bt.result["finite"] == 4
 
 
-@pytest.mark.parametrize("n,d,ninst", [(8, 3, 16), (12, 2, 4)])
-def test_no_root_reported_twice(hc, n, d, ninst):
-    """Full batches of the bench's largest classes (mixed tiers, duplicate
-    detection and re-tracking on): within every instance the finite
-    endpoints are pairwise distinct, and the Bezout count is reached up to
-    the few paths that also fail in FP64 (a property at any size)."""
+def _golden():
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "dense_sweep_oracle.json")
+    return json.load(open(path))
+
+
+@pytest.mark.parametrize("ci", range(5), ids=["q8", "q10", "q12", "c6", "c8"])
+def test_dense_sweep_matches_oracle_golden(hc, ci):
+    """The benchmarked sweep (16 systems per size class, mixed precision, the
+    bench's seeds) against the oracle's stored outcome on every path
+    (tests/golden/dense_sweep_oracle.json):
+      - every path the oracle ends at a finite root, the GPU does too;
+      - within every system the GPU's finite roots are pairwise distinct
+        (so, the oracle's root set being distinct too, the finite sets match);
+      - a finite GPU root on a start the oracle fails is a root by the
+        oracle's own evaluation (backward error <= 1e-10, cond_1 <= 1e12);
+      - sampled starts end within 1e-8 of the oracle's endpoint, tracked live."""
     from paper_2112_03444_gb300 import inputs
-    seeds = [100 + k for k in range(ninst)]
-    base, coefs = inputs.dense_batch(n, d, seeds)
-    pr = hc.Problem(base, gamma=inputs.unit_gamma(seeds[0]))
-    b = pr.track(n_instances=ninst, coef=coefs).wait()
-    total = 0
-    for s in range(ninst):
+    w = inputs.dense_sweep(0)[ci]
+    g = _golden()["classes"][ci]
+    assert (g["n"], g["d"]) == (w["n"], w["d"])
+    pr = hc.Problem(w["base"], gamma=w["gamma"])
+    b = pr.track(n_instances=len(w["seeds"]), coef=w["coefs"]).wait()
+    P = w["d"] ** w["n"]
+    for s, gs in enumerate(g["systems"]):
+        assert gs["seed"] == w["seeds"][s]
+        assert gs["distinct_finite"] == gs["counts"]["finite"]
         fin = (b.status[s] & 0x7F) == hc.PATH_FINITE
-        total += int(fin.sum())
+        ofin = np.ones(P, bool)
+        for p, _ in gs["not_finite"]:
+            ofin[p] = False
+        assert not np.any(ofin & ~fin), (s, np.nonzero(ofin & ~fin)[0])
         assert distinct(b.x[s][fin]) == int(fin.sum()), s
-    assert total >= ninst * d ** n - max(2, ninst * d ** n // 10000), total
+        extra = np.nonzero(fin & ~ofin)[0]
+        if len(extra):
+            op = oracle.OracleProblem(w["base"], gamma=w["gamma"], coef=w["coefs"][s])
+            for p in extra:
+                assert op.backward_error(b.x[s][p]) <= 1e-10, (s, int(p))
+                assert op.cond1(b.x[s][p]) <= 1e12, (s, int(p))
+    rng = np.random.default_rng(ci)
+    ids = rng.choice(P, size=min(24, P), replace=False)
+    ref = _oracle(w["base"], w["coefs"][0], w["gamma"], path_ids=ids)
+    rf = (ref["status"] & 0x7F) == oracle.FINITE
+    assert np.max(rel_dist(b.x[0][ids][rf], ref["x"][rf]), initial=0.0) <= TOL

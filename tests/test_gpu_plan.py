@@ -54,7 +54,8 @@ def test_dense_plan_replays_match_track_batch(hc):
     for i in range(3):
         fin = (a.status[i] & 0x7F) == hc.PATH_FINITE
         rfin = (ref["status"] & 0x7F) == oracle.FINITE
-        assert same_set(a.x[i][fin], ref["x"][rfin], 1e-8)
+        ok, msg = same_set(a.x[i][fin], ref["x"][rfin], 1e-8)
+        assert ok, (i, msg)
     plan.close()
 
 

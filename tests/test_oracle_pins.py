@@ -351,3 +351,80 @@ def test_track_is_deterministic_across_thread_counts():
     a = pr.track(threads=1)
     b = pr.track(threads=8)
     assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["status"], b["status"])
+
+
+# ---------------------------------------------------------------- classification quantities
+def test_backward_error_closed_form_values():
+    """Hand-computed backward errors max_i |F_i(x)| / sum_k |c_k| |x^a_k|.
+
+    F = (1+i) x - 2 at x = 1: |F| = |-1+i| = sqrt 2, denominator
+    |1+i| * 1 + |-2| = sqrt 2 + 2.  Dropping the |c| factor would give
+    sqrt 2 / 3; returning 0 or omitting the constant term fails too."""
+    pr = OracleProblem(poly_system(1, [{(1,): 1 + 1j, (0,): -2.0}]))
+    be = pr.backward_error(np.array([1.0 + 0j]))
+    assert abs(be - math.sqrt(2) / (math.sqrt(2) + 2)) < 1e-15
+    # x^2 - 4 at x = 2 + delta: |4 delta + delta^2| / ((2 + delta)^2 + 4)
+    pr = OracleProblem(poly_system(1, [{(2,): 1.0, (0,): -4.0}]))
+    for delta in (1e-3, -2e-5j, 0.5 + 0.25j):
+        x = 2 + delta
+        want = abs(4 * delta + delta ** 2) / (abs(x) ** 2 + 4)
+        # F is formed with cancellation: its rounding is a few ulps of the
+        # denominator, so the bound is absolute
+        assert abs(pr.backward_error(np.array([x])) - want) <= 1e-15
+    # the maximum over equations, each scaled by its own terms (point (1, 3)):
+    # F1 = x1 - 1 -> 0; F2 = 2 x1 x2 - 5 -> 1 / (6 + 5)
+    pr = OracleProblem(poly_system(2, [{(1, 0): 1.0, (0, 0): -1.0},
+                                       {(1, 1): 2.0, (0, 0): -5.0}]))
+    assert abs(pr.backward_error(np.array([1.0, 3.0 + 0j])) - 1 / 11) < 1e-15
+    # and exactly zero at the exact root
+    assert pr.backward_error(np.array([1.0, 2.5 + 0j])) == 0.0
+
+
+def _linear_system(A, b):
+    """F(x) = A x - b as a term list (its Jacobian is A everywhere)."""
+    n = A.shape[0]
+    polys = []
+    for i in range(n):
+        poly = {(0,) * n: -b[i]}
+        for j in range(n):
+            if A[i, j] != 0:
+                e = [0] * n
+                e[j] = 1
+                poly[tuple(e)] = A[i, j]
+        polys.append(poly)
+    return poly_system(n, polys)
+
+
+def test_cond1_closed_form_values():
+    """cond_1(A) = ||A||_1 ||A^-1||_1 with the modulus of complex entries.
+
+    diag(3+4i, 1): 5 * 1 = 5 (|Re| + |Im| would give 7).  The lower
+    triangular L = [[1,0,0],[0,10,0],[50,0,100]] has column sums 51, 10, 100
+    and L^-1 = [[1,0,0],[0,0.1,0],[-0.5,0,0.01]] column sums 1.5, 0.1, 0.01:
+    cond_1 = 150 (an inverse left out gives 100).  For U below the 1-norm
+    and the infinity-norm condition numbers differ, so a transposed norm
+    fails there."""
+    A = np.diag([3 + 4j, 1.0])
+    pr = OracleProblem(_linear_system(A, np.ones(2)))
+    assert abs(pr.cond1(np.zeros(2, complex)) - 5.0) < 1e-14
+    L = np.array([[1, 0, 0], [0, 10, 0], [50, 0, 100]], complex)
+    for M, want in ((L, 150.0), (L.T, 150.0)):
+        pr = OracleProblem(_linear_system(M, np.ones(3)))
+        assert abs(pr.cond1(np.zeros(3, complex)) - want) < 1e-12
+    U = np.array([[2, 7, 0], [0, 1, 3], [0, 0, 4]], complex)
+    pr = OracleProblem(_linear_system(U, np.ones(3)))
+    want = np.linalg.norm(U, 1) * np.linalg.norm(np.linalg.inv(U), 1)
+    assert abs(pr.cond1(np.zeros(3, complex)) - want) < 1e-12 * want
+    assert abs(want - np.linalg.norm(U, np.inf) * np.linalg.norm(np.linalg.inv(U), np.inf)) > 1
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_cond1_matches_library_on_random_jacobians(seed):
+    """At a random point of a dense quadratic system, cond_1(dF/dx) equals
+    numpy's 1-norm condition number of the oracle's own Jacobian (the
+    Jacobian itself is pinned by finite differences above)."""
+    sys_ = inputs.dense_system(4, 2, seed)
+    pr = OracleProblem(sys_)
+    x = inputs.random_complex(4, seed + 50)
+    _, Hx, _ = pr.eval(x, 1.0)
+    assert abs(pr.cond1(x) - np.linalg.cond(Hx, 1)) <= 1e-10 * np.linalg.cond(Hx, 1)
