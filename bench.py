@@ -451,6 +451,9 @@ def run_gpu(args):
                                        "launches / their summed launch time, against the FP64 "
                                        "FMA throughput from hc_measure_fma_peak(fp64=1)"))
 
+    # ---- configs 3 and 4 at their scale (extra keys; the headline stays the sweep)
+    params = None if args.no_param_legs else param_legs(hc, args)
+
     # ---- the standalone fused batched solver against cuBLAS (paper Fig. 3)
     solve = None if args.no_solve_leg else solve_leg(hc, torch, stream)
 
@@ -497,6 +500,7 @@ def run_gpu(args):
                                 "counters"),
         serving=serving,
         batched_solve=solve,
+        parameter_workloads=params,
         clocks=clocks,
     )
     if rank == 0 and not args.no_cpu:
@@ -513,6 +517,80 @@ def run_gpu(args):
 
 def bufs_host(bufs):
     return [dict(x=b["x"].cpu().numpy()) for b in bufs]
+
+
+# ---------------------------------------------------------------- configs 3 and 4 at scale
+def _status_diff(got, want):
+    return int(np.sum((np.asarray(got) & 0x7F) != (np.asarray(want) & 0x7F)))
+
+
+def param_legs(hc, args):
+    """4-view triangulation with tri_instances scenes in one batch, and the
+    trifocal pose with trifocal_instances scenes in one batch (orbit
+    representatives of the quaternion signs), both mixed precision.  Parity:
+    two triangulation instances against the FP64 oracle run live on all 296
+    starts; the first two trifocal instances are the scenes of the stored
+    oracle golden (tests/golden/trifocal_oracle.npz), compared on all 5344
+    starts through its endpoint projections."""
+    import oracle
+    from scipy.spatial import cKDTree
+    out = {}
+    # ---- 4-view triangulation
+    fam = inputs.triangulation_family(4)
+    z = np.load(os.path.join(START_DIR, "triangulation4.npz"))
+    I = args.tri_instances
+    p1 = np.stack([inputs.triangulation_scene(20_000 + k)[0] for k in range(I)])
+    pr = hc.Problem(fam.system, kind=hc.HC_PARAMETER, p0=z["p0"], start=z["start"])
+    pr.track(n_instances=min(I, 64), p1=p1[:64]).wait()                  # warm-up
+    t0 = time.perf_counter()
+    b = pr.track(n_instances=I, p1=p1).wait()
+    wall = time.perf_counter() - t0
+    r = b.result
+    checks = []
+    for k in (0, I - 1):
+        ref = oracle.OracleProblem(fam.system, kind=oracle.KIND_PARAMETER, p0=z["p0"],
+                                   p1=p1[k]).track(start=z["start"])
+        checks.append(dict(instance=k, status_diffs=_status_diff(b.status[k], ref["status"]),
+                           gpu=oracle.status_counts(b.status[k]),
+                           oracle=oracle.status_counts(ref["status"])))
+    out["triangulation4"] = dict(
+        instances=I, paths=r["paths"], device_ms=r["device_ms"], wall_ms=wall * 1e3,
+        systems_per_s=I / (r["device_ms"] * 1e-3), paths_per_s=r["finite"] / (r["device_ms"] * 1e-3),
+        finite=r["finite"], escalated=r["escalated"], oracle_checks=checks,
+        form="one hc_track_batch, mixed precision")
+    del b
+    # ---- trifocal pose, unknown focal length
+    fam = inputs.trifocal_family()
+    z = np.load(os.path.join(START_DIR, "trifocal_f.npz"))
+    gold = np.load(GOLDEN.replace("dense_sweep_oracle.json", "trifocal_oracle.npz"))
+    I = args.trifocal_instances
+    seeds = [int(sd) for sd in gold["scenes"]] + [30_000 + k for k in range(I - len(gold["scenes"]))]
+    p1 = np.stack([inputs.trifocal_scene(sd)[0] for sd in seeds])
+    pr = hc.Problem(fam.system, kind=hc.HC_PARAMETER, p0=z["p0"], start=z["start"],
+                    symmetries=fam.sign_masks)
+    t0 = time.perf_counter()
+    b = pr.track(n_instances=I, p1=p1).wait()
+    wall = time.perf_counter() - t0
+    r = b.result
+    c = gold["proj_coef"]
+    checks = []
+    for k in range(len(gold["scenes"])):
+        ost = gold[f"status{k}"] & 0x7F
+        gst = b.status[k] & 0x7F
+        both = (ost == 1) & (gst == 1)
+        gp, op = b.x[k][both] @ c, gold[f"proj{k}"][both]
+        tol = np.sum(np.abs(c)) * 1e-8 * np.maximum(1.0, gold[f"xnorm{k}"][both])
+        d, _ = cKDTree(np.stack([op.real, op.imag], 1)).query(np.stack([gp.real, gp.imag], 1))
+        checks.append(dict(scene=seeds[k], status_diffs=int(np.sum(gst != ost)),
+                           gpu_finite=int((gst == 1).sum()), oracle_finite=int((ost == 1).sum()),
+                           finite_matched=int(np.sum(d <= tol))))
+    out["trifocal_f"] = dict(
+        instances=I, paths=r["paths"], device_ms=r["device_ms"], wall_ms=wall * 1e3,
+        systems_per_s=I / (r["device_ms"] * 1e-3), paths_per_s=r["paths"] / (r["device_ms"] * 1e-3),
+        track_ms=r["track_ms"], retrack_ms=r["escalate_ms"], finite=r["finite"],
+        escalated=r["escalated"], golden_checks=checks,
+        form="one hc_track_batch, mixed precision, one start per orbit of the quaternion signs")
+    return out
 
 
 # ---------------------------------------------------------------- batched solve (Fig. 3)
@@ -690,9 +768,9 @@ def serving_problems(hc, precision, trifocal=True):
                   lambda s: inputs.triangulation_scene(s)[0]))
     if trifocal:
         z = np.load(os.path.join(START_DIR, "trifocal_f.npz"))
-        probs.append(("trifocal_f", hc.Problem(inputs.trifocal_family().system,
-                                                kind=hc.HC_PARAMETER, p0=z["p0"],
-                                                start=z["start"],
+        fam = inputs.trifocal_family()
+        probs.append(("trifocal_f", hc.Problem(fam.system, kind=hc.HC_PARAMETER, p0=z["p0"],
+                                                start=z["start"], symmetries=fam.sign_masks,
                                                 settings=dict(precision=precision)),
                       lambda s: inputs.trifocal_scene(s)[0]))
     return probs
@@ -779,6 +857,9 @@ def main():
     ap.add_argument("--no-fp64-leg", action="store_true")
     ap.add_argument("--no-serving-leg", action="store_true")
     ap.add_argument("--no-solve-leg", action="store_true")
+    ap.add_argument("--no-param-legs", action="store_true")
+    ap.add_argument("--tri-instances", type=int, default=10_000)
+    ap.add_argument("--trifocal-instances", type=int, default=64)
     ap.add_argument("--serve-rate", type=float, default=400.0,
                     help="offered requests/s of the serving leg")
     ap.add_argument("--serve-duration", type=float, default=2.0)

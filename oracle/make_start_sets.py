@@ -4,7 +4,8 @@ Runs the oracle's monodromy solver (oracle/monodromy.py, FP64 C++ tracking)
 once per problem family and stores the result as an input file:
   paper_2112_03444_gb300/startsets/<family>.npz
 with arrays start [S, n] complex128, p0 [P] complex128, and the loop log.
-Usage:  python -m oracle.make_start_sets [triangulation4] [trifocal_f]
+Usage:  python -m oracle.make_start_sets [triangulation4] [trifocal_f] [triangulation2]
+                                         [p3p] [pose5_depth]
 """
 import json
 import os
@@ -22,7 +23,10 @@ from paper_2112_03444_gb300 import inputs  # noqa: E402
 
 OUT = os.path.join(ROOT, "paper_2112_03444_gb300", "startsets")
 FAMILIES = {"triangulation4": lambda: inputs.triangulation_family(4),
-            "trifocal_f": inputs.trifocal_family}
+            "trifocal_f": inputs.trifocal_family,
+            "triangulation2": lambda: inputs.triangulation_family(2),
+            "p3p": inputs.p3p_family,
+            "pose5_depth": inputs.pose5_depth_family}
 
 
 def make(name, seed=0, stall_loops=10, threads=0):

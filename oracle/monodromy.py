@@ -47,6 +47,9 @@ def seed_pair(family, rng):
     p = _complex_normal(rng, P)
     lin = list(family.linear_params)
     p[lin] = 0.0
+    if family.complete_seed is not None:
+        # equations in no linear parameter: the family fixes x0 to satisfy them
+        x0 = family.complete_seed(x0, p)
     r = residual(sys_, x0, p)
     A = np.zeros((n, len(lin)), np.complex128)
     for c, l in enumerate(lin):

@@ -218,11 +218,20 @@ class ParamFamily:
     linear_params: list       # indices of params in which F is affine (for seeding)
     unit_groups: list         # unknown-index groups constrained by q.q = 1
     name: str
+    # optional: (x0, p) -> x0 with the equations that involve no linear
+    # parameter satisfied (monodromy seeding); None when there are none
+    complete_seed: object = None
+    # sign symmetries (bit masks of unknowns whose negation maps solutions to
+    # solutions); None: one per unit-quaternion group
+    sym_masks: list = None
 
     @property
     def sign_masks(self) -> list:
-        """Bit masks of the unit-quaternion groups: the rotation R(q) is
-        quadratic in q, so negating a group maps solutions to solutions."""
+        """Bit masks of the sign symmetries: by default the unit-quaternion
+        groups (R(q) is quadratic in q, so negating a group maps solutions to
+        solutions)."""
+        if self.sym_masks is not None:
+            return list(self.sym_masks)
         return [sum(1 << j for j in grp) for grp in self.unit_groups]
 
 
@@ -340,6 +349,95 @@ def trifocal_family() -> ParamFamily:
                        params=params, linear_params=sorted(linear),
                        unit_groups=[list(range(Q12, Q12 + 4)), list(range(Q13, Q13 + 4))],
                        name="trifocal_f")
+
+
+def p3p_family() -> ParamFamily:
+    """P3P in the depths (paper Sec. 4, Eq. P3PafterElim): with image points
+    gamma_k = (xi_k, eta_k, 1) and depths rho_k, the 3D points are
+    rho_k gamma_k in the camera frame, and the camera-independent distances
+    of the world points fix
+      |rho2 g2 - rho1 g1|^2 = a,  |rho3 g3 - rho1 g1|^2 = b,
+      (rho2 g2 - rho1 g1) . (rho3 g3 - rho1 g1) = c,
+    a = |G2 - G1|^2, b = |G3 - G1|^2, c = (G2 - G1) . (G3 - G1).
+    Unknowns rho1..3; parameters (xi_k, eta_k) k = 1..3, then a, b, c.  Every
+    term has even degree in the depths (rho -> -rho maps solutions to
+    solutions: sign mask 0b111); Bezout and the generic count are 8."""
+    n, P = 3, 9
+    rho = [_Poly.var(n, k) for k in range(3)]
+    g = [[_Poly.param(n, 2 * k), _Poly.param(n, 2 * k + 1), _Poly.const(n, 1.0)] for k in range(3)]
+
+    def diff(i, j):   # rho_i g_i - rho_j g_j
+        return [rho[i] * g[i][a] - rho[j] * g[j][a] for a in range(3)]
+
+    def dot(u, v):
+        out = _Poly(n)
+        for a in range(3):
+            out = out + u[a] * v[a]
+        return out
+    d21, d31 = diff(1, 0), diff(2, 0)
+    polys = [dot(d21, d21) - _Poly.param(n, 6), dot(d31, d31) - _Poly.param(n, 7),
+             dot(d21, d31) - _Poly.param(n, 8)]
+    params = [f"{s}{k + 1}" for k in range(3) for s in ("xi", "eta")] + ["a", "b", "c"]
+    return ParamFamily(system=_system_from(n, P, polys, "p3p"),
+                       unknowns=["rho1", "rho2", "rho3"], params=params,
+                       linear_params=[6, 7, 8], unit_groups=[], name="p3p", sym_masks=[0b111])
+
+
+def pose5_depth_family() -> ParamFamily:
+    """Relative pose with depth reconstruction from five points (paper Sec. 4,
+    Eq. FullRigidMotion): rhobar_i gbar_i = R(q) rho_i g_i + T, i = 1..5, with
+    g_i = (xi_i, eta_i, 1) in view 1, gbar_i = (xibar_i, etabar_i, 1) in view
+    2, the rotation by an unnormalised quaternion q with q . q = 1, and the
+    translation on the chart T = (a, b, 1) (the unit direction of the paper
+    fixed by its third coordinate instead, which keeps 16 unknowns for 16
+    equations).  Unknowns: rho_1..5, rhobar_1..5, q_0..3, a, b.  Parameters:
+    (xi_i, eta_i, xibar_i, etabar_i), i = 1..5.  R(q) is quadratic in q:
+    negating q maps solutions to solutions (sign mask of q)."""
+    n, P = 16, 20
+    RHO, RBAR, Q, A = 0, 5, 10, 14
+    X = lambda j: _Poly.var(n, j)
+    R = _quat_rot([X(Q + a) for a in range(4)])
+    T = [X(A), X(A + 1), _Poly.const(n, 1.0)]
+    polys = []
+    for i in range(5):
+        g = [_Poly.param(n, 4 * i), _Poly.param(n, 4 * i + 1), _Poly.const(n, 1.0)]
+        gb = [_Poly.param(n, 4 * i + 2), _Poly.param(n, 4 * i + 3), _Poly.const(n, 1.0)]
+        for r in range(3):
+            rg = _Poly(n)
+            for c in range(3):
+                rg = rg + R[r][c] * g[c]
+            polys.append(X(RBAR + i) * gb[r] - X(RHO + i) * rg - T[r])
+    polys.append(sum((X(Q + a) * X(Q + a) for a in range(4)), _Poly(n)) - 1.0)
+    unknowns = [f"rho{i + 1}" for i in range(5)] + [f"rhobar{i + 1}" for i in range(5)] + \
+               [f"q{a}" for a in range(4)] + ["a", "b"]
+    params = [f"{s}{i + 1}" for i in range(5) for s in ("xi", "eta", "xibar", "etabar")]
+
+    def complete(x0, p):
+        # the third row of each point equation holds no parameter in which F
+        # is affine: set rhobar_i = rho_i (R(q) g_i)_3 + 1
+        q = x0[Q:Q + 4]
+        Rq = _rot_numeric(q)
+        for i in range(5):
+            gi = np.array([p[4 * i], p[4 * i + 1], 1.0])
+            x0[RBAR + i] = x0[RHO + i] * (Rq[2] @ gi) + 1.0
+        return x0
+    return ParamFamily(system=_system_from(n, P, polys, "pose5_depth"), unknowns=unknowns,
+                       params=params,
+                       linear_params=sorted([4 * i + 2 for i in range(5)] +
+                                            [4 * i + 3 for i in range(5)]),
+                       unit_groups=[list(range(Q, Q + 4))], name="pose5_depth",
+                       complete_seed=complete)
+
+
+def _rot_numeric(q):
+    """R(q) of an unnormalised complex quaternion (the same formula as _quat_rot)."""
+    q0, q1, q2, q3 = q
+    return np.array([[q0 * q0 + q1 * q1 - q2 * q2 - q3 * q3, 2 * (q1 * q2 - q0 * q3),
+                      2 * (q1 * q3 + q0 * q2)],
+                     [2 * (q1 * q2 + q0 * q3), q0 * q0 - q1 * q1 + q2 * q2 - q3 * q3,
+                      2 * (q2 * q3 - q0 * q1)],
+                     [2 * (q1 * q3 - q0 * q2), 2 * (q2 * q3 + q0 * q1),
+                      q0 * q0 - q1 * q1 - q2 * q2 + q3 * q3]], dtype=np.complex128)
 
 
 # ---------------------------------------------------------------- scenes
@@ -504,6 +602,84 @@ def trifocal_scene(seed: int, noise_px: float = 0.5, width: int = 1920, height: 
         [Tv[1][0] / sz, Tv[1][1] / sz] + list(Tv[2] / sz) + [Xc[2] / sz for (Xc, _) in pts]
     return pack(noisy), dict(p_clean=pack(clean), x_true=np.array(x, dtype=np.complex128), f=f,
                              R=Rv, T=Tv)
+
+
+def p3p_scene(seed: int, noise_px: float = 0.5, f: float = 1000.0, width: int = 1920,
+              height: int = 1080):
+    """Synthetic P3P instance: three points with pixels uniform in the image
+    and depths U[2, 10] in the camera frame; image points with N(0,
+    noise_px) pixel noise, normalised by K^-1; a, b, c from the exact 3D
+    points (a P3P solver knows the world points).  Returns (p1, truth) with
+    truth['rho'] the true depths (an exact root of the noise-free p_clean)."""
+    rng = np.random.default_rng([seed, 0x93])
+    Kinv = np.linalg.inv(np.array([[f, 0, width / 2], [0, f, height / 2], [0, 0, 1.0]]))
+    pix = [(rng.uniform(0, width), rng.uniform(0, height)) for _ in range(3)]
+    depth = rng.uniform(2.0, 10.0, 3)
+    G = [d * (Kinv @ np.array([u, v, 1.0])) for d, (u, v) in zip(depth, pix)]
+    abc = [float((G[1] - G[0]) @ (G[1] - G[0])), float((G[2] - G[0]) @ (G[2] - G[0])),
+           float((G[1] - G[0]) @ (G[2] - G[0]))]
+
+    def pack(pixels):
+        out = []
+        for (u, v) in pixels:
+            g = Kinv @ np.array([u, v, 1.0])
+            out += [g[0], g[1]]
+        return np.array(out + abc, dtype=np.complex128)
+    noisy = [(u + rng.normal(0, noise_px), v + rng.normal(0, noise_px)) for (u, v) in pix]
+    return pack(noisy), dict(p_clean=pack(pix), rho=depth.astype(np.complex128))
+
+
+def pose5_scene(seed: int, noise_px: float = 0.5, f: float = 1000.0, width: int = 1920,
+                height: int = 1080, max_angle_deg: float = 30.0):
+    """Synthetic two-view scene for pose5_depth_family: camera 1 at the
+    identity, camera 2 rotated about a random axis by U[0, max_angle_deg]
+    degrees and translated by a random direction x U[0.5, 1.5] (with a
+    nonzero third component); five points with pixels uniform in image 1 and
+    depth U[2, 10], visible in front of camera 2; N(0, noise_px) pixel noise.
+    Returns (p1, truth); truth['x_true'] solves the noise-free p_clean (depths
+    and translation scaled by 1 / T_z onto the chart T = (a, b, 1))."""
+    rng = np.random.default_rng([seed, 0x5D])
+    K = np.array([[f, 0, width / 2], [0, f, height / 2], [0, 0, 1.0]])
+    Kinv = np.linalg.inv(K)
+    for _attempt in range(1000):
+        ax = rng.standard_normal(3)
+        R = _rot_axis_angle(ax, np.deg2rad(rng.uniform(0, max_angle_deg)))
+        T = rng.standard_normal(3)
+        T = T / np.linalg.norm(T) * rng.uniform(0.5, 1.5)
+        if abs(T[2]) < 0.2:
+            continue
+        pts, ok = [], True
+        for _ in range(5):
+            u, v = rng.uniform(0, width), rng.uniform(0, height)
+            d = rng.uniform(2.0, 10.0)
+            X1 = d * (Kinv @ np.array([u, v, 1.0]))
+            X2 = R @ X1 + T
+            if X2[2] <= 0.1:
+                ok = False
+                break
+            h = K @ (X2 / X2[2])
+            if not (0 <= h[0] < width and 0 <= h[1] < height):
+                ok = False
+                break
+            pts.append(((u, v), (h[0], h[1]), d, X2[2]))
+        if ok:
+            break
+
+    def pack(points):
+        out = []
+        for (u, v), (ub, vb) in points:
+            g = Kinv @ np.array([u, v, 1.0])
+            gb = Kinv @ np.array([ub, vb, 1.0])
+            out += [g[0], g[1], gb[0], gb[1]]
+        return np.array(out, dtype=np.complex128)
+    clean = [(a, b) for (a, b, _, _) in pts]
+    noisy = [((a[0] + rng.normal(0, noise_px), a[1] + rng.normal(0, noise_px)),
+              (b[0] + rng.normal(0, noise_px), b[1] + rng.normal(0, noise_px))) for (a, b) in clean]
+    sz = T[2]
+    x = [d / sz for (_, _, d, _) in pts] + [db / sz for (_, _, _, db) in pts] + \
+        list(_quat_of(R)) + [T[0] / sz, T[1] / sz]
+    return pack(noisy), dict(p_clean=pack(clean), x_true=np.array(x, dtype=np.complex128), R=R,
+                             T=T)
 
 
 def dense_parameter_family(n: int, d: int, seed: int):

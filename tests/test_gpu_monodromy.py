@@ -53,3 +53,19 @@ def test_gpu_monodromy_rejects_bad_descriptors(hc):
         hc.monodromy_solve(fam.system, z["start"][0], z["p0"], max_solutions=10,
                            stall_loops=3)
     assert e.value.code == hc.HC_ERR_INVALID
+
+
+@pytest.mark.parametrize("name,count", [("p3p", 8), ("pose5_depth", 40)])
+def test_gpu_monodromy_with_sign_symmetries(hc, name, count):
+    """P3P (rho -> -rho) and relative pose with depth (q -> -q): the GPU
+    monodromy, adding sign images of every new solution and tracking one
+    start per orbit, reproduces the oracle's committed start set."""
+    from paper_2112_03444_gb300 import inputs
+    fam = {"p3p": inputs.p3p_family, "pose5_depth": inputs.pose5_depth_family}[name]()
+    z = np.load(os.path.join(STARTS, f"{name}.npz"))
+    sols, info = hc.monodromy_solve(fam.system, z["start"][1], z["p0"], seed=5,
+                                    stall_loops=8, loops_per_round=4,
+                                    symmetries=fam.sign_masks)
+    assert len(sols) == count, (len(sols), info)
+    ok, msg = same_set(sols, z["start"], 1e-8)
+    assert ok, msg

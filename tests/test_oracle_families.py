@@ -147,3 +147,93 @@ def test_trifocal_tracking_recovers_the_true_pose():
             v[5:9] *= s13
             best = min(best, float(np.min(np.max(np.abs(fin - v), axis=1))))
     assert best < 1e-8, best
+
+
+# ---------------------------------------------------------------- P3P, 5-point pose + depth
+def _closed_under(S, mask, tol=1e-10):
+    sg = np.array([-1.0 if mask >> j & 1 else 1.0 for j in range(S.shape[1])])
+    for x in S:
+        d = np.max(np.abs(S - sg * x), axis=1) / max(1.0, float(np.max(np.abs(x))))
+        if np.min(d) > tol:
+            return False
+    return True
+
+
+def test_p3p_formulation_and_start_set():
+    """P3P in the depths (Sec. 4, Eq. P3PafterElim): the true depths of a
+    noise-free scene satisfy the three quadratics; the oracle's monodromy
+    start set has the paper's 8 solutions (Table 2), pairwise distinct, each
+    a root at p0, closed under rho -> -rho."""
+    fam = inputs.p3p_family()
+    assert fam.system.n == 3 and np.all(fam.system.degrees() == 2)
+    _, truth = inputs.p3p_scene(4, noise_px=0.0)
+    assert np.max(np.abs(monodromy.residual(fam.system, truth["rho"], truth["p_clean"]))) < 1e-10
+    z = np.load(os.path.join(STARTS, "p3p.npz"))
+    S = z["start"]
+    assert len(S) == 8 and distinct(S, 1e-6) == 8
+    for x in S:
+        assert np.max(np.abs(monodromy.residual(fam.system, x, z["p0"]))) < 1e-10
+    assert _closed_under(S, 0b111)
+
+
+def test_p3p_tracking_recovers_true_depths():
+    """From the 8 start solutions to a noise-free scene the oracle's parameter
+    homotopy ends at the true depths (and their negatives)."""
+    fam = inputs.p3p_family()
+    z = np.load(os.path.join(STARTS, "p3p.npz"))
+    for seed in (5, 6):
+        _, truth = inputs.p3p_scene(seed, noise_px=0.0)
+        r = OracleProblem(fam.system, kind=KIND_PARAMETER, p0=z["p0"],
+                          p1=truth["p_clean"]).track(start=z["start"])
+        fin = r["x"][(r["status"] & 0x7F) == oracle.FINITE]
+        for sg in (1, -1):
+            d = np.max(np.abs(fin - sg * truth["rho"]), axis=1) / np.max(np.abs(truth["rho"]))
+            assert np.min(d) < 1e-9, (seed, sg)
+
+
+def test_pose5_depth_formulation_and_start_set():
+    """Relative pose + depth from five points (Sec. 4, Eq. FullRigidMotion):
+    16 equations in 16 unknowns; the true pose of a noise-free scene (depths
+    and translation on the T = (a, b, 1) chart, unit quaternion) is a root,
+    with either quaternion sign; the oracle's monodromy start set is closed
+    under q -> -q.  (Our chart formulation has 40 solutions: 10 essential
+    matrices, the twisted pair, the quaternion sign; the paper's Table 2
+    count of 160 is for its own formulation, whose equations it does not
+    print.)"""
+    fam = inputs.pose5_depth_family()
+    assert fam.system.n == 16 and len(fam.unknowns) == 16 and fam.system.n_params == 20
+    for seed in (1, 2):
+        _, truth = inputs.pose5_scene(seed, noise_px=0.0)
+        x = truth["x_true"]
+        assert np.max(np.abs(monodromy.residual(fam.system, x, truth["p_clean"]))) < 1e-10
+        x2 = x.copy()
+        x2[10:14] *= -1
+        assert np.max(np.abs(monodromy.residual(fam.system, x2, truth["p_clean"]))) < 1e-10
+    z = np.load(os.path.join(STARTS, "pose5_depth.npz"))
+    S = z["start"]
+    assert len(S) == 40 and distinct(S, 1e-6) == 40
+    assert _closed_under(S, 0b1111 << 10)
+
+
+def test_pose5_depth_tracking_recovers_true_pose():
+    fam = inputs.pose5_depth_family()
+    z = np.load(os.path.join(STARTS, "pose5_depth.npz"))
+    _, truth = inputs.pose5_scene(3, noise_px=0.0)
+    r = OracleProblem(fam.system, kind=KIND_PARAMETER, p0=z["p0"],
+                      p1=truth["p_clean"]).track(start=z["start"])
+    fin = r["x"][(r["status"] & 0x7F) == oracle.FINITE]
+    xt = truth["x_true"]
+    d = np.max(np.abs(fin - xt), axis=1) / np.max(np.abs(xt))
+    assert np.min(d) < 1e-8
+
+
+def test_two_view_start_set():
+    """Two-view triangulation (Sec. 4, Eq. constraints, 5 x 5): 8 distinct
+    start solutions at p0, each a root; the zero correction is an exact root
+    of noise-free consistent data (tested above for the pinned endpoint)."""
+    fam = inputs.triangulation_family(2)
+    z = np.load(os.path.join(STARTS, "triangulation2.npz"))
+    S = z["start"]
+    assert S.shape == (8, 5) and distinct(S, 1e-6) == 8
+    for x in S:
+        assert np.max(np.abs(monodromy.residual(fam.system, x, z["p0"]))) < 1e-10
