@@ -52,7 +52,12 @@ typedef enum hc_status {
 /* Homotopy kinds (hc_problem_desc.kind). */
 enum {
   HC_TOTAL_DEGREE = 0,  /* H = (1-t) gamma G + t F, G_i = x_i^{d_i} - 1, d_i = deg F_i */
-  HC_PARAMETER = 1      /* H = F(x; (1-t) p0 + t p1), start solutions given at p0      */
+  HC_PARAMETER = 1,     /* H = F(x; (1-t) p0 + t p1), start solutions given at p0      */
+  HC_COEFFICIENT = 2    /* H = sum_k ((1-t) c_k(p0) + t c_k(p1)) x^a_k, c_k(p) the term
+                           coefficient at parameters p: the coefficients themselves
+                           interpolated, as Sec. 6 states; same inputs as
+                           HC_PARAMETER (the two agree when every coefficient is
+                           linear in the parameters)                              */
 };
 
 /* Tracking precision (hc_settings.precision). */
@@ -130,7 +135,9 @@ typedef struct hc_settings {
                              FP32 Jacobian and contract only linearly (about
                              cond * 6e-8 per iteration), so one exact Newton step
                              is worth about two of them                         */
-  int32_t reserved;       /* 0 */
+  int32_t block_threads;  /* threads per block of the main tracking launch: 0 (the
+                             default, 128), 32, 64 or 128; paths per block =
+                             threads / lanes (the autotuner's block axis)       */
 } hc_settings;
 
 /*
@@ -347,21 +354,38 @@ hc_status hc_plan_run(hc_plan* plan, const hc_batch_desc* b, hc_batch** out);
  * Autotuner (no counterpart in the paper, which fixes one warp per path in
  * Sec. 6).  Runs the caller's representative batch (*sample, as for
  * hc_track_batch; its outputs are overwritten) under each candidate
- * configuration -- all-FP64; mixed precision with the default lane width or
- * one path per warp; FP32 first-correction bound 0.01 or 0.1 -- twice each,
- * and keeps in the problem's settings the candidate with the shortest
- * device time among those that recover at least as many finite roots as the
- * all-FP64 run.  *report (may be NULL) lists what was tried.
+ * configuration -- all-FP64; mixed precision with lanes per path (the default
+ * width or one path per warp), paths per block (block_threads 128 or 64) and
+ * the FP32 first-correction bound (0.01 or 0.1) -- twice each, and keeps in
+ * the problem's settings the candidate with the shortest device time among
+ * those that recover at least as many finite roots as the all-FP64 run.
+ * *report (may be NULL) lists what was tried.
  */
 typedef struct hc_tune_report {
   int32_t n_candidates;
   int32_t best;                /* index into the arrays below                    */
-  double ms[8];                /* device time of each candidate's second run     */
-  int64_t finite[8];           /* finite roots found by each candidate           */
-  hc_settings tried[8];
+  int32_t cached;              /* hc_autotune_cached: 1 if the cache answered     */
+  int32_t reserved;
+  double ms[16];               /* device time of each candidate's second run     */
+  int64_t finite[16];          /* finite roots found by each candidate           */
+  hc_settings tried[16];
 } hc_tune_report;
 
 hc_status hc_autotune(hc_problem* p, const hc_batch_desc* sample, hc_tune_report* report);
+
+/*
+ * The autotuner with a cache file: cache_path is a JSON object mapping a key
+ * of the problem's shape and precision -- kind, n, total degree, term count,
+ * parameter count, symmetries, precision -- to the chosen lanes,
+ * block_threads, max_first_corr_fp32 and precision.  A key already in the
+ * file is applied to the problem's settings without tracking
+ * (report->cached = 1, n_candidates = 0); otherwise hc_autotune runs and its
+ * choice is added to the file (created if absent; other keys are kept).
+ * Errors: those of hc_autotune, HC_ERR_INVALID for an unreadable or
+ * unwritable cache file.
+ */
+hc_status hc_autotune_cached(hc_problem* p, const hc_batch_desc* sample, const char* cache_path,
+                             hc_tune_report* report);
 
 /*
  * Continuous-batching server (serving form of the tracker; no counterpart in

@@ -25,7 +25,7 @@ _lib = None
 FINITE, DIVERGED, FAIL_STEP, FAIL_MAXSTEPS, FAIL_NAN, SINGULAR, FAIL_REFINE = 1, 2, 3, 4, 5, 6, 7
 REAL_BIT = 0x80
 
-KIND_TOTAL_DEGREE, KIND_PARAMETER = 0, 1
+KIND_TOTAL_DEGREE, KIND_PARAMETER, KIND_COEFFICIENT = 0, 1, 2
 
 # Order of the settings vector passed to the C++ side.
 SETTINGS_ORDER = ("dt_min", "dt_max", "dt_init", "newton_tol", "max_newton", "max_steps",
@@ -91,6 +91,8 @@ class OracleProblem:
 
     kind = KIND_TOTAL_DEGREE: H = (1-t) gamma G + t F, G_i = x_i^{d_i} - 1.
     kind = KIND_PARAMETER:    H = F(x; (1-t) p0 + t p1).
+    kind = KIND_COEFFICIENT:  H = sum_k ((1-t) c_k(p0) + t c_k(p1)) x^alpha_k, the
+                              term coefficients c_k(p) interpolated (Sec. 6).
     """
 
     def __init__(self, system, kind=KIND_TOTAL_DEGREE, gamma=1.0 + 0j, p0=None, p1=None,

@@ -12,7 +12,8 @@
 //     the parameter homotopy H(x,t) = F(x; p(t)), p(t) = (1-t) p0 + t p1
 //     (Sec. 6 interpolates the system's coefficients between start and target;
 //     this oracle interpolates the parameters they depend on, which is the same
-//     thing when coefficients are linear in the parameters).
+//     thing when coefficients are linear in the parameters; kind 2 interpolates
+//     the coefficients themselves, c_k(t) = (1-t) c_k(p0) + t c_k(p1)).
 //   * Sec. 3, Eqs. 2-4: dx/dt = -(dH/dx)^-1 dH/dt; the predictor is the
 //     4th-order Runge-Kutta the paper names (classical tableau).
 //   * Sec. 3, Eqs. 5-6: Newton correction at t + dt.
@@ -47,7 +48,7 @@ namespace {
 
 using cd = std::complex<double>;
 
-enum : int { KIND_TOTAL_DEGREE = 0, KIND_PARAMETER = 1 };
+enum : int { KIND_TOTAL_DEGREE = 0, KIND_PARAMETER = 1, KIND_COEFFICIENT = 2 };
 enum : int {
   ST_FINITE = 1, ST_DIVERGED = 2, ST_FAIL_STEP = 3, ST_FAIL_MAXSTEPS = 4,
   ST_FAIL_NAN = 5, ST_SINGULAR = 6, ST_FAIL_REFINE = 7, ST_REAL_BIT = 0x80
@@ -112,7 +113,7 @@ void evaluate(const Problem& pr, const cd* x, double t, cd* H, cd* Hx, cd* Ht) {
   for (int i = 0; i < n; ++i) { H[i] = 0; Ht[i] = 0; }
   for (int i = 0; i < n * n; ++i) Hx[i] = 0;
 
-  std::vector<cd> p(pr.P), dp(pr.P);
+  std::vector<cd> p(pr.P), dp(pr.P), zero(pr.P, 0.0);
   for (int l = 0; l < pr.P; ++l) {
     if (pr.kind == KIND_PARAMETER) {
       p[l] = (1.0 - t) * pr.p0[l] + t * pr.p1[l];
@@ -129,7 +130,17 @@ void evaluate(const Problem& pr, const cd* x, double t, cd* H, cd* Hx, cd* Ht) {
     const int i = pr.eq[k];
     const int* a = &pr.exps[(size_t)k * n];
     cd c, dc;
-    term_coefficient(pr, k, p.data(), dp.data(), &c, &dc);
+    if (pr.kind == KIND_COEFFICIENT) {
+      // Sec. 6: the coefficients themselves are interpolated between the
+      // start system (parameters p0) and the target system (p1)
+      cd c0, c1, unused;
+      term_coefficient(pr, k, pr.p0.data(), zero.data(), &c0, &unused);
+      term_coefficient(pr, k, pr.p1.data(), zero.data(), &c1, &unused);
+      c = (1.0 - t) * c0 + t * c1;
+      dc = c1 - c0;
+    } else {
+      term_coefficient(pr, k, p.data(), dp.data(), &c, &dc);
+    }
     cd mono(1.0, 0.0);
     for (int j = 0; j < n; ++j) mono *= ipow(x[j], a[j]);
     F[i] += c * mono;
@@ -142,7 +153,7 @@ void evaluate(const Problem& pr, const cd* x, double t, cd* H, cd* Hx, cd* Ht) {
     }
   }
 
-  if (pr.kind == KIND_PARAMETER) {
+  if (pr.kind == KIND_PARAMETER || pr.kind == KIND_COEFFICIENT) {
     for (int i = 0; i < n; ++i) { H[i] = F[i]; Ht[i] = Ft[i]; }
     for (int i = 0; i < n * n; ++i) Hx[i] = Fx[i];
     return;

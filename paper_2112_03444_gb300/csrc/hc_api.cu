@@ -227,6 +227,34 @@ __global__ void summarize_kernel(int64_t items, const uint8_t* __restrict__ st,
   }
 }
 
+// Coefficient interpolation (HC_COEFFICIENT): per instance and (slot, row)
+// of the term tables, dc = c(p1) - c(p0), c(p) the slot's coefficient times
+// its parameter factors at p (cpar, -1: none), in FP64, FP32 and
+// double-float.  One thread per entry.
+__global__ void stage_coef_kernel(int64_t n_inst, int64_t slots, int mp,
+                                  const int32_t* __restrict__ cpar,
+                                  const double2* __restrict__ s64, const double2* __restrict__ c0,
+                                  const double2* __restrict__ p1, int P, double2* dc, float2* dcf,
+                                  hc::cdf* dcdf) {
+  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < n_inst * slots;
+       w += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t inst = w / slots, k = w - inst * slots;
+    double re = s64[k].x, im = s64[k].y;
+    for (int f = 0; f < mp; ++f) {
+      const int l = cpar[k * mp + f];
+      if (l < 0) continue;
+      const double2 v = p1[inst * P + l];
+      const double nr = re * v.x - im * v.y, ni = re * v.y + im * v.x;
+      re = nr;
+      im = ni;
+    }
+    const double2 d = make_double2(re - c0[k].x, im - c0[k].y);
+    dc[w] = d;
+    dcf[w] = make_float2((float)d.x, (float)d.y);
+    dcdf[w] = hc::to_cdf(cx<double>{d.x, d.y});
+  }
+}
+
 // Outputs of a batch tracked on orbit representatives (sign symmetries):
 // start j of instance i takes its representative's results, the unknowns of
 // group[sign[j]] negated.  One thread per output item.
@@ -314,6 +342,13 @@ struct hc_problem {
   hc::TermRec* d_rec = nullptr;
   double2* d_s64 = nullptr;
   hc::cdf* d_sdf = nullptr;  // the coefficients as double-floats
+  // coefficient interpolation: per (slot, row) the term's parameter factors
+  // [TT][L][maxpf] (-1: none), and c(p0) in FP64 / FP32 / double-float
+  bool coef_mode = false;
+  int32_t* d_cpar = nullptr;
+  double2* d_c0 = nullptr;
+  float2* d_c0f = nullptr;
+  hc::cdf* d_c0df = nullptr;
   // sign symmetries (parameter homotopies): group element masks, one tracked
   // start per orbit (reps), and per start its representative's position in
   // reps and the group element mapping the representative onto it
@@ -519,7 +554,8 @@ hc_status validate_settings(const hc_settings& s) {
       !(s.dt_min_fp32 >= s.dt_min) || !(s.max_first_corr_fp32 > 0) || s.max_steps_fp32 < 1 ||
       (s.precision != HC_PREC_FP64 && s.precision != HC_PREC_MIXED) ||
       (s.lanes != 0 && s.lanes != 32) || s.max_newton_ir < 1 || s.max_newton_ir > 32 ||
-      s.reserved != 0) {
+      (s.block_threads != 0 && s.block_threads != 32 && s.block_threads != 64 &&
+       s.block_threads != 128)) {
     set_err("invalid settings");
     return HC_ERR_INVALID;
   }
@@ -708,14 +744,18 @@ const char* build_orbits(hc_problem* p, int n_sym, const uint32_t* masks,
 // derivative feeds (x_j -> j, a parameter -> n, i.e. dH/dt through dp).  Rows
 // are padded to the same number of term slots, and every slot to the largest
 // factor count of its terms over the rows (padding factor: the 1).
-bool encode_terms(hc_problem* p, std::vector<hc::TermRec>& rec, std::vector<double2>& s64) {
+// With coefficient interpolation (HC_COEFFICIENT) the parameter factors are
+// left out of the records and listed per (slot, row) in cpar instead.
+bool encode_terms(hc_problem* p, std::vector<hc::TermRec>& rec, std::vector<double2>& s64,
+                  std::vector<int32_t>& cpar) {
   const int n = p->n, P = p->P, L = hc::lanes_for(n);
   const int one = L, pbase = L + 1, dbase = L + 1 + P;
-  if (p->kind != HC_PARAMETER || n + 2 > hc::kMaxTermEntries || dbase + P > 255) return false;
-  // per row: its terms as (coefficient, factors, targets)
+  if (p->kind == HC_TOTAL_DEGREE || n + 2 > hc::kMaxTermEntries || dbase + P > 255) return false;
+  const bool cmode = p->kind == HC_COEFFICIENT;
+  // per row: its terms as (coefficient, factors, targets, parameter list)
   struct Term {
     double re, im;
-    std::vector<int> f, tg;
+    std::vector<int> f, tg, par;
   };
   std::vector<std::vector<Term>> rows(n);
   for (int k = 0; k < p->T; ++k) {
@@ -729,7 +769,9 @@ bool encode_terms(hc_problem* p, std::vector<hc::TermRec>& rec, std::vector<doub
       }
     for (int f = 0; f < p->maxpf; ++f) {
       const int l = p->par[(size_t)k * p->maxpf + f];
-      if (l >= 0) {
+      if (l >= 0 && cmode) {
+        t.par.push_back(l);
+      } else if (l >= 0) {
         t.f.push_back(pbase + l);
         t.tg.push_back(n);
       }
@@ -751,6 +793,8 @@ bool encode_terms(hc_problem* p, std::vector<hc::TermRec>& rec, std::vector<doub
   }
   rec.assign((size_t)TT * L, hc::TermRec{});
   s64.assign((size_t)TT * L, make_double2(0.0, 0.0));
+  const int mp = std::max(p->maxpf, 1);
+  cpar.assign(cmode ? (size_t)TT * L * mp : 0, -1);
   for (int k = 0; k < TT; ++k) {
     int d = 1;
     for (int i = 0; i < n; ++i)
@@ -770,10 +814,13 @@ bool encode_terms(hc_problem* p, std::vector<hc::TermRec>& rec, std::vector<doub
         r.tgt[f] = (uint8_t)t.tg[f];
       }
       s64[(size_t)k * L + i] = make_double2(t.re, t.im);
+      for (size_t f = 0; cmode && f < t.par.size(); ++f)
+        cpar[((size_t)k * L + i) * mp + f] = t.par[f];
     }
   }
   p->TT = TT;
   p->terms = true;
+  p->coef_mode = cmode;
   p->L = L;
   p->extra = 1 + 3 * P;
   p->paths = p->n_start;
@@ -799,6 +846,10 @@ void free_problem(hc_problem* p) {
   cudaFree(p->d_rec);
   cudaFree(p->d_s64);
   cudaFree(p->d_sdf);
+  cudaFree(p->d_cpar);
+  cudaFree(p->d_c0);
+  cudaFree(p->d_c0f);
+  cudaFree(p->d_c0df);
   cudaFree(p->d_group);
   cudaFree(p->d_reps);
   cudaFree(p->d_rep_pos);
@@ -863,12 +914,77 @@ KernelRef retrack_kernel(int deg, int n, bool mixed) {
 }  // namespace hc
 using hc::retrack_kernel;
 
+namespace {
+// The tuning cache: a JSON object {"<key>": {"precision": p, "lanes": l,
+// "block_threads": b, "max_first_corr_fp32": c}, ...}, one entry per line
+// as written by write_tune_cache.  The reader accepts what the writer
+// writes (and an absent or empty file); anything else is refused.
+bool read_tune_cache(const char* path, std::map<std::string, std::string>& out) {
+  FILE* f = std::fopen(path, "r");
+  if (!f) return true;  // no cache yet
+  std::string text;
+  char buf[4096];
+  size_t got;
+  while ((got = std::fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, got);
+  std::fclose(f);
+  size_t pos = text.find('{');
+  if (pos == std::string::npos) return text.find_first_not_of(" \t\r\n") == std::string::npos;
+  for (;;) {
+    const size_t k0 = text.find('"', pos + 1);
+    if (k0 == std::string::npos) break;
+    const size_t k1 = text.find('"', k0 + 1);
+    const size_t o0 = text.find('{', k1);
+    const size_t o1 = text.find('}', o0);
+    if (k1 == std::string::npos || o0 == std::string::npos || o1 == std::string::npos) return false;
+    out[text.substr(k0 + 1, k1 - k0 - 1)] = text.substr(o0, o1 - o0 + 1);
+    pos = o1;
+  }
+  return true;
+}
+
+bool write_tune_cache(const char* path, const std::map<std::string, std::string>& entries) {
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "w");
+  if (!f) return false;
+  std::fprintf(f, "{\n");
+  size_t i = 0;
+  for (const auto& e : entries)
+    std::fprintf(f, "  \"%s\": %s%s\n", e.first.c_str(), e.second.c_str(),
+                 ++i < entries.size() ? "," : "");
+  std::fprintf(f, "}\n");
+  const bool ok = std::fclose(f) == 0;
+  return ok && std::rename(tmp.c_str(), path) == 0;
+}
+
+bool parse_tune_entry(const std::string& obj, hc_settings& s) {
+  auto num = [&](const char* name, double& v) {
+    const size_t at = obj.find(std::string("\"") + name + "\"");
+    if (at == std::string::npos) return false;
+    const size_t colon = obj.find(':', at);
+    if (colon == std::string::npos) return false;
+    char* end = nullptr;
+    v = std::strtod(obj.c_str() + colon + 1, &end);
+    return end != obj.c_str() + colon + 1;
+  };
+  double prec, lanes, block, corr;
+  if (!num("precision", prec) || !num("lanes", lanes) || !num("block_threads", block) ||
+      !num("max_first_corr_fp32", corr))
+    return false;
+  s.precision = (int32_t)prec;
+  s.lanes = (int32_t)lanes;
+  s.block_threads = (int32_t)block;
+  s.max_first_corr_fp32 = corr;
+  return true;
+}
+}  // namespace
+
 namespace hc {
 // Device bytes one instance of a batch needs with P paths per instance
 // (inputs, encoded tables, outputs, scratch): the admission measure.
 int64_t instance_device_bytes(const hc_problem* p, int64_t P) {
   const int64_t n = p->n;
-  int64_t b = 16 * (int64_t)(p->kind == HC_PARAMETER ? p->P : p->T);  // inputs
+  int64_t b = 16 * (int64_t)(p->kind != HC_TOTAL_DEGREE ? p->P : p->T);  // inputs
+  if (p->coef_mode) b += 40 * (int64_t)p->TT * p->L;                      // dc tables
   if (!p->terms) b += 32 * p->Estride + 24 * p->Dstride;              // E, Edf, D64, D32
   b += P * (16 * n + 1 + 12 + 8);                                     // x, status, steps, be
   b += P * (8 + 8 + 8 + 8 * n + 8);                                   // lists, t_io, x32, ids
@@ -921,7 +1037,7 @@ hc_settings hc_default_settings(void) {
   s.escalate = 1;
   s.lanes = 0;
   s.max_newton_ir = 6;
-  s.reserved = 0;
+  s.block_threads = 0;
   return s;
 }
 
@@ -934,7 +1050,8 @@ hc_status hc_create_problem(const hc_problem_desc* d, hc_problem** out) {
   const int n = d->n, T = d->n_terms;
   if (n < 1 || n > 32 || T < 1 || !d->term_eq || !d->term_coef || !d->term_exp ||
       d->max_pfac < 0 || d->max_pfac > 8 || (d->max_pfac > 0 && !d->term_param) ||
-      (d->kind != HC_TOTAL_DEGREE && d->kind != HC_PARAMETER) || d->n_params < 0) {
+      (d->kind != HC_TOTAL_DEGREE && d->kind != HC_PARAMETER && d->kind != HC_COEFFICIENT) ||
+      d->n_params < 0) {
     set_err("invalid problem descriptor");
     return HC_ERR_INVALID;
   }
@@ -970,7 +1087,7 @@ hc_status hc_create_problem(const hc_problem_desc* d, hc_problem** out) {
       set_err("an equation has no terms");
       return HC_ERR_INVALID;
     }
-  if (d->n_sym != 0 && d->kind != HC_PARAMETER) {
+  if (d->n_sym != 0 && d->kind == HC_TOTAL_DEGREE) {
     set_err("sign symmetries need a parameter homotopy");
     return HC_ERR_INVALID;
   }
@@ -979,7 +1096,7 @@ hc_status hc_create_problem(const hc_problem_desc* d, hc_problem** out) {
     set_err("gamma must have unit modulus");
     return HC_ERR_INVALID;
   }
-  if (d->kind == HC_PARAMETER && (d->n_params < 1 || !d->p0 || d->n_start < 1 || !d->start)) {
+  if (d->kind != HC_TOTAL_DEGREE && (d->n_params < 1 || !d->p0 || d->n_start < 1 || !d->start)) {
     set_err("parameter homotopy needs p0 and start solutions");
     return HC_ERR_INVALID;
   }
@@ -999,7 +1116,7 @@ hc_status hc_create_problem(const hc_problem_desc* d, hc_problem** out) {
   if (p->maxpf) p->par.assign(d->term_param, d->term_param + (size_t)T * p->maxpf);
   cudaGetDevice(&p->device);
 
-  if (d->kind == HC_PARAMETER) {
+  if (d->kind != HC_TOTAL_DEGREE) {
     p->n_start = d->n_start;
     for (int64_t k = 0; k < (int64_t)d->n_params * 2; ++k)
       if (!std::isfinite(d->p0[k])) {
@@ -1021,7 +1138,8 @@ hc_status hc_create_problem(const hc_problem_desc* d, hc_problem** out) {
     }
     std::vector<hc::TermRec> rec;
     std::vector<double2> s64;
-    if (!encode_terms(p, rec, s64)) {
+    std::vector<int32_t> cpar;
+    if (!encode_terms(p, rec, s64, cpar)) {
       delete p;
       set_err("parameter homotopy: n <= 32, at most 8 factors per term, L + 1 + 2 n_params <= 255");
       return HC_ERR_UNSUPPORTED;
@@ -1035,12 +1153,39 @@ hc_status hc_create_problem(const hc_problem_desc* d, hc_problem** out) {
     // nearest float to the remainder
     std::vector<hc::cdf> sdf(s64.size());
     for (size_t k = 0; k < s64.size(); ++k) sdf[k] = hc::split_cdf_host(s64[k].x, s64[k].y);
+    // coefficient interpolation: c(p0) of every (slot, row), the term
+    // coefficient times its parameter factors at p0
+    std::vector<double2> c0;
+    std::vector<float2> c0f;
+    std::vector<hc::cdf> c0df;
+    if (p->coef_mode) {
+      const int mp = std::max(p->maxpf, 1);
+      c0.resize(s64.size());
+      c0f.resize(s64.size());
+      c0df.resize(s64.size());
+      for (size_t k = 0; k < s64.size(); ++k) {
+        double re = s64[k].x, im = s64[k].y;
+        for (int f = 0; f < mp; ++f) {
+          const int l = cpar[k * mp + f];
+          if (l < 0) continue;
+          const double pr = d->p0[2 * l], pi = d->p0[2 * l + 1];
+          const double nr = re * pr - im * pi, ni = re * pi + im * pr;
+          re = nr;
+          im = ni;
+        }
+        c0[k] = make_double2(re, im);
+        c0f[k] = make_float2((float)re, (float)im);
+        c0df[k] = hc::split_cdf_host(re, im);
+      }
+    }
     std::vector<double2> p0v(d->n_params), sv((size_t)d->n_start * n);
     for (int l = 0; l < d->n_params; ++l) p0v[l] = make_double2(d->p0[2 * l], d->p0[2 * l + 1]);
     for (size_t k = 0; k < sv.size(); ++k) sv[k] = make_double2(d->start[2 * k], d->start[2 * k + 1]);
     hc_status st;
     if ((st = upload(rec, &p->d_rec)) != HC_OK || (st = upload(s64, &p->d_s64)) != HC_OK ||
-        (st = upload(sdf, &p->d_sdf)) != HC_OK ||
+        (st = upload(sdf, &p->d_sdf)) != HC_OK || (st = upload(cpar, &p->d_cpar)) != HC_OK ||
+        (st = upload(c0, &p->d_c0)) != HC_OK || (st = upload(c0f, &p->d_c0f)) != HC_OK ||
+        (st = upload(c0df, &p->d_c0df)) != HC_OK ||
         (st = upload(p0v, &p->d_p0)) != HC_OK || (st = upload(sv, &p->d_start)) != HC_OK ||
         (st = upload(p->group, &p->d_group)) != HC_OK || (st = upload(reps, &p->d_reps)) != HC_OK ||
         (st = upload(rep_pos, &p->d_rep_pos)) != HC_OK || (st = upload(sign, &p->d_sign)) != HC_OK) {
@@ -1082,7 +1227,7 @@ hc_status hc_problem_query(const hc_problem* p, hc_problem_info* out) {
   }
   out->n = p->n;
   out->kind = p->kind;
-  out->inputs_per_instance = p->kind == HC_PARAMETER ? p->P : p->T;
+  out->inputs_per_instance = p->kind != HC_TOTAL_DEGREE ? p->P : p->T;
   out->lanes = p->terms ? hc::term_kernel(p->n, true, 0).lanes : p->L;
   out->paths = p->paths;
   out->device_bytes_per_instance = hc::instance_device_bytes(p, p->paths);
@@ -1118,6 +1263,10 @@ struct Bufs {
   uint8_t* cst = nullptr;
   int32_t* csteps = nullptr;
   double* cbe = nullptr;
+  // coefficient interpolation: per-instance coefficient changes
+  double2* dc = nullptr;
+  float2* dcf = nullptr;
+  hc::cdf* dcdf = nullptr;
 };
 
 // The batch tracks orbit representatives (sign symmetries, no start subset).
@@ -1136,6 +1285,15 @@ hc_status alloc_scratch(hc_problem* p, int64_t n_inst, Bufs& B, A&& alloc) {
   const int64_t items = n_inst * tracked_paths(p, B);
   void* q;
   hc_status rc;
+  if (p->coef_mode) {
+    const size_t e = (size_t)n_inst * p->TT * p->L;
+    if ((rc = alloc(sizeof(double2) * e, &q)) != HC_OK) return rc;
+    B.dc = (double2*)q;
+    if ((rc = alloc(sizeof(float2) * e, &q)) != HC_OK) return rc;
+    B.dcf = (float2*)q;
+    if ((rc = alloc(sizeof(hc::cdf) * e, &q)) != HC_OK) return rc;
+    B.dcdf = (hc::cdf*)q;
+  }
   if (sym_active(p, B)) {
     if ((rc = alloc(sizeof(double) * 2 * p->n * items, &q)) != HC_OK) return rc;
     B.cx = (double*)q;
@@ -1169,6 +1327,9 @@ hc_status alloc_scratch(hc_problem* p, int64_t n_inst, Bufs& B, A&& alloc) {
   }
   return HC_OK;
 }
+
+// Threads per block of the main tracking launch (settings.block_threads).
+int main_threads(const hc_settings& s) { return s.block_threads ? s.block_threads : hc::kBlock; }
 
 // Events of one enqueue: ek0..ek2 time the tracking launch and the
 // re-tracking tiers; fork and join order the re-tracking stream after the
@@ -1310,12 +1471,28 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
     ta.p0 = p->d_p0;
     ta.p1 = B.d_p1;
     ta.start = p->d_start;
+    if (p->coef_mode) {
+      const int64_t slots = (int64_t)p->TT * p->L;
+      const int gs = (int)std::min<int64_t>((n_inst * slots + 255) / 256, 4096);
+      stage_coef_kernel<<<std::max(gs, 1), 256, 0, st>>>(n_inst, slots, std::max(p->maxpf, 1),
+                                                         p->d_cpar, p->d_s64, p->d_c0, B.d_p1,
+                                                         p->P, B.dc, B.dcf, B.dcdf);
+      HC_CUDA(cudaGetLastError());
+      ta.coef_mode = 1;
+      ta.c0 = p->d_c0;
+      ta.c0f = p->d_c0f;
+      ta.c0df = p->d_c0df;
+      ta.dc = B.dc;
+      ta.dcf = B.dcf;
+      ta.dcdf = B.dcdf;
+    }
     const hc::KernelRef k = hc::term_kernel(n, mixed, mixed ? p->s.lanes : 0);
     auto smem_of = [&](const hc::KernelRef& kr, int threads = hc::kBlock) {
       return (size_t)hc::block_smem_bytes(kr.lanes, p->extra, kr.acc_bytes, threads);
     };
     HC_CUDA(mark(ev.ek0, st));
-    if ((rc = launch_generic(k, &ta, smem_of(k), items, st)) != HC_OK) return rc;
+    const int bth = std::max(main_threads(p->s), k.lanes);
+    if ((rc = launch_generic(k, &ta, smem_of(k, bth), items, st, bth)) != HC_OK) return rc;
     HC_CUDA(mark(ev.ek1, st));
     if (escalate) {
       if (ev.capture) HC_CUDA(cudaEventRecord(ev.fork, st));
@@ -1356,7 +1533,8 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
       return HC_ERR_UNSUPPORTED;
     }
     HC_CUDA(mark(ev.ek0, st));
-    if ((rc = launch_tracker(k, a, items, st)) != HC_OK) return rc;
+    if ((rc = launch_tracker(k, a, items, st, std::max(main_threads(p->s), k.lanes))) != HC_OK)
+      return rc;
     HC_CUDA(mark(ev.ek1, st));
     if (escalate) {
       if (ev.capture) HC_CUDA(cudaEventRecord(ev.fork, st));
@@ -1412,7 +1590,7 @@ hc_status validate_batch(hc_problem* p, const hc_batch_desc* b) {
         return HC_ERR_INVALID;
       }
   }
-  if (p->kind == HC_PARAMETER && !b->p1) {
+  if (p->kind != HC_TOTAL_DEGREE && !b->p1) {
     set_err("parameter homotopy batch needs p1");
     return HC_ERR_INVALID;
   }
@@ -1973,16 +2151,18 @@ hc_status hc_autotune(hc_problem* p, const hc_batch_desc* sample, hc_tune_report
     const bool has = p->terms ? hc::term_kernel(p->n, true, lanes).lanes == (lanes ? lanes : hc::term_kernel(p->n, true, 0).lanes)
                               : hc::dense_kernel(p->deg, p->n, true, lanes).lanes == (lanes ? lanes : p->L);
     if (lanes && (!has || p->n > 16)) continue;
-    for (double corr : {0.01, 0.1}) {
-      c = base;
-      c.precision = HC_PREC_MIXED;
-      c.escalate = 1;
-      c.lanes = lanes;
-      c.max_first_corr_fp32 = corr;
-      cand.push_back(c);
-    }
+    for (int block : {128, 64})
+      for (double corr : {0.01, 0.1}) {
+        c = base;
+        c.precision = HC_PREC_MIXED;
+        c.escalate = 1;
+        c.lanes = lanes;
+        c.block_threads = block;
+        c.max_first_corr_fp32 = corr;
+        cand.push_back(c);
+      }
   }
-  if (cand.size() > 8) cand.resize(8);
+  if (cand.size() > 16) cand.resize(16);
   std::vector<double> ms(cand.size(), 0.0);
   std::vector<int64_t> fin(cand.size(), -1);
   for (size_t i = 0; i < cand.size(); ++i) {
@@ -2018,6 +2198,58 @@ hc_status hc_autotune(hc_problem* p, const hc_batch_desc* sample, hc_tune_report
       report->finite[i] = fin[i];
       report->tried[i] = cand[i];
     }
+  }
+  return HC_OK;
+}
+
+hc_status hc_autotune_cached(hc_problem* p, const hc_batch_desc* sample, const char* cache_path,
+                             hc_tune_report* report) {
+  if (!p || p->magic != kProblemMagic || !sample || !cache_path) {
+    set_err("invalid autotune arguments");
+    return HC_ERR_INVALID;
+  }
+  int deg = 0;
+  for (int k = 0; k < p->T; ++k) {
+    int d = 0;
+    for (int j = 0; j < p->n; ++j) d += p->exps[(size_t)k * p->n + j];
+    deg = std::max(deg, d);
+  }
+  char key[160];
+  std::snprintf(key, sizeof(key), "kind=%d n=%d deg=%d terms=%d params=%d sym=%d prec=%d", p->kind,
+                p->n, deg, p->T, p->P, p->n_group, p->s.precision);
+  std::map<std::string, std::string> entries;  // key -> its JSON object text
+  if (!read_tune_cache(cache_path, entries)) {
+    set_err("hc_autotune_cached: the cache file is not a tuning cache");
+    return HC_ERR_INVALID;
+  }
+  auto it = entries.find(key);
+  if (it != entries.end()) {
+    hc_settings s = p->s;
+    if (!parse_tune_entry(it->second, s) || validate_settings(s) != HC_OK) {
+      set_err("hc_autotune_cached: malformed cache entry");
+      return HC_ERR_INVALID;
+    }
+    p->s = s;
+    if (report) {
+      std::memset(report, 0, sizeof(*report));
+      report->cached = 1;
+      report->tried[0] = s;
+    }
+    return HC_OK;
+  }
+  hc_tune_report local;
+  hc_tune_report* rep = report ? report : &local;
+  hc_status rc = hc_autotune(p, sample, rep);
+  if (rc != HC_OK) return rc;
+  char obj[200];
+  std::snprintf(obj, sizeof(obj),
+                "{\"precision\": %d, \"lanes\": %d, \"block_threads\": %d, "
+                "\"max_first_corr_fp32\": %.17g}",
+                p->s.precision, p->s.lanes, p->s.block_threads, p->s.max_first_corr_fp32);
+  entries[key] = obj;
+  if (!write_tune_cache(cache_path, entries)) {
+    set_err("hc_autotune_cached: cannot write the cache file");
+    return HC_ERR_INVALID;
   }
   return HC_OK;
 }

@@ -131,6 +131,17 @@ struct TermArgs {
   const double2* p0;     // [P]
   const double2* p1;     // [instances][P]
   const double2* start;  // [paths][n]
+  // coefficient interpolation (HC_COEFFICIENT): the records carry no
+  // parameter factors; the coefficient of slot k, row i at time t is
+  // c0 + t dc, c0 = c(p0) shared, dc = c(p1) - c(p0) per instance, each in
+  // FP64, FP32 and double-float, layout [TT][ls] (dc: [instances][TT][ls])
+  int coef_mode;
+  const double2* c0;
+  const float2* c0f;
+  const cdf* c0df;
+  const double2* dc;
+  const float2* dcf;
+  const cdf* dcdf;
 };
 
 struct KernelRef {

@@ -134,7 +134,8 @@ extern "C" hc_status hc_monodromy_solve(const hc_monodromy_desc* d, int64_t* n_s
                                         hc_monodromy_info* info) {
   const auto t0 = std::chrono::steady_clock::now();
   if (!d || !d->family || !d->x0 || !d->p0 || !d->out || !n_solutions ||
-      d->family->kind != HC_PARAMETER || d->family->n < 1 || d->family->n_params < 1 ||
+      (d->family->kind != HC_PARAMETER && d->family->kind != HC_COEFFICIENT) ||
+      d->family->n < 1 || d->family->n_params < 1 ||
       d->stall_loops < 1 || d->max_loops < 1 || d->loops_per_round < 1 ||
       d->max_solutions < 1 || d->reserved != 0) {
     hc::set_last_error("hc_monodromy_solve: invalid descriptor");

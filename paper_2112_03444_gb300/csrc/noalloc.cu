@@ -310,7 +310,9 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
     void* argv[] = {(void*)&args};
     return cudaLaunchKernel(k.fn, dim3((unsigned)grid), dim3(threads), argv, smem, st);
   };
-  const hc::KernelRef k = hc::dense_kernel(degree, n, mixed, 0);
+  // the autotuner's group width where that variant exists (as hc_track_batch)
+  hc::KernelRef k = hc::dense_kernel(degree, n, mixed, mixed ? settings->lanes : 0);
+  if (!k.fn) k = hc::dense_kernel(degree, n, mixed, 0);
   if (!k.fn) {
     hc::set_last_error("hc_track_dense_noalloc: no kernel for this shape");
     return HC_ERR_UNSUPPORTED;

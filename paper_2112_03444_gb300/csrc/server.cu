@@ -178,7 +178,7 @@ void dispatch(hc_server* s) {
     std::memset(&b, 0, sizeof(b));
     b.n_instances = (int32_t)k;
     b.flags = 0;
-    if (info.kind == HC_PARAMETER)
+    if (info.kind != HC_TOTAL_DEGREE)
       b.p1 = static_cast<const double*>(sl.in.ptr);
     else
       b.coef = static_cast<const double*>(sl.in.ptr);

@@ -108,9 +108,10 @@ struct TermEval {
 
   // One term of D factors: add its value to h and its derivatives to the
   // lane's accumulators (the coefficient rides in the suffix product).
+  // Returns the product of the factors (without the coefficient).
   template <int D, class R>
-  __device__ __forceinline__ void term(const TermRec& rc, cx<R> s, const cx<R>* V, cx<R>* A,
-                                       cx<R>& h) const {
+  __device__ __forceinline__ cx<R> term(const TermRec& rc, cx<R> s, const cx<R>* V, cx<R>* A,
+                                        cx<R>& h) const {
     cx<R> pre[D];
     cx<R> run = mk<R>(R(1), R(0));
 #pragma unroll
@@ -132,6 +133,23 @@ struct TermEval {
       }
       if (f > 0) suf = suf * v;
     }
+    return run;
+  }
+
+  // Coefficient interpolation (a->coef_mode): the coefficient of record r
+  // at time t, c0 + t dc, and its t-derivative dc, for this instance.
+  template <class R>
+  __device__ __forceinline__ void coef_at(int64_t r, R t, cx<R>& s, cx<R>& dcr) const {
+    const int64_t rd = inst * (int64_t)a->TT * a->ls + r;
+    if constexpr (std::is_same<R, float>::value) {
+      const float2 c = a->c0f[r], d = a->dcf[rd];
+      dcr = mk<float>(d.x, d.y);
+      s = cfma(mk<float>(t, 0.f), dcr, mk<float>(c.x, c.y));
+    } else {
+      const double2 c = a->c0[r], d = a->dc[rd];
+      dcr = mk<double>(d.x, d.y);
+      s = cfma(mk<double>(t, 0.0), dcr, mk<double>(c.x, c.y));
+    }
   }
 
   template <class R>
@@ -148,22 +166,27 @@ struct TermEval {
     for (int k = 0; k < a->TT; ++k) {
       const int64_t r = (int64_t)k * a->ls + ii;
       const TermRec rc = a->rec[r];
-      cx<R> s;
-      if constexpr (std::is_same<R, float>::value)
+      cx<R> s, dcr = czero<R>();
+      if (a->coef_mode)
+        coef_at<R>(r, t, s, dcr);
+      else if constexpr (std::is_same<R, float>::value)
         s = mk<float>(rc.s.x, rc.s.y);
       else
         s = mk<double>(a->s64[r].x, a->s64[r].y);
+      cx<R> run = czero<R>();
       switch (rc.d) {  // the same at a slot for every row and path: no divergence
-        case 1: term<1, R>(rc, s, V, A, h); break;
-        case 2: term<2, R>(rc, s, V, A, h); break;
-        case 3: term<3, R>(rc, s, V, A, h); break;
-        case 4: term<4, R>(rc, s, V, A, h); break;
-        case 5: term<5, R>(rc, s, V, A, h); break;
-        case 6: term<6, R>(rc, s, V, A, h); break;
-        case 7: term<7, R>(rc, s, V, A, h); break;
-        case 8: term<8, R>(rc, s, V, A, h); break;
+        case 1: run = term<1, R>(rc, s, V, A, h); break;
+        case 2: run = term<2, R>(rc, s, V, A, h); break;
+        case 3: run = term<3, R>(rc, s, V, A, h); break;
+        case 4: run = term<4, R>(rc, s, V, A, h); break;
+        case 5: run = term<5, R>(rc, s, V, A, h); break;
+        case 6: run = term<6, R>(rc, s, V, A, h); break;
+        case 7: run = term<7, R>(rc, s, V, A, h); break;
+        case 8: run = term<8, R>(rc, s, V, A, h); break;
         default: break;
       }
+      // coefficient interpolation: d/dt of (c0 + t dc) x^a is dc x^a
+      if (a->coef_mode) A[N * L] = cfma(dcr, run, A[N * L]);
     }
 #pragma unroll
     for (int j = 0; j < N; ++j) row[j] = A[j * L];
@@ -185,7 +208,11 @@ struct TermEval {
       cx<double> prod = Vd[rc.idx[0]];
 #pragma unroll 1
       for (int f = 1; f < rc.d; ++f) prod = prod * Vd[rc.idx[f]];
-      const cx<double> s = mk<double>(a->s64[r].x, a->s64[r].y);
+      cx<double> s, dcr;
+      if (a->coef_mode)
+        coef_at<double>(r, t, s, dcr);
+      else
+        s = mk<double>(a->s64[r].x, a->s64[r].y);
       h = cfma(s, prod, h);
       if (SCALE) s_abs += cabs2(cvt<float>(s)) * cabs2(cvt<float>(prod));
     }
@@ -217,7 +244,10 @@ struct TermEval {
       cdf prod = V[rc.idx[0]];
 #pragma unroll 1
       for (int f = 1; f < rc.d; ++f) prod = cdf_mul(prod, V[rc.idx[f]]);
-      const cdf s = a->sdf[r];
+      const cdf s = a->coef_mode
+                        ? cdf_add(a->c0df[r],
+                                  cdf_scale(tdf, a->dcdf[inst * (int64_t)a->TT * a->ls + r]))
+                        : a->sdf[r];
       h = cdf_fma(s, prod, h);
       if (SCALE) s_abs += cdf_abs_hi(s) * cdf_abs_hi(prod);
     }

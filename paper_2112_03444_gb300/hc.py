@@ -28,7 +28,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 HC_OK, HC_PENDING = 0, 1
 HC_ERR_INVALID, HC_ERR_OOM, HC_ERR_CUDA, HC_ERR_TIMEOUT = -1, -2, -3, -4
 HC_ERR_NUMERIC, HC_ERR_BUSY, HC_ERR_UNSUPPORTED = -5, -6, -7
-HC_TOTAL_DEGREE, HC_PARAMETER = 0, 1
+HC_TOTAL_DEGREE, HC_PARAMETER, HC_COEFFICIENT = 0, 1, 2
 HC_PREC_FP64, HC_PREC_MIXED = 0, 1
 HC_DEVICE_PTRS, HC_BLOCKING_ADMIT = 1, 2
 PATH_FINITE, PATH_DIVERGED, PATH_FAIL_STEP, PATH_FAIL_MAXSTEPS = 1, 2, 3, 4
@@ -47,7 +47,7 @@ class hc_settings(ctypes.Structure):
                 ("grow_after", ctypes.c_int32), ("refine_iters", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("escalate", ctypes.c_int32),
                 ("lanes", ctypes.c_int32), ("max_newton_ir", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("block_threads", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -134,12 +134,16 @@ class hc_request_info(ctypes.Structure):
 
 class hc_tune_report(ctypes.Structure):
     _fields_ = [("n_candidates", ctypes.c_int32), ("best", ctypes.c_int32),
-                ("ms", ctypes.c_double * 8), ("finite", ctypes.c_int64 * 8),
-                ("tried", hc_settings * 8)]
+                ("cached", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("ms", ctypes.c_double * 16), ("finite", ctypes.c_int64 * 16),
+                ("tried", hc_settings * 16)]
 
 
 _lib.hc_autotune.restype = ctypes.c_int32
 _lib.hc_autotune.argtypes = [_P, ctypes.POINTER(hc_batch_desc), ctypes.POINTER(hc_tune_report)]
+_lib.hc_autotune_cached.restype = ctypes.c_int32
+_lib.hc_autotune_cached.argtypes = [_P, ctypes.POINTER(hc_batch_desc), ctypes.c_char_p,
+                                    ctypes.POINTER(hc_tune_report)]
 _lib.hc_problem_query.restype = ctypes.c_int32
 _lib.hc_problem_query.argtypes = [_P, ctypes.POINTER(hc_problem_info)]
 _lib.hc_server_default_config.restype = hc_server_config
@@ -168,7 +172,7 @@ EXPORTED = ("hc_status_string", "hc_last_error", "hc_default_settings", "hc_crea
             "hc_measure_fma_peak", "hc_track_dense_noalloc", "hc_server_default_config",
             "hc_server_create", "hc_server_submit", "hc_server_wait", "hc_server_stats",
             "hc_autotune", "hc_plan_create", "hc_plan_run", "hc_set_memory_cap",
-            "hc_batched_solve", "hc_monodromy_solve")
+            "hc_batched_solve", "hc_monodromy_solve", "hc_autotune_cached")
 
 
 def problem_query(problem: int) -> dict:
@@ -492,9 +496,10 @@ class Problem:
         """A Plan: this batch size captured once as a CUDA graph (hc_plan_create)."""
         return Plan(self, n_instances)
 
-    def autotune(self, n_instances=1, coef=None, p1=None):
-        """hc_autotune on a host sample batch; returns the report as a dict and
-        keeps the chosen settings in the problem (and in self.settings)."""
+    def autotune(self, n_instances=1, coef=None, p1=None, cache=None):
+        """hc_autotune (or hc_autotune_cached with a cache file path) on a host
+        sample batch; returns the report as a dict and keeps the chosen
+        settings in the problem (and in self.settings)."""
         I, P, n = int(n_instances), self.paths, self.n
         bufs = dict(x=np.zeros((I, P, n), np.complex128), st=np.zeros((I, P), np.uint8),
                     steps=np.zeros((I, P, 3), np.int32))
@@ -506,11 +511,16 @@ class Problem:
         b.p1 = _addr(p1)
         b.x_out, b.status_out, b.steps_out = (_addr(bufs[k]) for k in ("x", "st", "steps"))
         rep = hc_tune_report()
-        _check(_lib.hc_autotune(self.h, ctypes.byref(b), ctypes.byref(rep)), "hc_autotune")
+        if cache is None:
+            _check(_lib.hc_autotune(self.h, ctypes.byref(b), ctypes.byref(rep)), "hc_autotune")
+        else:
+            _check(_lib.hc_autotune_cached(self.h, ctypes.byref(b), str(cache).encode(),
+                                           ctypes.byref(rep)), "hc_autotune_cached")
         self.settings = rep.tried[rep.best]
-        return dict(best=rep.best, ms=list(rep.ms[:rep.n_candidates]),
+        return dict(best=rep.best, cached=bool(rep.cached), ms=list(rep.ms[:rep.n_candidates]),
                     finite=list(rep.finite[:rep.n_candidates]),
                     tried=[dict(precision=rep.tried[i].precision, lanes=rep.tried[i].lanes,
+                                block_threads=rep.tried[i].block_threads,
                                 max_first_corr_fp32=rep.tried[i].max_first_corr_fp32)
                            for i in range(rep.n_candidates)])
 

@@ -727,3 +727,43 @@ def dense_sweep(rank: int = 0, systems: int = DENSE_SWEEP_SYSTEMS):
         base, coefs = dense_batch(n, d, seeds)
         out.append(dict(n=n, d=d, base=base, coefs=coefs, seeds=seeds, gamma=unit_gamma(seeds[0])))
     return out
+
+
+def total_degree_as_parameter_family(system: TermSystem, gamma: complex):
+    """A total-degree homotopy written as a parameter homotopy: the family
+    F(x; p) = sum_k p_k x^alpha_k over the union of the monomials of F and of
+    the start system G_i = x_i^{d_i} - 1, with p1 = F's coefficients (0 where
+    only G has a monomial) and p0 = gamma G's (gamma on x_i^{d_i}, -gamma on
+    the constant of equation i, 0 elsewhere), so that F(x; (1-t) p0 + t p1) =
+    (1-t) gamma G(x) + t F(x).  Returns (family system, p0, p1, start) with
+    start the prod d_i roots of unity, path k from the base-d_i digits of k
+    (variable 1 least significant)."""
+    n = system.n
+    deg = system.degrees()
+    terms = {}
+    for k in range(system.n_terms):
+        key = (int(system.term_eq[k]), tuple(int(e) for e in system.term_exp[k]))
+        terms[key] = terms.get(key, 0) + complex(system.term_coef[k])
+    g = {}
+    for i in range(n):
+        e = [0] * n
+        e[i] = int(deg[i])
+        g[(i, tuple(e))] = complex(gamma)
+        g[(i, (0,) * n)] = g.get((i, (0,) * n), 0) - complex(gamma)
+    keys = sorted(set(terms) | set(g))
+    T = len(keys)
+    sys_ = TermSystem(n=n, term_eq=np.array([k[0] for k in keys]), term_coef=np.ones(T),
+                      term_exp=np.array([k[1] for k in keys]).reshape(T, n),
+                      term_param=np.arange(T, dtype=np.int32)[:, None], n_params=T,
+                      name=f"{system.name}_as_parameter_family")
+    p0 = np.array([g.get(k, 0) for k in keys], np.complex128)
+    p1 = np.array([terms.get(k, 0) for k in keys], np.complex128)
+    paths = int(np.prod(deg))
+    start = np.zeros((paths, n), np.complex128)
+    for p in range(paths):
+        r = p
+        for i in range(n):
+            d = int(deg[i])
+            start[p, i] = np.exp(2j * np.pi * (r % d) / d)
+            r //= d
+    return sys_, p0, p1, start

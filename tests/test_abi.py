@@ -110,7 +110,8 @@ def test_null_handles_are_rejected(hc):
     hc._lib.hc_destroy(None)  # no-op
 
 
-@pytest.mark.parametrize("field,value", [("max_newton_ir", 0), ("max_newton_ir", 33), ("reserved", 1),
+@pytest.mark.parametrize("field,value", [("max_newton_ir", 0), ("max_newton_ir", 33),
+                                         ("block_threads", 16), ("block_threads", 256),
                                          ("lanes", 16)])
 def test_create_problem_rejects_bad_iteration_limits(hc, field, value):
     from paper_2112_03444_gb300 import inputs
@@ -122,7 +123,7 @@ def test_create_problem_rejects_bad_iteration_limits(hc, field, value):
 
 def test_default_refinement_iterations(hc):
     s = hc.default_settings()
-    assert s.max_newton_ir == 2 * s.max_newton and s.reserved == 0
+    assert s.max_newton_ir == 2 * s.max_newton and s.block_threads == 0
 
 
 def test_plan_calls_reject_null_handles(hc):

@@ -40,16 +40,17 @@ def _ill_determined(ref_problem, start_row, base_class):
     return False
 
 
-def _check(hc, system, p0, p1s, start, precision, symmetries=()):
+def _check(hc, system, p0, p1s, start, precision, symmetries=(), kind=None):
     """Exact status counts and bijective endpoint match, on every path whose
     oracle outcome is stable; a path on which the GPU and the oracle differ
     must be ill-determined (see PERTURB), at most 1 % of an instance, and a
     finite GPU endpoint there must still pass the backward-error test."""
-    pr = hc.Problem(system, kind=hc.HC_PARAMETER, p0=p0, start=start,
+    kind = hc.HC_PARAMETER if kind is None else kind
+    pr = hc.Problem(system, kind=kind, p0=p0, start=start,
                     settings=dict(precision=precision), symmetries=symmetries)
     b = pr.track(n_instances=len(p1s), p1=np.array(p1s)).wait()
     for s, p1 in enumerate(p1s):
-        refp = OracleProblem(system, kind=KIND_PARAMETER, p0=p0, p1=p1)
+        refp = OracleProblem(system, kind=int(kind), p0=p0, p1=p1)
         ref = refp.track(start=start)
         gc, oc = b.status[s] & 0x7F, ref["status"] & 0x7F
         keep = np.ones(len(start), bool)
@@ -111,6 +112,23 @@ def test_more_vision_problems_match_oracle(hc, name, precision, sym):
     p1s = [scene(s)[0] for s in (61, 62, 63)]
     _check(hc, fam.system, z["p0"], p1s, z["start"], precision,
            symmetries=fam.sign_masks if sym else ())
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("name", ["triangulation4", "p3p", "pose5_depth"])
+def test_coefficient_interpolation_matches_oracle(hc, name, precision):
+    """The coefficient-interpolation homotopy of Sec. 6 (HC_COEFFICIENT: the
+    term coefficients, products of parameters, interpolated linearly) against
+    the oracle's own coefficient-interpolation mode, from the monodromy start
+    sets to three noisy scenes."""
+    from paper_2112_03444_gb300 import inputs
+    if name == "triangulation4":
+        fam, scene = inputs.triangulation_family(4), inputs.triangulation_scene
+    else:
+        fam, scene = _family(name)
+    z = np.load(os.path.join(STARTS, f"{name}.npz"))
+    p1s = [scene(s)[0] for s in (71, 72, 73)]
+    _check(hc, fam.system, z["p0"], p1s, z["start"], precision, kind=hc.HC_COEFFICIENT)
 
 
 def test_parameter_batch_device_pointers(hc):
@@ -241,8 +259,8 @@ def test_trifocal_orbit_reduction_is_exact(hc):
         best, sg = j, signs[0]
         for e in range(1, 4):
             y = signs[e] * S[j]
-            d, i = tree.query(np.concatenate([y.real, y.imag]))
-            assert d < 1e-9
+            d, i = tree.query(np.concatenate([y.real, y.imag]), p=np.inf)
+            assert d <= 1e-9 * max(1.0, float(np.max(np.abs(y))))   # the library's rule
             if i < best:
                 best, sg = i, signs[e]
         exact[j] = sg * S[best]
@@ -273,3 +291,69 @@ def test_symmetry_validation(hc):
         hc.Problem(fam.system, kind=hc.HC_PARAMETER, p0=z["p0"], start=z["start"][:5],
                    symmetries=fam.sign_masks)
     assert e.value.code == hc.HC_ERR_INVALID
+
+
+def _poly(n, polys):
+    from paper_2112_03444_gb300 import inputs
+    return inputs.system_from_polys(n, polys)
+
+
+EDGE_CASES = {
+    # x_i^2 = a_i, a_i > 0: 8 real roots
+    "decoupled_real_squares": (3, [{(2, 0, 0): 1, (0, 0, 0): -2.0}, {(0, 2, 0): 1, (0, 0, 0): -0.5},
+                                   {(0, 0, 2): 1, (0, 0, 0): -3.0}], 5),
+    # x^2 = 1 + i: two finite non-real roots
+    "complex_square": (1, [{(2,): 1, (0,): -(1 + 1j)}], 6),
+    # x1^2 = a, x2^2 = x1 + b
+    "triangular": (2, [{(2, 0): 1, (0, 0): -(1.5 - 0.5j)},
+                       {(0, 2): 1, (1, 0): -1, (0, 0): -(0.25 + 2j)}], 8),
+    # x1 x2 = 1, x1 x2 + x1 = 2: one finite root, three paths to infinity
+    "deficient": (2, [{(1, 1): 1, (0, 0): -1}, {(1, 1): 1, (1, 0): 1, (0, 0): -2}], 9),
+    # x^2 = 0: both paths end at a double root
+    "double_root": (1, [{(2,): 1.0}], 10),
+}
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("case", sorted(EDGE_CASES))
+def test_edge_cases_match_oracle_exactly(hc, case, precision):
+    """The method's degenerate cases (paths to infinity, a double root, real
+    roots), each a total-degree homotopy written as a parameter family: the
+    GPU's statuses equal the oracle's path by path -- diverged, singular,
+    failed and the real bit included -- and the finite endpoints match."""
+    from paper_2112_03444_gb300 import inputs
+    n, polys, gseed = EDGE_CASES[case]
+    fam, p0, p1, start = inputs.total_degree_as_parameter_family(_poly(n, polys),
+                                                                 inputs.unit_gamma(gseed))
+    pr = hc.Problem(fam, kind=hc.HC_PARAMETER, p0=p0, start=start,
+                    settings=dict(precision=precision))
+    b = pr.track(n_instances=1, p1=p1[None, :]).wait()
+    ref = OracleProblem(fam, kind=KIND_PARAMETER, p0=p0, p1=p1).track(start=start)
+    assert np.array_equal(b.status[0], ref["status"]), (b.status[0], ref["status"])
+    fin = (ref["status"] & 0x7F) == oracle.FINITE
+    ok, msg = same_set(b.x[0][fin], ref["x"][fin], TOL)
+    assert ok, msg
+    # and the oracle's parameter form is its total-degree homotopy (pinned there)
+    td = OracleProblem(_poly(n, polys), gamma=inputs.unit_gamma(gseed)).track()
+    assert oracle.status_counts(td["status"]) == oracle.status_counts(ref["status"])
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_path_to_infinity_is_diverged_like_the_oracle(hc, precision):
+    """F(x; p) = (p x - y, p y - 1) has the single root y = 1/p, x = 1/p^2;
+    from p = 1 to p = 0 the path leaves every bounded set like (1-t)^-2 and
+    passes the divergence radius before the step size underflows: both the
+    GPU and the oracle classify it HC_PATH_DIVERGED (the oracle's class is
+    checked too, so the test fails if either changes)."""
+    from paper_2112_03444_gb300 import inputs
+    fam = inputs.TermSystem(n=2, term_eq=[0, 0, 1, 1], term_coef=[1, -1, 1, -1],
+                            term_exp=[[1, 0], [0, 1], [0, 1], [0, 0]],
+                            term_param=[[0], [-1], [0], [-1]], n_params=1)
+    p0, p1 = np.array([1.0 + 0j]), np.array([0.0 + 0j])
+    start = np.array([[1.0, 1.0]], np.complex128)
+    pr = hc.Problem(fam, kind=hc.HC_PARAMETER, p0=p0, start=start,
+                    settings=dict(precision=precision))
+    b = pr.track(n_instances=1, p1=p1[None, :]).wait()
+    ref = OracleProblem(fam, kind=KIND_PARAMETER, p0=p0, p1=p1).track(start=start)
+    assert ref["status"][0] == oracle.DIVERGED
+    assert b.status[0][0] == ref["status"][0]

@@ -89,3 +89,50 @@ def test_autotune_keeps_fp64_recovery(hc):
     assert rep["finite"][rep["best"]] >= rep["finite"][0] == 2 * 128
     b = pr.track(n_instances=2, coef=coefs).wait()
     assert b.result["finite"] == 256
+
+
+@pytest.mark.parametrize("block", [32, 64])
+def test_block_size_does_not_change_the_paths(hc, block):
+    """Paths per block (block_threads) only regroups lane groups into blocks:
+    with re-tracking off, every path's statuses and endpoints are the same
+    bit for bit."""
+    from paper_2112_03444_gb300 import inputs
+    base, coefs = inputs.dense_batch(8, 3, [97])
+    g = inputs.unit_gamma(97)
+    out = []
+    for bt in (0, block):
+        pr = hc.Problem(base, gamma=g, settings=dict(block_threads=bt, escalate=0))
+        out.append(pr.track(n_instances=1, coef=coefs).wait())
+    assert np.array_equal(out[0].status, out[1].status)
+    assert np.array_equal(out[0].x, out[1].x, equal_nan=True)
+
+
+def test_autotune_cache_roundtrip(hc, tmp_path):
+    """hc_autotune_cached: the first call tunes (block and lane axes included)
+    and writes the choice under the problem's shape key; a second problem of
+    the same shape takes it from the file without tracking; a malformed file
+    is refused."""
+    import json
+    from paper_2112_03444_gb300 import inputs
+    base, coefs = inputs.dense_batch(8, 2, [98, 99])
+    cache = tmp_path / "tune.json"
+    pr = hc.Problem(base, gamma=inputs.unit_gamma(98))
+    rep = pr.autotune(n_instances=2, coef=coefs, cache=cache)
+    assert not rep["cached"] and len(rep["ms"]) >= 5
+    assert {t["block_threads"] for t in rep["tried"][1:]} >= {64, 128}
+    doc = json.loads(cache.read_text())
+    (key, entry), = doc.items()
+    assert "n=8" in key and "deg=2" in key
+    assert entry["block_threads"] == rep["tried"][rep["best"]]["block_threads"]
+    pr2 = hc.Problem(base, gamma=inputs.unit_gamma(98))
+    rep2 = pr2.autotune(n_instances=2, coef=coefs, cache=cache)
+    assert rep2["cached"] and rep2["ms"] == []
+    assert pr2.settings.block_threads == entry["block_threads"]
+    assert pr2.settings.lanes == entry["lanes"]
+    b = pr2.track(n_instances=2, coef=coefs).wait()
+    assert b.result["finite"] == 2 * 256
+    bad = tmp_path / "bad.json"
+    bad.write_text('{"kind=0 n=8 deg=2 terms=360 params=0 sym=1 prec=1": {"lanes": ')
+    with pytest.raises(hc.HCError):
+        hc.Problem(base, gamma=inputs.unit_gamma(98)).autotune(n_instances=2, coef=coefs,
+                                                               cache=bad)

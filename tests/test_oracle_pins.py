@@ -428,3 +428,42 @@ def test_cond1_matches_library_on_random_jacobians(seed):
     x = inputs.random_complex(4, seed + 50)
     _, Hx, _ = pr.eval(x, 1.0)
     assert abs(pr.cond1(x) - np.linalg.cond(Hx, 1)) <= 1e-10 * np.linalg.cond(Hx, 1)
+
+
+# ---------------------------------------------------------------- coefficient interpolation
+def test_coefficient_interpolation_closed_form():
+    """Sec. 6 interpolates the coefficients: F = p0 p1 x^2 - 1 with p(0) = (a0,
+    b0), p(1) = (a1, b1) gives H = c(t) x^2 - 1, c(t) = (1-t) a0 b0 + t a1 b1,
+    dH/dt = (a1 b1 - a0 b0) x^2, dH/dx = 2 c(t) x; the parameter homotopy
+    instead has c(t) = ((1-t) a0 + t a1)((1-t) b0 + t b1)."""
+    sys_ = inputs.TermSystem(n=1, term_eq=np.array([0, 0]), term_coef=np.array([1.0, -1.0]),
+                             term_exp=np.array([[2], [0]]), term_param=np.array([[0, 1], [-1, -1]]),
+                             n_params=2)
+    a0, b0, a1, b1 = 1 + 2j, 0.5 - 1j, -2 + 0.25j, 3 + 1j
+    p0, p1 = np.array([a0, b0]), np.array([a1, b1])
+    x, t = np.array([0.7 - 0.4j]), 0.3
+    pc = OracleProblem(sys_, kind=oracle.KIND_COEFFICIENT, p0=p0, p1=p1)
+    H, Hx, Ht = pc.eval(x, t)
+    c = (1 - t) * a0 * b0 + t * a1 * b1
+    assert abs(H[0] - (c * x[0] ** 2 - 1)) < 1e-14
+    assert abs(Ht[0] - (a1 * b1 - a0 * b0) * x[0] ** 2) < 1e-14
+    assert abs(Hx[0, 0] - 2 * c * x[0]) < 1e-14
+    pp = OracleProblem(sys_, kind=oracle.KIND_PARAMETER, p0=p0, p1=p1)
+    cp = ((1 - t) * a0 + t * a1) * ((1 - t) * b0 + t * b1)
+    assert abs(pp.eval(x, t)[0][0] - (cp * x[0] ** 2 - 1)) < 1e-14
+    # tracking from x = 1/sqrt(a0 b0) ends at a square root of 1/(a1 b1)
+    r = pc.track(start=np.array([[1 / np.sqrt(a0 * b0)]]))
+    assert (r["status"][0] & 0x7F) == oracle.FINITE
+    assert abs(r["x"][0, 0] ** 2 * a1 * b1 - 1) < 1e-12
+
+
+def test_coefficient_interpolation_equals_parameter_homotopy_when_linear():
+    """When every coefficient is one parameter (the dense family written as
+    a parameter family), interpolating coefficients and interpolating
+    parameters are the same homotopy: identical results, bit for bit."""
+    sys_, p1, p0 = inputs.dense_parameter_family(3, 2, 62)
+    start = np.array([OracleProblem(inputs.dense_system(3, 2, 62)).start_point(k) for k in range(8)])
+    a = OracleProblem(sys_, kind=KIND_PARAMETER, p0=p0, p1=p1).track(start=start)
+    b = OracleProblem(sys_, kind=oracle.KIND_COEFFICIENT, p0=p0, p1=p1).track(start=start)
+    assert np.array_equal(a["status"], b["status"])
+    assert np.array_equal(a["x"], b["x"])
