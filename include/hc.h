@@ -138,6 +138,25 @@ typedef struct hc_settings {
   int32_t block_threads;  /* threads per block of the main tracking launch: 0 (the
                              default, 128), 32, 64 or 128; paths per block =
                              threads / lanes (the autotuner's block axis)       */
+  /* Power-series endgame (Morgan, Sommese & Wampler 1992; the paper is
+   * silent on endgames), off by default.  Past t = 1 - eg_s0 the step control
+   * lands on the sample times 1 - eg_s0 eg_ratio^k (k < eg_samples); the cycle
+   * number c (<= eg_cmax) comes from the ratio of successive sample
+   * differences, and the endpoint is predicted by cubic Hermite
+   * extrapolation to s = 0 in w = (1 - t)^(1/c) while the samples converge.
+   * Two agreeing predictions with c > 1 end the path at the prediction,
+   * HC_PATH_SINGULAR if its backward error passes; a step-size failure inside
+   * the endgame takes the last such prediction.  Paths with c = 1 (nonsingular
+   * endpoints) are tracked to t = 1 as without the endgame.  It runs in the all-FP64 kernel (precision FP64, and the
+   * all-FP64 re-tracking tier of the mixed pipeline, which receives the
+   * paths that fail near their end).                                        */
+  int32_t endgame;        /* 0: off, 1: power-series endgame */
+  int32_t eg_cmax;        /* 8 */
+  int32_t eg_samples;     /* 40 */
+  int32_t eg_reserved;    /* 0 */
+  double eg_s0;           /* 0.1 */
+  double eg_ratio;        /* 0.5 */
+  double eg_tol;          /* agreement of two predictions, relative: 1e-8 */
 } hc_settings;
 
 /*
@@ -403,7 +422,9 @@ hc_status hc_autotune_cached(hc_problem* p, const hc_batch_desc* sample, const c
 typedef struct hc_server hc_server;  /* opaque */
 
 typedef struct hc_server_config {
-  int32_t n_streams;           /* concurrent batches (streams), default 4            */
+  int32_t n_streams;           /* concurrent batches (streams), default 4; while
+                                  several problems wait, one problem holds at most
+                                  half of them                                     */
   int32_t max_batch_instances; /* instances per batch, default 64                    */
   int64_t max_device_bytes;    /* admission cap on in-flight batches, default 8 GiB  */
 } hc_server_config;

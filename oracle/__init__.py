@@ -30,12 +30,14 @@ KIND_TOTAL_DEGREE, KIND_PARAMETER, KIND_COEFFICIENT = 0, 1, 2
 # Order of the settings vector passed to the C++ side.
 SETTINGS_ORDER = ("dt_min", "dt_max", "dt_init", "newton_tol", "max_newton", "max_steps",
                   "grow_after", "refine_tol", "refine_iters", "r_inf", "finite_tol",
-                  "real_tol", "singular_cond", "max_first_corr")
+                  "real_tol", "singular_cond", "max_first_corr", "endgame", "eg_s0",
+                  "eg_ratio", "eg_tol", "eg_cmax", "eg_samples")
 
 DEFAULT_SETTINGS = dict(dt_min=1e-6, dt_max=0.05, dt_init=0.01, newton_tol=1e-8,
                         max_newton=3, max_steps=100000, grow_after=3, refine_tol=1e-13,
                         refine_iters=8, r_inf=1e8, finite_tol=1e-10, real_tol=1e-8,
-                        singular_cond=1e12, max_first_corr=0.1)
+                        singular_cond=1e12, max_first_corr=0.1, endgame=0, eg_s0=0.1,
+                        eg_ratio=0.5, eg_tol=1e-8, eg_cmax=8, eg_samples=40)
 
 
 def build(force: bool = False) -> str:

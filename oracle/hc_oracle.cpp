@@ -61,6 +61,10 @@ struct Settings {
   int refine_iters;
   double r_inf, finite_tol, real_tol, singular_cond;
   double max_first_corr;
+  // power-series endgame (off when endgame == 0)
+  int endgame;
+  double eg_s0, eg_ratio, eg_tol;
+  int eg_cmax, eg_samples;
 };
 
 Settings settings_from(const double* s) {
@@ -70,6 +74,8 @@ Settings settings_from(const double* s) {
   o.refine_tol = s[7]; o.refine_iters = (int)s[8];
   o.r_inf = s[9]; o.finite_tol = s[10]; o.real_tol = s[11]; o.singular_cond = s[12];
   o.max_first_corr = s[13];
+  o.endgame = (int)s[14]; o.eg_s0 = s[15]; o.eg_ratio = s[16]; o.eg_tol = s[17];
+  o.eg_cmax = (int)s[18]; o.eg_samples = (int)s[19];
   return o;
 }
 
@@ -307,6 +313,82 @@ double cond1_at_end(const Problem& pr, const cd* x) {
   return an * norm1(n, inv.data());
 }
 
+// ---------------------------------------------------------------- endgame
+// Power-series endgame (Morgan, Sommese & Wampler, "A power series method for
+// computing singular solutions to nonlinear analytic systems", Numer. Math.
+// 63, 1992; the paper itself is silent on endgames).  With s = 1 - t, a path
+// ending at a root of multiplicity m has a fractional power series
+// x(s) = sum_k a_k s^(k/c), c the cycle (winding) number; it is analytic in
+// w = s^(1/c).  Samples at geometric s_k = s0 h^k give c from the ratio of
+// successive differences (|x_k - x_(k+1)| ~ s_k^(1/c)), and the value at
+// w = 0 of the cubic Hermite interpolant of two samples (values and
+// dx/dw = dx/ds c w^(c-1)) predicts the endpoint.
+struct Endgame {
+  int n = 0, samples = 0, c = 1, next = 0;
+  double s_next = 0.0, dn_prev = 0.0;
+  bool have_pred = false;
+  std::vector<cd> xa, da, pred;  // previous sample, its dx/ds, the last prediction
+};
+
+// value at w = 0 of the cubic Hermite interpolant through (wb, xb, Db) and
+// (wa, xa, Da), wb < wa
+cd hermite_at_zero(double wb, cd xb, cd Db, double wa, cd xa, cd Da) {
+  const double dl = wa - wb, tau = -wb / dl;
+  const double t2 = tau * tau, t3 = t2 * tau;
+  const double h00 = 2 * t3 - 3 * t2 + 1, h10 = t3 - 2 * t2 + tau;
+  const double h01 = -2 * t3 + 3 * t2, h11 = t3 - t2;
+  return h00 * xb + h10 * dl * Db + h01 * xa + h11 * dl * Da;
+}
+
+// A sample at s (the path point x and dx/ds there).  A prediction is made
+// only while the samples converge: the difference to the previous sample
+// shrinks, and the predicted endpoint lies within the tail such a series
+// leaves, 4 |x_k - x_(k-1)| / (1 - h^(1/c)), of the sample (paths to
+// infinity, whose differences grow, get none).  Returns true once two
+// successive predictions with the same cycle number c > 1 agree within
+// eg_tol (1 + |x|): eg.pred then holds the endpoint and eg.c the cycle number.
+// (A path with c = 1 ends at a nonsingular root that ordinary tracking
+// reaches; a Newton refinement started from a misjudged c = 1 prediction
+// next to a multiple root could land anywhere.)
+bool endgame_sample(Endgame& eg, const Settings& s, double sk, const cd* x, const cd* dxds) {
+  const int n = eg.n;
+  bool done = false;
+  if (eg.samples >= 1) {
+    double dn = 0.0;
+    for (int i = 0; i < n; ++i) dn = std::max(dn, std::abs(x[i] - eg.xa[i]));
+    bool predicted = false;
+    if (eg.samples >= 2 && dn > 0.0 && eg.dn_prev > 0.0 && dn < eg.dn_prev) {
+      const double r = std::log(s.eg_ratio) / std::log(dn / eg.dn_prev);
+      const int c = std::min(std::max((int)std::lround(r), 1), s.eg_cmax);
+      const double sa = sk / s.eg_ratio;  // the previous sample's s
+      const double wb = std::pow(sk, 1.0 / c), wa = std::pow(sa, 1.0 / c);
+      std::vector<cd> P(n);
+      double pn = 0.0, dp = 0.0, dx = 0.0;
+      for (int i = 0; i < n; ++i) {
+        const cd Db = dxds[i] * ((double)c * std::pow(wb, c - 1));
+        const cd Da = eg.da[i] * ((double)c * std::pow(wa, c - 1));
+        P[i] = hermite_at_zero(wb, x[i], Db, wa, eg.xa[i], Da);
+        pn = std::max(pn, std::abs(P[i]));
+        dx = std::max(dx, std::abs(P[i] - x[i]));
+        if (eg.have_pred) dp = std::max(dp, std::abs(P[i] - eg.pred[i]));
+      }
+      const double tail = 4.0 * dn / (1.0 - std::pow(s.eg_ratio, 1.0 / c));
+      if (dx <= tail) {
+        done = c > 1 && eg.have_pred && c == eg.c && dp <= s.eg_tol * (1.0 + pn);
+        eg.pred = P;
+        eg.c = c;
+        predicted = true;
+      }
+    }
+    eg.have_pred = predicted;
+    eg.dn_prev = dn;
+  }
+  eg.xa.assign(x, x + n);
+  eg.da.assign(dxds, dxds + n);
+  ++eg.samples;
+  return done;
+}
+
 struct PathResult {
   std::vector<cd> x;
   int status = 0;
@@ -324,11 +406,25 @@ PathResult track_one(const Problem& pr, const Settings& s, const cd* x0) {
   int consec = 0;
   bool failed = false;
 
+  // endgame: sample times 1 - s_k, s_k = s0 h^k (k < eg_samples), formed by
+  // repeated multiplication; the step control lands on each of them
+  Endgame eg;
+  eg.n = n;
+  eg.s_next = s.eg_s0;
+  bool eg_done = false;
+  while (s.endgame && eg.next < s.eg_samples && 1.0 - eg.s_next <= t) {
+    eg.s_next *= s.eg_ratio;
+    ++eg.next;
+  }
+  auto eg_active = [&]() { return s.endgame && eg.next < s.eg_samples; };
+
   while (t < 1.0) {
     if (r.accepted + r.rejected >= s.max_steps) { r.status = ST_FAIL_MAXSTEPS; failed = true; break; }
-    const bool last = dt >= 1.0 - t;
-    const double h = last ? 1.0 - t : dt;
-    const double t1 = last ? 1.0 : t + h;
+    const double target = eg_active() ? 1.0 - eg.s_next : 1.0;
+    const bool last = dt >= target - t;
+    const double h = last ? target - t : dt;
+    const double t1 = last ? target : t + h;
+    const bool landing = last && eg_active();
     bool conv = false;
     if (rk4(pr, r.x.data(), t, h, xp.data())) {
       for (int it = 0; it < s.max_newton; ++it) {
@@ -348,11 +444,41 @@ PathResult track_one(const Problem& pr, const Settings& s, const cd* x0) {
       ++r.accepted;
       if (++consec >= s.grow_after) { dt = std::min(2.0 * dt, s.dt_max); consec = 0; }
       if (norm_inf(n, r.x.data()) > s.r_inf) { r.status = ST_DIVERGED; failed = true; break; }
+      if (landing) {
+        // a sample: dx/ds = -dx/dt from the Davidenko equation at (x, t)
+        std::vector<cd> dxdt(n), dxds(n);
+        const double sk = eg.s_next;
+        eg.s_next *= s.eg_ratio;
+        ++eg.next;
+        if (davidenko(pr, r.x.data(), t, dxdt.data())) {
+          for (int i = 0; i < n; ++i) dxds[i] = -dxdt[i];
+          if (endgame_sample(eg, s, sk, r.x.data(), dxds.data())) { eg_done = true; break; }
+        }
+      }
     } else {
       ++r.rejected;
       consec = 0;
       dt *= 0.5;
-      if (dt < s.dt_min) { r.status = ST_FAIL_STEP; failed = true; break; }
+      if (dt < s.dt_min) {
+        // inside the endgame the last prediction stands in for the endpoint
+        if (s.endgame && eg.have_pred && eg.c > 1) { eg_done = true; break; }
+        r.status = ST_FAIL_STEP; failed = true; break;
+      }
+    }
+  }
+  if (eg_done) {
+    r.x = eg.pred;
+    t = 1.0;
+    if (eg.c > 1) {
+      // a root of multiplicity > 1: the prediction is the endpoint (a Newton
+      // step there divides rounding noise by rounding noise), singular by its
+      // cycle number; the backward error alone decides
+      r.t = t;
+      if (!all_finite(n, r.x.data())) { r.status = ST_FAIL_NAN; return r; }
+      if (norm_inf(n, r.x.data()) > s.r_inf) { r.status = ST_DIVERGED; return r; }
+      r.be = backward_error(pr, r.x.data());
+      r.status = (r.be <= s.finite_tol) ? ST_SINGULAR : ST_FAIL_REFINE;
+      return r;
     }
   }
   r.t = t;

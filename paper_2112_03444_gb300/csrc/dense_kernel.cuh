@@ -33,7 +33,8 @@ template <int N, int DEG, bool MIXED, int L>
 __global__ void __launch_bounds__(kBlock, 4) dense_td_kernel(const DenseArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Group g = make_group<L>();
-  const GroupMem sm = make_group_mem<L>(smem, DenseShape<N, DEG>::EXTRA);
+  const GroupMem sm =
+      make_group_mem<L>(smem, DenseShape<N, DEG>::EXTRA, 0, endgame_smem_bytes(L, MIXED));
   DenseProblem<N, DEG, L> prob{&a, sm, g.mask};
   run_tracker<N, L, MIXED>(prob, a.c, g, sm);
 }
@@ -43,7 +44,7 @@ template <int DEG, bool MIXED, int N, int LANES = 0>
 KernelRef dense_ref() {
   constexpr int L = LANES ? LANES : ((N <= 4) ? 4 : (N <= 8) ? 8 : (N <= 16) ? 16 : 32);
   return KernelRef{reinterpret_cast<const void*>(&dense_td_kernel<N, DEG, MIXED, L>), L,
-                   DenseShape<N, DEG>::EXTRA};
+                   DenseShape<N, DEG>::EXTRA, 0, endgame_smem_bytes(L, MIXED)};
 }
 
 }  // namespace hc

@@ -543,6 +543,12 @@ hc::DevSettings dev_settings(const hc_settings& s) {
   d.max_steps = s.max_steps;
   d.grow_after = s.grow_after;
   d.refine_iters = s.refine_iters;
+  d.endgame = s.endgame;
+  d.eg_cmax = s.eg_cmax;
+  d.eg_samples = s.eg_samples;
+  d.eg_s0 = s.eg_s0;
+  d.eg_ratio = s.eg_ratio;
+  d.eg_tol = s.eg_tol;
   return d;
 }
 
@@ -555,7 +561,11 @@ hc_status validate_settings(const hc_settings& s) {
       (s.precision != HC_PREC_FP64 && s.precision != HC_PREC_MIXED) ||
       (s.lanes != 0 && s.lanes != 32) || s.max_newton_ir < 1 || s.max_newton_ir > 32 ||
       (s.block_threads != 0 && s.block_threads != 32 && s.block_threads != 64 &&
-       s.block_threads != 128)) {
+       s.block_threads != 128) ||
+      (s.endgame != 0 && s.endgame != 1) || s.eg_reserved != 0 ||
+      (s.endgame && (!(s.eg_s0 > 0 && s.eg_s0 < 1) || !(s.eg_ratio > 0 && s.eg_ratio < 1) ||
+                     !(s.eg_tol > 0) || s.eg_cmax < 1 || s.eg_cmax > 16 || s.eg_samples < 1 ||
+                     s.eg_samples > 60))) {
     set_err("invalid settings");
     return HC_ERR_INVALID;
   }
@@ -899,7 +909,7 @@ hc_status launch_generic(const hc::KernelRef& k, void* args, size_t smem, int64_
 
 hc_status launch_tracker(const hc::KernelRef& k, const hc::DenseArgs& a, int64_t max_items,
                          cudaStream_t st, int threads = hc::kBlock) {
-  const size_t smem = (size_t)hc::block_smem_bytes(k.lanes, k.extra, 0, threads);
+  const size_t smem = (size_t)hc::block_smem_bytes(k.lanes, k.extra, 0, threads, k.eg_bytes);
   return launch_generic(k, (void*)&a, smem, max_items, st, threads);
 }
 
@@ -1038,6 +1048,13 @@ hc_settings hc_default_settings(void) {
   s.lanes = 0;
   s.max_newton_ir = 6;
   s.block_threads = 0;
+  s.endgame = 0;
+  s.eg_cmax = 8;
+  s.eg_samples = 40;
+  s.eg_reserved = 0;
+  s.eg_s0 = 0.1;
+  s.eg_ratio = 0.5;
+  s.eg_tol = 1e-8;
   return s;
 }
 
@@ -1488,7 +1505,7 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
     }
     const hc::KernelRef k = hc::term_kernel(n, mixed, mixed ? p->s.lanes : 0);
     auto smem_of = [&](const hc::KernelRef& kr, int threads = hc::kBlock) {
-      return (size_t)hc::block_smem_bytes(kr.lanes, p->extra, kr.acc_bytes, threads);
+      return (size_t)hc::block_smem_bytes(kr.lanes, p->extra, kr.acc_bytes, threads, kr.eg_bytes);
     };
     HC_CUDA(mark(ev.ek0, st));
     const int bth = std::max(main_threads(p->s), k.lanes);

@@ -18,13 +18,17 @@ constexpr int kBlock = 128;  // threads per block of the tracking kernels
 // The stride between groups is 16 bytes past a multiple of 128: the groups
 // of a warp reading their own broadcast word (a point entry, a monomial,
 // the pivot row) then hit different banks.
-__host__ __device__ constexpr int group_smem_bytes(int L, int extra, int acc = 0) {
-  return ((32 * (L + 2) + acc + (L + extra) * 16 + L * 16 + (L + extra) * 8 + 127) & ~127) + 16;
+// The all-FP64 kernels add eg bytes for the endgame's samples (three complex
+// doubles per lane: the previous sample, its dx/ds, the last prediction).
+__host__ __device__ constexpr int group_smem_bytes(int L, int extra, int acc = 0, int eg = 0) {
+  return ((32 * (L + 2) + acc + (L + extra) * 16 + L * 16 + (L + extra) * 8 + eg + 127) & ~127) +
+         16;
 }
+__host__ __device__ constexpr int endgame_smem_bytes(int L, bool mixed) { return mixed ? 0 : 48 * L; }
 // Dynamic shared memory of one tracking block of `threads` threads
 __host__ __device__ constexpr int block_smem_bytes(int L, int extra, int acc = 0,
-                                                   int threads = kBlock) {
-  return (threads / L) * group_smem_bytes(L, extra, acc);
+                                                   int threads = kBlock, int eg = 0) {
+  return (threads / L) * group_smem_bytes(L, extra, acc, eg);
 }
 // Threads per block of a launch: one warp for one-path-per-warp launches of
 // the re-tracking tiers (a hard path then holds only its own warp's
@@ -149,6 +153,7 @@ struct KernelRef {
   int lanes;        // lanes per path (L)
   int extra;        // per-group shared entries behind the point the kernel itself needs
   int acc_bytes;    // bytes of one evaluator accumulator (per lane and row entry), 0: none
+  int eg_bytes;     // per-group endgame sample bytes (all-FP64 kernels), 0: none
 };
 
 // Lanes per path chosen for n unknowns (one row per lane, groups are powers

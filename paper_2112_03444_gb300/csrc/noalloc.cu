@@ -297,7 +297,7 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
   NA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   auto launch = [&](const hc::KernelRef& k, const hc::DenseArgs& args, int64_t max_items,
                     int threads = hc::kBlock) {
-    const size_t smem = (size_t)hc::block_smem_bytes(k.lanes, k.extra, 0, threads);
+    const size_t smem = (size_t)hc::block_smem_bytes(k.lanes, k.extra, 0, threads, k.eg_bytes);
     int blocks = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k.fn, threads, smem) !=
         cudaSuccess)

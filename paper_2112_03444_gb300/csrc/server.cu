@@ -2,7 +2,8 @@
 //
 // Requests are single system instances queued per problem.  A dispatcher
 // thread owns n_streams CUDA streams; whenever a stream is free it takes the
-// problem whose oldest pending request has waited longest, packs up to
+// problem whose oldest pending request has waited longest (no problem holding
+// more than half the streams while others wait), packs up to
 // max_batch_instances of its pending requests into one batch (one persistent
 // launch), and enqueues it if the device memory of the in-flight batches
 // plus the new one stays within max_device_bytes.  Finished batches are
@@ -68,6 +69,7 @@ struct Slot {
   cudaStream_t stream = nullptr;
   bool busy = false;
   hc_batch* batch = nullptr;
+  hc_problem* problem = nullptr;
   std::vector<Request*> reqs;
   size_t bytes = 0;
   Pinned in, x, st, steps;
@@ -137,11 +139,22 @@ void dispatch(hc_server* s) {
         break;
       }
     if (!free_slot) return;
-    // the problem with the oldest waiting request
+    // The problem with the oldest waiting request -- but while other
+    // problems have requests waiting, none may hold more than half the
+    // streams: long batches of a hard problem (seconds of re-tracking tail)
+    // would otherwise take every stream and queue the quick ones behind them.
+    int waiting_problems = 0;
+    for (auto& kv : s->pending) waiting_problems += kv.second.empty() ? 0 : 1;
+    const int share = std::max(1, (int)s->slots.size() / 2);
     hc_problem* best = nullptr;
     Clock::time_point oldest;
     for (auto& kv : s->pending) {
       if (kv.second.empty()) continue;
+      if (waiting_problems > 1) {
+        int held = 0;
+        for (auto& sp : s->slots) held += (sp->busy && sp->problem == kv.first) ? 1 : 0;
+        if (held >= share) continue;
+      }
       const auto t = kv.second.front()->t_submit;
       if (!best || t < oldest) {
         best = kv.first;
@@ -206,6 +219,7 @@ void dispatch(hc_server* s) {
     }
     sl.busy = true;
     sl.batch = bt;
+    sl.problem = best;
     sl.reqs = std::move(take);
     sl.bytes = (size_t)(per * k);
     s->bytes_inflight += sl.bytes;

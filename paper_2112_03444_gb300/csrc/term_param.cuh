@@ -276,7 +276,8 @@ template <int N, bool MIXED, int L>
 __global__ void __launch_bounds__(kBlock) term_param_kernel(const __grid_constant__ TermArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Group g = make_group<L>();
-  const GroupMem sm = make_group_mem<L>(smem, a.extra, term_acc_bytes<N, MIXED, L>());
+  const GroupMem sm = make_group_mem<L>(smem, a.extra, term_acc_bytes<N, MIXED, L>(),
+                                        endgame_smem_bytes(L, MIXED));
   TermProblem<N, L, MIXED> prob{&a, g, sm};
   run_tracker<N, L, MIXED>(prob, a.c, g, sm);
 }
@@ -285,7 +286,7 @@ template <bool MIXED, int N, int LANES = 0>
 KernelRef term_ref() {
   constexpr int L = LANES ? LANES : ((N <= 4) ? 4 : (N <= 8) ? 8 : (N <= 16) ? 16 : 32);
   return KernelRef{reinterpret_cast<const void*>(&term_param_kernel<N, MIXED, L>), L, 0,
-                   term_acc_bytes<N, MIXED, L>()};
+                   term_acc_bytes<N, MIXED, L>(), endgame_smem_bytes(L, MIXED)};
 }
 
 }  // namespace hc

@@ -86,21 +86,44 @@ struct GroupMem {
   cx<double>* vd;
   cx<double>* sb;  // holds L values of cx<R>
   cx<float>* vf;
+  cx<double>* eg;  // all-FP64 kernels: endgame samples [3][L] (previous sample,
+                   // its dx/ds, the last prediction), 16-byte aligned
 };
 
 template <int L>
 __device__ __forceinline__ GroupMem make_group_mem(unsigned char* smem, int extra,
-                                                   int acc_bytes = 0) {
-  unsigned char* b = smem + (threadIdx.x / L) * group_smem_bytes(L, extra, acc_bytes);
+                                                   int acc_bytes = 0, int eg_bytes = 0) {
+  unsigned char* b = smem + (threadIdx.x / L) * group_smem_bytes(L, extra, acc_bytes, eg_bytes);
   GroupMem m;
   m.pv = b;
   b += 32 * (L + 2);
   m.acc = b;
   b += acc_bytes;
+  m.eg = reinterpret_cast<cx<double>*>(b);
+  b += eg_bytes;
   m.vd = reinterpret_cast<cx<double>*>(b);
   m.sb = reinterpret_cast<cx<double>*>(b + (L + extra) * 16);
   m.vf = reinterpret_cast<cx<float>*>(b + (L + extra) * 16 + L * 16);
   return m;
+}
+
+// max over the group of a double (butterfly over the group's L lanes)
+template <int L>
+__device__ __forceinline__ double gmaxd(const Group& g, double v) {
+#pragma unroll
+  for (int o = L / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(g.mask, v, o));
+  return v;
+}
+
+// Value at w = 0 of the cubic Hermite interpolant through (wb, xb, Db) and
+// (wa, xa, Da), wb < wa (the power-series endgame's prediction).
+__device__ __forceinline__ cx<double> hermite_at_zero(double wb, cx<double> xb, cx<double> Db,
+                                                      double wa, cx<double> xa, cx<double> Da) {
+  const double dl = wa - wb, tau = -wb / dl;
+  const double t2 = tau * tau, t3 = t2 * tau;
+  const double h00 = 2 * t3 - 3 * t2 + 1, h10 = t3 - 2 * t2 + tau;
+  const double h01 = -2 * t3 + 3 * t2, h11 = t3 - t2;
+  return h00 * xb + (h10 * dl) * Db + h01 * xa + (h11 * dl) * Da;
 }
 
 // Persistent loop of one lane group over the work items of a launch.
@@ -149,6 +172,17 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
   // arithmetic until the path's first rejected FP64-state step, then in FP64
   bool res64 = false;
   float cond_inorm = 0.f, cond_anorm = 0.f, be = 0.f;
+  // Power-series endgame (all-FP64 kernels, settings.endgame): the index and
+  // s = 1 - t of the next sample, the s of the sample awaiting its dx/ds, the
+  // samples taken, the cycle number of the last prediction, the previous
+  // sample difference; landing: the current step ends on a sample; pending:
+  // the point is a sample whose derivative the next RK stage 1 gives; have:
+  // a prediction stands; sing: the endpoint came from a prediction with c > 1.
+  int eg_next = 0, eg_count = 0, eg_c = 1;
+  double eg_s = 0.0, eg_s_sample = 0.0, eg_dnprev = 0.0;
+  bool eg_landing = false, eg_pending = false, eg_have = false, eg_sing = false;
+  const bool eg_on = !MIXED && s.endgame != 0;
+  auto eg_active = [&]() { return eg_on && eg_next < s.eg_samples; };
 
   cx<R> row[N + 1];
   cx<R> x[N];
@@ -167,9 +201,13 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
   };
   auto begin_step = [&]() {
     if (HI()) {
-      const bool last = dt >= 1.0 - t;
-      h = last ? 1.0 - t : dt;
-      t1 = last ? 1.0 : t + h;
+      // with the endgame the step ends at the next sample time at the latest
+      const bool ega = eg_active();
+      const double target = ega ? 1.0 - eg_s : 1.0;
+      const bool last = dt >= target - t;
+      h = last ? target - t : dt;
+      t1 = last ? target : t + h;
+      eg_landing = last && ega;
     } else {
       // a step ending within FP32 rounding of the phase end takes the rest
       const bool last = 1.0001f * dtf >= tAf - tf;
@@ -195,6 +233,63 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
     mode = M_REFINE;
     it = 0;
   };
+  // the endgame's prediction (cycle number > 1) as the endpoint: no Newton
+  // step (at a multiple root it divides rounding noise by rounding noise),
+  // the backward error alone decides
+  auto eg_finish = [&]() {
+    xd = (g.gl < N) ? sm.eg[2 * L + g.gl] : czero<double>();
+    t = 1.0;
+    enter_refine();
+    eg_sing = true;
+  };
+  // A sample at s = eg_s_sample: the point xd and dx/ds = -dxdt.  A
+  // prediction is made only while the samples converge (the difference to
+  // the previous sample shrinks, and the prediction lies within the tail
+  // 4 |x_k - x_(k-1)| / (1 - h^(1/c)) of the sample); true once two successive
+  // predictions with the same cycle number c > 1 agree within eg_tol (1 + |x|)
+  // (paths with c = 1 end at nonsingular roots that ordinary tracking
+  // reaches; a refinement from a misjudged c = 1 prediction next to a
+  // multiple root could land anywhere).
+  auto eg_sample = [&](cx<double> dxdt) -> bool {
+    cx<double>* xa = sm.eg;
+    cx<double>* da = sm.eg + L;
+    cx<double>* pr = sm.eg + 2 * L;
+    const cx<double> xk = act ? xd : czero<double>();
+    const cx<double> dk = act ? -dxdt : czero<double>();
+    bool done = false;
+    if (eg_count >= 1) {
+      const double dn = gmaxd<L>(g, act ? cabs2(xk - xa[g.gl]) : 0.0);
+      bool predicted = false;
+      if (eg_count >= 2 && dn > 0.0 && eg_dnprev > 0.0 && dn < eg_dnprev) {
+        const double r = log(s.eg_ratio) / log(dn / eg_dnprev);
+        const int cc = min(max((int)lround(r), 1), s.eg_cmax);
+        const double sk = eg_s_sample, sa = sk / s.eg_ratio;
+        const double wb = pow(sk, 1.0 / cc), wa = pow(sa, 1.0 / cc);
+        const double fb = (double)cc * pow(wb, cc - 1), fa = (double)cc * pow(wa, cc - 1);
+        const cx<double> P =
+            act ? hermite_at_zero(wb, xk, fb * dk, wa, xa[g.gl], fa * da[g.gl]) : czero<double>();
+        const double pn = gmaxd<L>(g, act ? cabs2(P) : 0.0);
+        const double dx = gmaxd<L>(g, act ? cabs2(P - xk) : 0.0);
+        const double dp = gmaxd<L>(g, (act && eg_have) ? cabs2(P - pr[g.gl]) : 0.0);
+        const double tail = 4.0 * dn / (1.0 - pow(s.eg_ratio, 1.0 / cc));
+        if (dx <= tail) {
+          done = cc > 1 && eg_have && cc == eg_c && dp <= s.eg_tol * (1.0 + pn);
+          if (act) pr[g.gl] = P;
+          eg_c = cc;
+          predicted = true;
+        }
+      }
+      eg_have = predicted;
+      eg_dnprev = dn;
+    }
+    if (act) {
+      xa[g.gl] = xk;
+      da[g.gl] = dk;
+    }
+    ++eg_count;
+    __syncwarp(g.mask);
+    return done;
+  };
   auto reject = [&]() {
     ++nrej;
     consec = 0;
@@ -202,8 +297,12 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
       res64 = true;
       dt *= 0.5;
       if (dt < s.dt_min) {
-        status = ST_FAIL_STEP;
-        mode = M_DONE;
+        if (eg_on && eg_have && eg_c > 1) {  // inside the endgame the last prediction stands in
+          eg_finish();
+        } else {
+          status = ST_FAIL_STEP;
+          mode = M_DONE;
+        }
       } else {
         begin_step();
       }
@@ -327,6 +426,18 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
       consec = nacc = nrej = nnewt = status = 0;
       res64 = false;
       be = 0.f;
+      // endgame: the first sample time after the start point
+      eg_count = 0;
+      eg_c = 1;
+      eg_dnprev = 0.0;
+      eg_landing = eg_pending = eg_have = eg_sing = false;
+      eg_next = 0;
+      eg_s = s.eg_s0;
+      if (eg_on)
+        while (eg_next < s.eg_samples && 1.0 - eg_s <= t) {
+          eg_s *= s.eg_ratio;
+          ++eg_next;
+        }
       if (t >= 1.0)
         enter_refine();
       else
@@ -436,6 +547,16 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
 
     // ---- 3. state machine
     if (mode == M_RK) {
+      if constexpr (!MIXED) {
+        // stage 1 at a sample point gives its dx/dt
+        if (stage == 0 && eg_pending) {
+          eg_pending = false;
+          if (sok && eg_sample(d)) {
+            eg_finish();
+            continue;
+          }
+        }
+      }
       step_ok = step_ok && sok;
       kprev = d;
       ksum = ksum + ((stage == 0 || stage == 3) ? R(1) : R(2)) * d;
@@ -489,6 +610,12 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
           enter_refine();
         } else {
           if (!HI() && tf >= tAf) promote((double)dtf);  // enter the FP64-state phase
+          if (eg_on && eg_landing) {  // the step ended on a sample time
+            eg_pending = true;
+            eg_s_sample = eg_s;
+            eg_s *= s.eg_ratio;
+            ++eg_next;
+          }
           begin_step();
         }
       } else if (bad || ++it >= ((MIXED && HI()) ? s.max_newton_ir : s.max_newton)) {
@@ -499,8 +626,8 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
       const float dn = sqrt_approx(gmaxf(g, act ? (float)cnorm2(d) : 0.f));
       const float xnn = sqrt_approx(gmaxf(g, act ? cnorm2(cvt<float>(xnew)) : 0.f));
       const bool bad = !sok || !(dn <= 3.0e38f) || !(xnn <= 3.0e38f);
-      if (!bad) xd = xnew;
-      if (bad || dn <= (float)s.refine_tol * (1.f + xnn) || ++it >= s.refine_iters) {
+      if (!bad && !eg_sing) xd = xnew;
+      if (bad || eg_sing || dn <= (float)s.refine_tol * (1.f + xnn) || ++it >= s.refine_iters) {
         // classify: finiteness, divergence, backward error (FP64 residual)
         const bool fin = !gany(g, act && !cfinite(xd));
         const float xnf = gmaxf(g, act ? cabs2(cvt<float>(xd)) : 0.f);
@@ -522,6 +649,9 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
           be = gmaxf(g, (float)bei);
           if (!((double)be <= s.finite_tol)) {
             status = ST_FAIL_REFINE;
+            mode = M_DONE;
+          } else if (eg_sing) {  // cycle number > 1: a singular root
+            status = ST_SINGULAR;
             mode = M_DONE;
           } else {
             mode = M_COND;  // condition number: one solve per column of the inverse

@@ -47,7 +47,10 @@ class hc_settings(ctypes.Structure):
                 ("grow_after", ctypes.c_int32), ("refine_iters", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("escalate", ctypes.c_int32),
                 ("lanes", ctypes.c_int32), ("max_newton_ir", ctypes.c_int32),
-                ("block_threads", ctypes.c_int32)]
+                ("block_threads", ctypes.c_int32), ("endgame", ctypes.c_int32),
+                ("eg_cmax", ctypes.c_int32), ("eg_samples", ctypes.c_int32),
+                ("eg_reserved", ctypes.c_int32), ("eg_s0", ctypes.c_double),
+                ("eg_ratio", ctypes.c_double), ("eg_tol", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -357,3 +357,36 @@ def test_path_to_infinity_is_diverged_like_the_oracle(hc, precision):
     ref = OracleProblem(fam, kind=KIND_PARAMETER, p0=p0, p1=p1).track(start=start)
     assert ref["status"][0] == oracle.DIVERGED
     assert b.status[0][0] == ref["status"][0]
+
+
+ENDGAME_CASES = {
+    "triple_root": (2, [{(3, 0): 1.0, (2, 0): -3.0, (1, 0): 3.0, (0, 0): -1.0},
+                        {(0, 1): 1.0, (0, 0): -1.0}], 4),
+    "double_root": (2, [{(2, 0): 1.0, (1, 0): -2.0, (0, 0): 1.0}, {(0, 1): 1.0, (0, 0): -1.0}], 3),
+    "deficient": EDGE_CASES["deficient"],
+    "decoupled_real_squares": EDGE_CASES["decoupled_real_squares"],
+}
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("case", sorted(ENDGAME_CASES))
+def test_endgame_matches_oracle(hc, case, precision):
+    """The power-series endgame (settings.endgame = 1) against the oracle's
+    own endgame: statuses path by path (singular endpoints of multiple roots
+    included) and the finite and singular endpoints within 1e-8.  In mixed
+    precision the endgame runs in the all-FP64 re-tracking tier, which gets
+    the paths that fail near their end."""
+    from paper_2112_03444_gb300 import inputs
+    n, polys, gseed = ENDGAME_CASES[case]
+    fam, p0, p1, start = inputs.total_degree_as_parameter_family(_poly(n, polys),
+                                                                 inputs.unit_gamma(gseed))
+    pr = hc.Problem(fam, kind=hc.HC_PARAMETER, p0=p0, start=start,
+                    settings=dict(precision=precision, endgame=1))
+    b = pr.track(n_instances=1, p1=p1[None, :]).wait()
+    ref = OracleProblem(fam, kind=KIND_PARAMETER, p0=p0, p1=p1).track(
+        start=start, settings=dict(endgame=1))
+    assert np.array_equal(b.status[0] & 0x7F, ref["status"] & 0x7F), (b.status[0], ref["status"])
+    for cls in (oracle.FINITE, oracle.SINGULAR):
+        m = (ref["status"] & 0x7F) == cls
+        if m.any():
+            assert np.max(rel_dist(b.x[0][m], ref["x"][m])) <= TOL, cls

@@ -467,3 +467,51 @@ def test_coefficient_interpolation_equals_parameter_homotopy_when_linear():
     b = OracleProblem(sys_, kind=oracle.KIND_COEFFICIENT, p0=p0, p1=p1).track(start=start)
     assert np.array_equal(a["status"], b["status"])
     assert np.array_equal(a["x"], b["x"])
+
+
+# ---------------------------------------------------------------- power-series endgame
+def _triple_root_system():
+    """(x1 - 1)^3 = 0, x2 = 1: one root (1, 1) of multiplicity 3, reached by
+    all three total-degree paths with cycle number 3."""
+    return poly_system(2, [{(3, 0): 1.0, (2, 0): -3.0, (1, 0): 3.0, (0, 0): -1.0},
+                           {(0, 1): 1.0, (0, 0): -1.0}])
+
+
+def test_endgame_finds_the_multiple_root():
+    """Closed form: every path of the triple root ends within 1e-8 of (1, 1);
+    those the endgame finishes are classified singular (cycle number 3 > 1),
+    where without it the same paths fail by step-size underflow."""
+    sys_ = _triple_root_system()
+    off = OracleProblem(sys_, gamma=inputs.unit_gamma(4)).track()
+    on = OracleProblem(sys_, gamma=inputs.unit_gamma(4)).track(settings=dict(endgame=1))
+    assert np.all((off["status"] & 0x7F) == oracle.FAIL_STEP)
+    sing = (on["status"] & 0x7F) == oracle.SINGULAR
+    assert sing.sum() >= 2
+    assert np.max(np.abs(on["x"][sing] - np.array([1.0, 1.0]))) < 1e-8
+    assert np.all(on["be"][sing] <= 1e-10)
+    steps_on = on["counts"][sing, :2].sum()
+    steps_off = off["counts"][sing, :2].sum()
+    assert steps_on < steps_off
+
+
+@pytest.mark.parametrize("seed", [5, 6, 7])
+def test_endgame_leaves_nonsingular_endpoints_alone(seed):
+    """Dense random systems (all roots simple): the endgame's predictions
+    converge with cycle number 1, and refinement gives the same statuses and
+    endpoints as without it."""
+    sys_ = inputs.dense_system(4, 2, seed)
+    a = OracleProblem(sys_, gamma=inputs.unit_gamma(seed)).track()
+    b = OracleProblem(sys_, gamma=inputs.unit_gamma(seed)).track(settings=dict(endgame=1))
+    assert np.array_equal(a["status"], b["status"])
+    ok, msg = same_set(a["x"], b["x"], 1e-10)
+    assert ok, msg
+
+
+def test_endgame_makes_no_prediction_for_paths_to_infinity():
+    """x1 x2 = 1, x1 x2 + x1 = 2: one finite root (1, 1).  Paths to infinity
+    have growing sample differences, so the endgame predicts nothing for
+    them: no path other than the one to (1, 1) ends finite (a prediction
+    refined onto (1, 1) would be a path jump)."""
+    sys_ = poly_system(2, [{(1, 1): 1, (0, 0): -1}, {(1, 1): 1, (1, 0): 1, (0, 0): -2}])
+    r = OracleProblem(sys_, gamma=inputs.unit_gamma(9)).track(settings=dict(endgame=1))
+    assert oracle.status_counts(r["status"])["finite"] == 1
