@@ -63,12 +63,21 @@ enum {
 /* Tracking precision (hc_settings.precision). */
 enum {
   HC_PREC_FP64 = 0,   /* every step in complex FP64 (the plain reference form)         */
-  HC_PREC_MIXED = 1   /* complex FP32 predictor and corrector; FP64 state x in the
+  HC_PREC_MIXED = 1,  /* complex FP32 predictor and corrector; FP64 state x in the
                          endgame (t > t_endgame) with double-float corrector
                          residuals (FP64 after a rejected step there), FP64
                          residuals in the final Newton refinement; colliding
                          endpoints (path jumps) and failed paths re-tracked with
-                         high-precision residuals, then in FP64                  */
+                         high-precision residuals, then in the precision
+                         retrack_precision names                               */
+  HC_PREC_DF = 2      /* FP64 state, time and step control as HC_PREC_FP64; the
+                         evaluation of H, Hx, Ht and the solve in complex
+                         double-float arithmetic (pairs of FP32 numbers, about
+                         48 significant bits, FP32's exponent range) on the
+                         FP32 pipe; the corrector's residual from that
+                         evaluation until a step of the path is rejected, in
+                         FP64 after; FP64 refinement residuals and backward
+                         error.  Dense systems track one path per warp.       */
 };
 
 /* Per-path status codes (hc_batch_desc.status_out).  HC_PATH_REAL is or-ed
@@ -147,13 +156,20 @@ typedef struct hc_settings {
    * Two agreeing predictions with c > 1 end the path at the prediction,
    * HC_PATH_SINGULAR if its backward error passes; a step-size failure inside
    * the endgame takes the last such prediction.  Paths with c = 1 (nonsingular
-   * endpoints) are tracked to t = 1 as without the endgame.  It runs in the all-FP64 kernel (precision FP64, and the
-   * all-FP64 re-tracking tier of the mixed pipeline, which receives the
-   * paths that fail near their end).                                        */
+   * endpoints) are tracked to t = 1 as without the endgame.  It runs in the
+   * FP64-state kernels (precisions FP64 and DF, and the last re-tracking tier
+   * of the mixed pipeline, which receives the paths that fail near their end). */
   int32_t endgame;        /* 0: off, 1: power-series endgame */
   int32_t eg_cmax;        /* 8 */
   int32_t eg_samples;     /* 40 */
-  int32_t eg_reserved;    /* 0 */
+  int32_t retrack_precision; /* precision of the last re-tracking tier of the mixed
+                             pipeline: HC_PREC_DF (the default; GB300 issues FP64
+                             at a small fraction of its FP32 rate) or
+                             HC_PREC_FP64.  With the endgame on, that tier runs
+                             in FP64 whatever this says: the endgame's
+                             extrapolation uses dx/ds at its samples, which a
+                             double-float solve near a multiple root gives
+                             with about five bits less                       */
   double eg_s0;           /* 0.1 */
   double eg_ratio;        /* 0.5 */
   double eg_tol;          /* agreement of two predictions, relative: 1e-8 */
@@ -300,6 +316,29 @@ typedef struct hc_problem_info {
 } hc_problem_info;
 
 hc_status hc_problem_query(const hc_problem* p, hc_problem_info* out);
+
+/*
+ * Sec. 6 ("Parallel Evaluations of the Jacobian and Vectors": dH/dx, dH/dt
+ * and H evaluated together from the terms of the equations) and Sec. 3 (H):
+ * evaluate the problem's homotopy at n_points points with the tracker's own
+ * device evaluator, in FP64 (HC_PREC_FP64), FP32 (HC_PREC_MIXED) or
+ * double-float (HC_PREC_DF) arithmetic.
+ *   inputs   host, the instances' data as in hc_batch_desc: total degree
+ *            coef [n_instances][T] complex (NULL: the problem's own
+ *            coefficients), parameter and coefficient-interpolation
+ *            homotopies p1 [n_instances][n_params] complex (required)
+ *   instance host [n_points], each in [0, n_instances)
+ *   x        host [n_points][n] complex; t host [n_points]
+ *   H, Ht    host out [n_points][n] complex; Hx host out [n_points][n][n]
+ *            complex, row-major (Hx[k][i][j] = dH_i/dx_j at point k)
+ * Synchronous; allocates its device buffers per call on the problem's
+ * device.  Returns HC_ERR_INVALID for bad arguments or an out-of-range
+ * instance index, HC_ERR_UNSUPPORTED for a shape without an evaluation
+ * kernel, HC_ERR_OOM / HC_ERR_CUDA for device failures.
+ */
+hc_status hc_evaluate(const hc_problem* p, int32_t precision, int32_t n_instances,
+                      const double* inputs, int64_t n_points, const int64_t* instance,
+                      const double* x, const double* t, double* H, double* Hx, double* Ht);
 
 /*
  * Sec. 3 (predictor-corrector tracking of every start path from t = 0 to

@@ -27,6 +27,8 @@
 //      kernels.cuh); slice N pair 0 holds the constant c_i0.
 //   E: [M][L] complex double, nested Horner order; Edf the same entries as
 //      double-floats (16 bytes each: hi re, hi im, lo re, lo im).
+//   Ddf: D as complex double-floats (cx<df>: re hi, re lo, im hi, im lo), the
+//      table of the double-float kernels, which evaluate with R = df.
 #pragma once
 
 #include <type_traits>
@@ -64,6 +66,7 @@ struct DenseTD {
   static constexpr int L = (N <= 4) ? 4 : (N <= 8) ? 8 : (N <= 16) ? 16 : 32;
   const cx<float>* D32;
   const cx<double>* D64;
+  const cx<df>* Ddf;
   const cx<double>* E;
   const cdf* Edf;
   cx<double> gamma;
@@ -71,6 +74,7 @@ struct DenseTD {
   cdf gammadf;
   cx<float>* Vf;   // the group's shared copies of the evaluation point (+ monomials)
   cx<double>* Vd;
+  cx<df>* Vx;      // double-float kernels: the point as double-floats (+ monomials)
   unsigned gmask;  // lanes of the group
 
   template <class R>
@@ -79,6 +83,8 @@ struct DenseTD {
   __device__ __forceinline__ cx<R>* vptr() const {
     if constexpr (std::is_same<R, float>::value)
       return Vf;
+    else if constexpr (std::is_same<R, df>::value)
+      return Vx;
     else
       return Vd;
   }
@@ -98,8 +104,13 @@ struct DenseTD {
     if constexpr (PARTS > 1) {
 #pragma unroll
       for (int o = L; o < L * PARTS; o <<= 1) {
-        v.re += __shfl_xor_sync(0xffffffffu, v.re, o);
-        v.im += __shfl_xor_sync(0xffffffffu, v.im, o);
+        if constexpr (std::is_same<R, df>::value) {
+          v.re = v.re + shfl_xor_df(v.re, o);
+          v.im = v.im + shfl_xor_df(v.im, o);
+        } else {
+          v.re += __shfl_xor_sync(0xffffffffu, v.re, o);
+          v.im += __shfl_xor_sync(0xffffffffu, v.im, o);
+        }
       }
     }
     return v;
@@ -141,6 +152,11 @@ struct DenseTD {
     auto pair = [&](int j, int q) { return D + ((int64_t)(j * (S::MPP / 2) + q) * L + rr) * 2; };
     cx<R>* V = vptr<R>();
     cx<R>* Q = V + L_GROUP;
+    if constexpr (std::is_same<R, df>::value) {
+      // the tracker keeps the point in FP64 (Vd): split it once per evaluation
+      if (i < N) V[i] = to_cxdf(Vd[i]);
+      __syncwarp(gmask);
+    }
     if constexpr (DEG == 3) {
       // x_k x_l for k <= l in graded order, the group's lanes sharing the work
 #pragma unroll 1
@@ -184,7 +200,7 @@ struct DenseTD {
       cx<R> a2[N];
 #pragma unroll
       for (int j = 0; j < N; ++j) a2[j] = czero<R>();
-#pragma unroll 2
+#pragma unroll 1
       for (int q = part; q < S::NQ2 / 2; q += PARTS) {
         cx<R> m0, m1;
         ld2(Q + 2 * q, m0, m1);
@@ -227,6 +243,8 @@ struct DenseTD {
     cx<R> gm;
     if constexpr (std::is_same<R, float>::value)
       gm = gamma32;
+    else if constexpr (std::is_same<R, df>::value)
+      gm = to_cxdf(gammadf);
     else
       gm = gamma;
     const cx<R> gG = gm * G;
@@ -416,10 +434,12 @@ struct DenseTD {
       if constexpr (N & 1) {
         Vf[N] = czero<float>();
         Vd[N] = czero<double>();
+        if (Vx) Vx[N] = czero<df>();
       }
       if constexpr (DEG == 3 && (S::NQ & 1)) {
         Vf[L_GROUP + S::NQ] = czero<float>();
         Vd[L_GROUP + S::NQ] = czero<double>();
+        if (Vx) Vx[L_GROUP + S::NQ] = czero<df>();
       }
     }
   }
@@ -440,6 +460,8 @@ template <class R>
 __device__ __forceinline__ const cx<R>* DenseTD<N, DEG, LG>::dptr() const {
   if constexpr (std::is_same<R, float>::value)
     return D32;
+  else if constexpr (std::is_same<R, df>::value)
+    return Ddf;
   else
     return D64;
 }

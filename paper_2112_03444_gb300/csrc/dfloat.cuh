@@ -29,8 +29,20 @@
 
 namespace hc {
 
+// Besides the explicit functions below, df is an arithmetic type (the
+// operators and overloads at the end of this file), so that the evaluators
+// and the dense solve -- templates on their real type R -- run in
+// double-floats with R = df: the kernels of the double-float precision
+// (HC_PREC_DF) and of the last re-tracking tier of the mixed pipeline.
 struct df {
   float hi, lo;
+  df() = default;
+  __host__ __device__ constexpr df(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ constexpr explicit df(int v) : hi((float)v), lo(0.f) {}
+  // nearest double-float to v (hi carries the leading 24 bits)
+  __host__ __device__ explicit df(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
+  __host__ __device__ explicit operator float() const { return hi + lo; }
+  __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
 };
 
 // s + e = a + b exactly (six operations, no precondition)
@@ -129,5 +141,78 @@ inline cdf split_cdf_host(double re, double im) {
 
 // |z| from the high parts (scales and tests need FP32 accuracy only)
 __device__ __forceinline__ float cdf_abs_hi(cdf z) { return sqrtf(fmaf(z.hr, z.hr, z.hi_ * z.hi_)); }
+
+// ---------------------------------------------------------------- df as R
+// Real operations.  Sums: df_add (TwoSum of the high parts, the low parts
+// added, renormalised).  Products: x y with the exact TwoProd of the high
+// parts plus the cross terms.  Both are accurate to a small multiple of
+// u^2 = 2^-48 relative to the operands' magnitudes.
+__device__ __forceinline__ df operator+(df a, df b) { return df_add(a, b); }
+__device__ __forceinline__ df operator-(df a) { return df{-a.hi, -a.lo}; }
+__device__ __forceinline__ df operator-(df a, df b) { return df_add(a, df{-b.hi, -b.lo}); }
+__device__ __forceinline__ df operator*(df a, df b) {
+  float p, e;
+  two_prod(a.hi, b.hi, p, e);
+  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+  df r;
+  two_sum(p, e, r.hi, r.lo);
+  return r;
+}
+
+// x1 y1 + x2 y2 (df_dot2 without the addend)
+__device__ __forceinline__ df df_sdot2(df x1, df y1, df x2, df y2) {
+  float p1, e1, p2, e2;
+  two_prod(x1.hi, y1.hi, p1, e1);
+  two_prod(x2.hi, y2.hi, p2, e2);
+  float l = __fmaf_rn(x1.hi, y1.lo, __fmaf_rn(x1.lo, y1.hi, e1));
+  l = __fadd_rn(l, __fmaf_rn(x2.hi, y2.lo, __fmaf_rn(x2.lo, y2.hi, e2)));
+  float s, es;
+  two_sum(p1, p2, s, es);
+  df r;
+  two_sum(s, __fadd_rn(l, es), r.hi, r.lo);
+  return r;
+}
+
+// 1 / d: one Newton step r = r0 + r0 (1 - d r0) from the FP32 reciprocal
+// r0 of the high part; the residual 1 - d r0 is formed with df_dot2, which
+// keeps it exact to u^2 while it cancels (accuracy about u^2 relative).
+__device__ __forceinline__ df df_recip(df d) {
+  const float r0 = __frcp_rn(d.hi);
+  const df one{1.f, 0.f}, z{0.f, 0.f};
+  const df e = df_dot2(one, df{-d.hi, -d.lo}, df{r0, 0.f}, z, z);
+  return df_add(df{r0, 0.f}, df{r0, 0.f} * e);
+}
+
+// Complex operations on cx<df> (overloads of the templates in
+// hc_device.cuh; a complex product is two two-term dot products).
+__device__ __forceinline__ cx<df> operator*(cx<df> a, cx<df> b) {
+  return {df_sdot2(a.re, b.re, -a.im, b.im), df_sdot2(a.re, b.im, a.im, b.re)};
+}
+__device__ __forceinline__ cx<df> cfma(cx<df> a, cx<df> b, cx<df> acc) {
+  return {df_dot2(acc.re, a.re, b.re, -a.im, b.im), df_dot2(acc.im, a.re, b.im, a.im, b.re)};
+}
+__device__ __forceinline__ cx<df> cfms(cx<df> a, cx<df> b, cx<df> acc) {
+  return {df_dot2(acc.re, -a.re, b.re, a.im, b.im), df_dot2(acc.im, -a.re, b.im, -a.im, b.re)};
+}
+// 1/z = conj(z) / |z|^2 (|z| must stay inside FP32's range, as for the
+// FP32 solve: a pivot outside it gives a non-finite reciprocal and the step
+// is rejected)
+__device__ __forceinline__ cx<df> crecip(cx<df> z) {
+  const df inv = df_recip(df_sdot2(z.re, z.re, z.im, z.im));
+  return {z.re * inv, -(z.im * inv)};
+}
+// magnitudes for pivot choice and tests: FP32 accuracy from the high parts
+__device__ __forceinline__ float cabs1(cx<df> z) { return fabsf(z.re.hi) + fabsf(z.im.hi); }
+__device__ __forceinline__ float cnorm2(cx<df> z) {
+  return fmaf(z.re.hi, z.re.hi, z.im.hi * z.im.hi);
+}
+__device__ __forceinline__ float cabs2(cx<df> z) { return sqrtf(cnorm2(z)); }
+// complex double <-> complex double-float
+__device__ __forceinline__ cx<df> to_cxdf(cx<double> z) { return {df(z.re), df(z.im)}; }
+__device__ __forceinline__ cx<df> to_cxdf(cdf z) { return {z.re(), z.im()}; }
+// butterfly sum over the lanes xor o (o = L .. L * PARTS / 2) of a warp
+__device__ __forceinline__ df shfl_xor_df(df v, int o) {
+  return df{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+}
 
 }  // namespace hc

@@ -26,14 +26,27 @@ KernelRef dense_ref_d2_32(int n, int lanes);
 KernelRef dense_ref_d3_64(int n, int lanes);
 KernelRef dense_ref_d3_32(int n, int lanes);
 
+KernelRef dense_ref_d2_df(int n);
+KernelRef dense_ref_d3_df(int n);
+
 KernelRef term_ref_64(int n, int lanes);
 KernelRef term_ref_32(int n, int lanes);
+KernelRef term_ref_df(int n);
 
-KernelRef term_kernel(int n, bool mixed, int lanes) {
-  return mixed ? term_ref_32(n, lanes) : term_ref_64(n, lanes);
+// The double-float kernels come in one width each: one path per warp for
+// dense systems, the default width for term tables.
+KernelRef term_kernel(int n, int prec, int lanes) {
+  if (prec == HC_PREC_DF) return term_ref_df(n);
+  return prec == HC_PREC_MIXED ? term_ref_32(n, lanes) : term_ref_64(n, lanes);
 }
 
-KernelRef dense_kernel(int deg, int n, bool mixed, int lanes) {
+KernelRef dense_kernel(int deg, int n, int prec, int lanes) {
+  const bool mixed = prec == HC_PREC_MIXED;
+  if (prec == HC_PREC_DF) {
+    if (deg == 2) return dense_ref_d2_df(n);
+    if (deg == 3) return dense_ref_d3_df(n);
+    return KernelRef{nullptr, 0};
+  }
   if (deg == 2) return mixed ? dense_ref_d2_32(n, lanes) : dense_ref_d2_64(n, lanes);
   if (deg == 3) return mixed ? dense_ref_d3_32(n, lanes) : dense_ref_d3_64(n, lanes);
   return KernelRef{nullptr, 0};
@@ -65,7 +78,8 @@ __global__ void stage_dense_kernel(int64_t n_inst, int T, const double2* __restr
                                    int64_t coef_stride, const int* __restrict__ emap, int ndc,
                                    const int* __restrict__ dterm, const int* __restrict__ dslot,
                                    const float* __restrict__ dmult, double2* E, hc::cdf* Edf,
-                                   int64_t Es, float2* D32, double2* D64, int64_t Ds) {
+                                   int64_t Es, float2* D32, double2* D64, float4* Ddf,
+                                   int64_t Ds) {
   const int64_t per = (int64_t)T + ndc;
   const int64_t total = n_inst * per;
   for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < total;
@@ -83,6 +97,10 @@ __global__ void stage_dense_kernel(int64_t n_inst, int T, const double2* __restr
       const double2 dv = make_double2(m * v.x, m * v.y);
       if (D64) D64[inst * Ds + dslot[r]] = dv;
       if (D32) D32[inst * Ds + dslot[r]] = make_float2((float)dv.x, (float)dv.y);
+      if (Ddf) {  // cx<df> layout: re hi, re lo, im hi, im lo
+        const hc::df re(dv.x), im(dv.y);
+        Ddf[inst * Ds + dslot[r]] = make_float4(re.hi, re.lo, im.hi, im.lo);
+      }
     }
   }
 }
@@ -558,11 +576,13 @@ hc_status validate_settings(const hc_settings& s) {
       s.grow_after < 1 || s.refine_iters < 0 || s.refine_iters > 64 || !(s.newton_tol > 0) ||
       !(s.newton_tol_fp32 > 0) || !(s.max_first_corr > 0) || !(s.r_inf > 0) ||
       !(s.dt_min_fp32 >= s.dt_min) || !(s.max_first_corr_fp32 > 0) || s.max_steps_fp32 < 1 ||
-      (s.precision != HC_PREC_FP64 && s.precision != HC_PREC_MIXED) ||
+      (s.precision != HC_PREC_FP64 && s.precision != HC_PREC_MIXED &&
+       s.precision != HC_PREC_DF) ||
+      (s.retrack_precision != HC_PREC_FP64 && s.retrack_precision != HC_PREC_DF) ||
       (s.lanes != 0 && s.lanes != 32) || s.max_newton_ir < 1 || s.max_newton_ir > 32 ||
       (s.block_threads != 0 && s.block_threads != 32 && s.block_threads != 64 &&
        s.block_threads != 128) ||
-      (s.endgame != 0 && s.endgame != 1) || s.eg_reserved != 0 ||
+      (s.endgame != 0 && s.endgame != 1) ||
       (s.endgame && (!(s.eg_s0 > 0 && s.eg_s0 < 1) || !(s.eg_ratio > 0 && s.eg_ratio < 1) ||
                      !(s.eg_tol > 0) || s.eg_cmax < 1 || s.eg_cmax > 16 || s.eg_samples < 1 ||
                      s.eg_samples > 60))) {
@@ -892,6 +912,14 @@ Occ occupancy(const void* fn, size_t smem, int threads) {
   return o;
 }
 
+// Largest dynamic shared memory a block may opt in to on the current device.
+size_t max_block_smem() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return (size_t)v;
+}
+
 // Persistent launch: grid = resident blocks per SM x SMs, or fewer when the
 // items (at most max_items) need fewer groups.
 hc_status launch_generic(const hc::KernelRef& k, void* args, size_t smem, int64_t max_items,
@@ -909,7 +937,8 @@ hc_status launch_generic(const hc::KernelRef& k, void* args, size_t smem, int64_
 
 hc_status launch_tracker(const hc::KernelRef& k, const hc::DenseArgs& a, int64_t max_items,
                          cudaStream_t st, int threads = hc::kBlock) {
-  const size_t smem = (size_t)hc::block_smem_bytes(k.lanes, k.extra, 0, threads, k.eg_bytes);
+  const size_t smem =
+      (size_t)hc::block_smem_bytes(k.lanes, k.extra, 0, threads, k.eg_bytes, k.vx);
   return launch_generic(k, (void*)&a, smem, max_items, st, threads);
 }
 
@@ -917,9 +946,9 @@ hc_status launch_tracker(const hc::KernelRef& k, const hc::DenseArgs& a, int64_t
 
 // ------------------------------------------------------------------ C-ABI
 namespace hc {
-KernelRef retrack_kernel(int deg, int n, bool mixed) {
-  const KernelRef k = dense_kernel(deg, n, mixed, 32);
-  return k.fn ? k : dense_kernel(deg, n, mixed, 0);
+KernelRef retrack_kernel(int deg, int n, int prec) {
+  const KernelRef k = dense_kernel(deg, n, prec, 32);
+  return k.fn ? k : dense_kernel(deg, n, prec, 0);
 }
 }  // namespace hc
 using hc::retrack_kernel;
@@ -1051,7 +1080,7 @@ hc_settings hc_default_settings(void) {
   s.endgame = 0;
   s.eg_cmax = 8;
   s.eg_samples = 40;
-  s.eg_reserved = 0;
+  s.retrack_precision = HC_PREC_DF;
   s.eg_s0 = 0.1;
   s.eg_ratio = 0.5;
   s.eg_tol = 1e-8;
@@ -1161,7 +1190,7 @@ hc_status hc_create_problem(const hc_problem_desc* d, hc_problem** out) {
       set_err("parameter homotopy: n <= 32, at most 8 factors per term, L + 1 + 2 n_params <= 255");
       return HC_ERR_UNSUPPORTED;
     }
-    if (!hc::term_kernel(n, true, 0).fn) {
+    if (!hc::term_kernel(n, HC_PREC_MIXED, 0).fn) {
       delete p;
       set_err("this build has parameter-homotopy kernels for n <= 24");
       return HC_ERR_UNSUPPORTED;
@@ -1245,7 +1274,7 @@ hc_status hc_problem_query(const hc_problem* p, hc_problem_info* out) {
   out->n = p->n;
   out->kind = p->kind;
   out->inputs_per_instance = p->kind != HC_TOTAL_DEGREE ? p->P : p->T;
-  out->lanes = p->terms ? hc::term_kernel(p->n, true, 0).lanes : p->L;
+  out->lanes = p->terms ? hc::term_kernel(p->n, HC_PREC_MIXED, 0).lanes : p->L;
   out->paths = p->paths;
   out->device_bytes_per_instance = hc::instance_device_bytes(p, p->paths);
   return HC_OK;
@@ -1263,7 +1292,7 @@ struct Bufs {
   const double* d_coef = nullptr;  // dense: per-instance coefficients (or the problem's)
   int64_t coef_stride = 0;
   const double2* d_p1 = nullptr;   // parameter families: target parameters
-  void *E = nullptr, *Edf = nullptr, *D64 = nullptr, *D32 = nullptr;
+  void *E = nullptr, *Edf = nullptr, *D64 = nullptr, *D32 = nullptr, *Ddf = nullptr;
   double* d_x = nullptr;
   uint8_t* d_status = nullptr;
   int32_t* d_steps = nullptr;
@@ -1322,9 +1351,12 @@ hc_status alloc_scratch(hc_problem* p, int64_t n_inst, Bufs& B, A&& alloc) {
     B.cbe = (double*)q;
   }
   if (!p->terms) {
+    const int prec = p->s.precision, last = hc::last_tier_precision(p->s);
     if ((rc = alloc(sizeof(cx<double>) * p->Estride * n_inst, &B.E)) != HC_OK) return rc;
-    if (!mixed || escalate)
+    if (prec == HC_PREC_FP64 || (escalate && last == HC_PREC_FP64))
       if ((rc = alloc(sizeof(cx<double>) * p->Dstride * n_inst, &B.D64)) != HC_OK) return rc;
+    if (prec == HC_PREC_DF || (escalate && last == HC_PREC_DF))
+      if ((rc = alloc(sizeof(cx<hc::df>) * p->Dstride * n_inst, &B.Ddf)) != HC_OK) return rc;
     if (mixed) {
       if ((rc = alloc(sizeof(cx<float>) * p->Dstride * n_inst, &B.D32)) != HC_OK) return rc;
       if ((rc = alloc(sizeof(hc::cdf) * p->Estride * n_inst, &B.Edf)) != HC_OK) return rc;
@@ -1385,6 +1417,7 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
     HC_CUDA(cudaMemsetAsync(B.E, 0, sizeof(cx<double>) * p->Estride * n_inst, st));
     if (B.Edf) HC_CUDA(cudaMemsetAsync(B.Edf, 0, sizeof(hc::cdf) * p->Estride * n_inst, st));
     if (B.D64) HC_CUDA(cudaMemsetAsync(B.D64, 0, sizeof(cx<double>) * p->Dstride * n_inst, st));
+    if (B.Ddf) HC_CUDA(cudaMemsetAsync(B.Ddf, 0, sizeof(cx<hc::df>) * p->Dstride * n_inst, st));
     if (B.D32) HC_CUDA(cudaMemsetAsync(B.D32, 0, sizeof(cx<float>) * p->Dstride * n_inst, st));
     const int64_t work = n_inst * (p->T + p->ndc);
     const int grid = (int)std::min<int64_t>((work + 255) / 256, 4096);
@@ -1392,7 +1425,7 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
                                             p->d_emap, p->ndc, p->d_dterm, p->d_dslot,
                                             p->d_dmult, (double2*)B.E, (hc::cdf*)B.Edf, p->Estride,
                                             (float2*)B.D32,
-                                            (double2*)B.D64, p->Dstride);
+                                            (double2*)B.D64, (float4*)B.Ddf, p->Dstride);
     HC_CUDA(cudaGetLastError());
   }
   HC_CUDA(cudaMemsetAsync(B.d_ctl, 0, kCtlBytes, st));
@@ -1503,12 +1536,20 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
       ta.dcf = B.dcf;
       ta.dcdf = B.dcdf;
     }
-    const hc::KernelRef k = hc::term_kernel(n, mixed, mixed ? p->s.lanes : 0);
+    const hc::KernelRef k = hc::term_kernel(n, p->s.precision, mixed ? p->s.lanes : 0);
     auto smem_of = [&](const hc::KernelRef& kr, int threads = hc::kBlock) {
-      return (size_t)hc::block_smem_bytes(kr.lanes, p->extra, kr.acc_bytes, threads, kr.eg_bytes);
+      return (size_t)hc::block_smem_bytes(kr.lanes, p->extra, kr.acc_bytes, threads, kr.eg_bytes,
+                                          kr.vx);
+    };
+    // fewer paths per block where a block's groups would not fit in shared
+    // memory (many parameters: V holds 1 + 3 P entries per group)
+    const size_t smem_cap = max_block_smem();
+    auto fit = [&](const hc::KernelRef& kr, int threads) {
+      while (threads > 32 && threads > kr.lanes && smem_of(kr, threads) > smem_cap) threads /= 2;
+      return threads;
     };
     HC_CUDA(mark(ev.ek0, st));
-    const int bth = std::max(main_threads(p->s), k.lanes);
+    const int bth = fit(k, std::max(main_threads(p->s), k.lanes));
     if ((rc = launch_generic(k, &ta, smem_of(k, bth), items, st, bth)) != HC_OK) return rc;
     HC_CUDA(mark(ev.ek1, st));
     if (escalate) {
@@ -1516,13 +1557,13 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
       if ((rc = dedupe()) != HC_OK) return rc;
       hc::TermArgs td = ta;
       td.c = cd;
-      const int th = hc::retrack_threads(k.lanes);
+      const int th = fit(k, hc::retrack_threads(k.lanes));
       if ((rc = launch_generic(k, &td, smem_of(k, th), esc_groups, hs, th)) != HC_OK) return rc;
       if ((rc = dedupe_again()) != HC_OK) return rc;
       hc::TermArgs te = ta;
       te.c = ce;
-      const hc::KernelRef k64 = hc::term_kernel(n, false, 0);
-      const int th64 = hc::retrack_threads(k64.lanes);
+      const hc::KernelRef k64 = hc::term_kernel(n, hc::last_tier_precision(p->s), 0);
+      const int th64 = fit(k64, hc::retrack_threads(k64.lanes));
       if ((rc = launch_generic(k64, &te, smem_of(k64, th64), esc_groups, hs, th64)) != HC_OK)
         return rc;
       HC_CUDA(mark(ev.ek2, hs));
@@ -1537,6 +1578,7 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
     a.c = cm;
     a.D32 = (const cx<float>*)B.D32;
     a.D64 = (const cx<double>*)B.D64;
+    a.Ddf = (const cx<hc::df>*)B.Ddf;
     a.E = (const cx<double>*)B.E;
     a.Edf = (const hc::cdf*)B.Edf;
     a.Dstride = p->Dstride;
@@ -1544,7 +1586,7 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
     a.gamma = cx<double>{p->gamma[0], p->gamma[1]};
     a.gamma32 = cx<float>{(float)p->gamma[0], (float)p->gamma[1]};
     a.gammadf = hc::split_cdf_host(p->gamma[0], p->gamma[1]);
-    const hc::KernelRef k = hc::dense_kernel(p->deg, n, mixed, mixed ? p->s.lanes : 0);
+    const hc::KernelRef k = hc::dense_kernel(p->deg, n, p->s.precision, mixed ? p->s.lanes : 0);
     if (!k.fn) {
       set_err("no kernel for this problem shape");
       return HC_ERR_UNSUPPORTED;
@@ -1560,13 +1602,13 @@ hc_status enqueue_compute(hc_problem* p, int64_t n_inst, const Bufs& B, cudaStre
       // the rows split over the warp where that variant exists
       hc::DenseArgs dd = a;
       dd.c = cd;
-      const hc::KernelRef kr = retrack_kernel(p->deg, n, true);
+      const hc::KernelRef kr = retrack_kernel(p->deg, n, HC_PREC_MIXED);
       if ((rc = launch_tracker(kr, dd, esc_groups, hs, hc::retrack_threads(kr.lanes))) != HC_OK)
         return rc;
       if ((rc = dedupe_again()) != HC_OK) return rc;
       hc::DenseArgs e = a;
       e.c = ce;
-      const hc::KernelRef k64 = retrack_kernel(p->deg, n, false);
+      const hc::KernelRef k64 = retrack_kernel(p->deg, n, hc::last_tier_precision(p->s));
       if ((rc = launch_tracker(k64, e, esc_groups, hs, hc::retrack_threads(k64.lanes))) != HC_OK)
         return rc;
       HC_CUDA(mark(ev.ek2, hs));
@@ -2165,8 +2207,8 @@ hc_status hc_autotune(hc_problem* p, const hc_batch_desc* sample, hc_tune_report
   c.precision = HC_PREC_FP64;
   cand.push_back(c);  // the recovery reference
   for (int lanes : {0, 32}) {
-    const bool has = p->terms ? hc::term_kernel(p->n, true, lanes).lanes == (lanes ? lanes : hc::term_kernel(p->n, true, 0).lanes)
-                              : hc::dense_kernel(p->deg, p->n, true, lanes).lanes == (lanes ? lanes : p->L);
+    const bool has = p->terms ? hc::term_kernel(p->n, HC_PREC_MIXED, lanes).lanes == (lanes ? lanes : hc::term_kernel(p->n, HC_PREC_MIXED, 0).lanes)
+                              : hc::dense_kernel(p->deg, p->n, HC_PREC_MIXED, lanes).lanes == (lanes ? lanes : p->L);
     if (lanes && (!has || p->n > 16)) continue;
     for (int block : {128, 64})
       for (double corr : {0.01, 0.1}) {
@@ -2320,3 +2362,176 @@ namespace hc {
 DevSettings to_dev_settings(const hc_settings& s) { return dev_settings(s); }
 hc_status check_settings(const hc_settings& s) { return validate_settings(s); }
 }  // namespace hc
+
+// ------------------------------------------------------------------ hc_evaluate
+extern "C" hc_status hc_evaluate(const hc_problem* p, int32_t precision, int32_t n_instances,
+                                 const double* inputs, int64_t n_points, const int64_t* instance,
+                                 const double* x, const double* t, double* H, double* Hx,
+                                 double* Ht) {
+  if (!p || p->magic != kProblemMagic || n_instances < 1 || n_points < 0 ||
+      (n_points > 0 && (!instance || !x || !t || !H || !Hx || !Ht)) ||
+      (precision != HC_PREC_FP64 && precision != HC_PREC_MIXED && precision != HC_PREC_DF) ||
+      (p->kind != HC_TOTAL_DEGREE && !inputs)) {
+    set_err("hc_evaluate: invalid arguments");
+    return HC_ERR_INVALID;
+  }
+  for (int64_t k = 0; k < n_points; ++k)
+    if (instance[k] < 0 || instance[k] >= n_instances) {
+      set_err("hc_evaluate: an instance index is out of range");
+      return HC_ERR_INVALID;
+    }
+  if (n_points == 0) return HC_OK;
+  const hc::KernelRef k = p->terms ? hc::term_eval_kernel(p->n, precision)
+                                   : hc::dense_eval_kernel(p->deg, p->n, precision);
+  if (!k.fn) {
+    set_err("hc_evaluate: no evaluation kernel for this problem shape");
+    return HC_ERR_UNSUPPORTED;
+  }
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != p->device) HC_CUDA(cudaSetDevice(p->device));
+  const int n = p->n;
+  std::vector<void*> mem;
+  cudaStream_t st = nullptr;
+  hc_status rc = HC_OK;
+  auto dalloc = [&](size_t bytes, void** q) -> hc_status {
+    *q = nullptr;
+    if (cudaMalloc(q, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+      set_err("hc_evaluate: cudaMalloc failed");
+      return HC_ERR_OOM;
+    }
+    mem.push_back(*q);
+    return HC_OK;
+  };
+  auto up = [&](const void* src, size_t bytes, void** q) -> hc_status {
+    hc_status r = dalloc(bytes, q);
+    if (r != HC_OK) return r;
+    if (cudaMemcpyAsync(*q, src, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      set_err("hc_evaluate: upload failed");
+      return HC_ERR_CUDA;
+    }
+    return HC_OK;
+  };
+  auto body = [&]() -> hc_status {
+    HC_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    hc::EvalPoints e;
+    void *dinst, *dx, *dt, *dH, *dHx, *dHt;
+    hc_status r;
+    if ((r = up(instance, sizeof(int64_t) * n_points, &dinst)) != HC_OK ||
+        (r = up(x, sizeof(double2) * n * n_points, &dx)) != HC_OK ||
+        (r = up(t, sizeof(double) * n_points, &dt)) != HC_OK ||
+        (r = dalloc(sizeof(double2) * n * n_points, &dH)) != HC_OK ||
+        (r = dalloc(sizeof(double2) * n * n * n_points, &dHx)) != HC_OK ||
+        (r = dalloc(sizeof(double2) * n * n_points, &dHt)) != HC_OK)
+      return r;
+    e.n_points = n_points;
+    e.inst = (const int64_t*)dinst;
+    e.x = (const double2*)dx;
+    e.t = (const double*)dt;
+    e.H = (double2*)dH;
+    e.Hx = (double2*)dHx;
+    e.Ht = (double2*)dHt;
+    const int threads = hc::kBlock;
+    size_t smem = 0;
+    void* argp = nullptr;
+    hc::DenseEvalArgs da;
+    hc::TermEvalArgs ta;
+    std::memset(&da, 0, sizeof(da));
+    std::memset(&ta, 0, sizeof(ta));
+    if (p->terms) {
+      void* dp1;
+      if ((r = up(inputs, sizeof(double2) * p->P * n_instances, &dp1)) != HC_OK) return r;
+      hc::TermArgs& a = ta.a;
+      a.rec = p->d_rec;
+      a.s64 = p->d_s64;
+      a.sdf = p->d_sdf;
+      a.TT = p->TT;
+      a.P = p->P;
+      a.ls = p->L;
+      a.extra = p->extra;
+      a.p0 = p->d_p0;
+      a.p1 = (const double2*)dp1;
+      a.start = p->d_start;
+      if (p->coef_mode) {
+        const int64_t slots = (int64_t)p->TT * p->L, cnt = slots * n_instances;
+        void *dc, *dcf, *dcdf;
+        if ((r = dalloc(sizeof(double2) * cnt, &dc)) != HC_OK ||
+            (r = dalloc(sizeof(float2) * cnt, &dcf)) != HC_OK ||
+            (r = dalloc(sizeof(hc::cdf) * cnt, &dcdf)) != HC_OK)
+          return r;
+        const int gs = (int)std::min<int64_t>((cnt + 255) / 256, 4096);
+        stage_coef_kernel<<<std::max(gs, 1), 256, 0, st>>>(
+            n_instances, slots, std::max(p->maxpf, 1), p->d_cpar, p->d_s64, p->d_c0,
+            (const double2*)dp1, p->P, (double2*)dc, (float2*)dcf, (hc::cdf*)dcdf);
+        HC_CUDA(cudaGetLastError());
+        a.coef_mode = 1;
+        a.c0 = p->d_c0;
+        a.c0f = p->d_c0f;
+        a.c0df = p->d_c0df;
+        a.dc = (const double2*)dc;
+        a.dcf = (const float2*)dcf;
+        a.dcdf = (const hc::cdf*)dcdf;
+      }
+      ta.e = e;
+      smem = (size_t)hc::block_smem_bytes(k.lanes, p->extra, k.acc_bytes, threads, 0, k.vx);
+      argp = &ta;
+    } else {
+      const void* coef = p->d_coef;
+      int64_t stride = 0;
+      if (inputs) {
+        void* dcoef;
+        if ((r = up(inputs, sizeof(double2) * p->T * n_instances, &dcoef)) != HC_OK) return r;
+        coef = dcoef;
+        stride = p->T;
+      }
+      void *E, *D32 = nullptr, *D64 = nullptr, *Ddf = nullptr;
+      const size_t es = (size_t)p->Estride * n_instances, ds = (size_t)p->Dstride * n_instances;
+      if ((r = dalloc(sizeof(double2) * es, &E)) != HC_OK) return r;
+      if (precision == HC_PREC_MIXED && (r = dalloc(sizeof(float2) * ds, &D32)) != HC_OK) return r;
+      if (precision == HC_PREC_FP64 && (r = dalloc(sizeof(double2) * ds, &D64)) != HC_OK) return r;
+      if (precision == HC_PREC_DF && (r = dalloc(sizeof(float4) * ds, &Ddf)) != HC_OK) return r;
+      HC_CUDA(cudaMemsetAsync(E, 0, sizeof(double2) * es, st));
+      if (D32) HC_CUDA(cudaMemsetAsync(D32, 0, sizeof(float2) * ds, st));
+      if (D64) HC_CUDA(cudaMemsetAsync(D64, 0, sizeof(double2) * ds, st));
+      if (Ddf) HC_CUDA(cudaMemsetAsync(Ddf, 0, sizeof(float4) * ds, st));
+      const int64_t work = (int64_t)n_instances * (p->T + p->ndc);
+      const int grid = (int)std::min<int64_t>((work + 255) / 256, 4096);
+      stage_dense_kernel<<<std::max(grid, 1), 256, 0, st>>>(
+          n_instances, p->T, (const double2*)coef, stride, p->d_emap, p->ndc, p->d_dterm,
+          p->d_dslot, p->d_dmult, (double2*)E, nullptr, p->Estride, (float2*)D32,
+          (double2*)D64, (float4*)Ddf, p->Dstride);
+      HC_CUDA(cudaGetLastError());
+      hc::DenseArgs& a = da.a;
+      a.D32 = (const cx<float>*)D32;
+      a.D64 = (const cx<double>*)D64;
+      a.Ddf = (const cx<hc::df>*)Ddf;
+      a.E = (const cx<double>*)E;
+      a.Dstride = p->Dstride;
+      a.Estride = p->Estride;
+      a.gamma = cx<double>{p->gamma[0], p->gamma[1]};
+      a.gamma32 = cx<float>{(float)p->gamma[0], (float)p->gamma[1]};
+      a.gammadf = hc::split_cdf_host(p->gamma[0], p->gamma[1]);
+      da.e = e;
+      smem = (size_t)hc::block_smem_bytes(k.lanes, k.extra, 0, threads, 0, k.vx);
+      argp = &da;
+    }
+    if (smem > 48 * 1024)
+      HC_CUDA(cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t groups = (n_points + threads / k.lanes - 1) / (threads / k.lanes);
+    const int grid = (int)std::min<int64_t>(groups, 65535);
+    void* argv[] = {argp};
+    HC_CUDA(cudaLaunchKernel(k.fn, dim3((unsigned)grid), dim3(threads), argv, smem, st));
+    HC_CUDA(cudaMemcpyAsync(H, dH, sizeof(double2) * n * n_points, cudaMemcpyDeviceToHost, st));
+    HC_CUDA(cudaMemcpyAsync(Hx, dHx, sizeof(double2) * n * n * n_points, cudaMemcpyDeviceToHost,
+                            st));
+    HC_CUDA(cudaMemcpyAsync(Ht, dHt, sizeof(double2) * n * n_points, cudaMemcpyDeviceToHost, st));
+    HC_CUDA(cudaStreamSynchronize(st));
+    return HC_OK;
+  };
+  rc = body();
+  if (st) cudaStreamSynchronize(st);
+  for (void* q : mem) cudaFree(q);
+  if (st) cudaStreamDestroy(st);
+  if (cur != p->device) cudaSetDevice(cur);
+  return rc;
+}

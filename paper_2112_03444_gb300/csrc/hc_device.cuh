@@ -147,7 +147,8 @@ __device__ __forceinline__ R gsum(const Group& g, R v) {
 // The pivot row reaches the other lanes through shared memory: the pivot
 // lane stores its remaining columns (FP32: two complex numbers per 16-byte
 // store; the pivot column's slot carries 1/pivot), the group synchronises,
-// and every lane reads them back with 16-byte broadcast loads.  Two buffers
+// and every lane reads them back with 16-byte broadcast loads (FP64 and
+// double-float: one complex entry per 16-byte word).  Two buffers
 // alternate, so one __syncwarp per pivot step orders writes after the
 // previous step's reads.  pv: 2 * ((N + NR + 1) & ~1) entries, 16-byte
 // aligned, private to the group.
@@ -195,12 +196,9 @@ __device__ __forceinline__ bool gj_solve(const Group& g, cx<R> (&a)[N + NR], cx<
           const cx<R> v1 = (j + 1 == k) ? inv : (j + 1 < W ? a[j + 1 < W ? j + 1 : 0] : czero<R>());
           reinterpret_cast<float4*>(buf)[j >> 1] = make_float4(v0.re, v0.im, v1.re, v1.im);
         }
-      } else {
+      } else {  // FP64 or double-float: one 16-byte store per entry
 #pragma unroll
-        for (int j = k; j < W; ++j) {
-          const cx<R> v = (j == k) ? inv : a[j];
-          reinterpret_cast<double2*>(buf)[j] = make_double2(v.re, v.im);
-        }
+        for (int j = k; j < W; ++j) buf[j] = (j == k) ? inv : a[j];
       }
       used = true;
       dinv = inv;
@@ -217,10 +215,7 @@ __device__ __forceinline__ bool gj_solve(const Group& g, cx<R> (&a)[N + NR], cx<
       }
     } else {
 #pragma unroll
-      for (int j = k; j < W; ++j) {
-        const double2 q = reinterpret_cast<const double2*>(buf)[j];
-        row_p[j] = mk<R>(q.x, q.y);
-      }
+      for (int j = k; j < W; ++j) row_p[j] = buf[j];
     }
     const cx<R> l = me ? czero<R>() : a[k] * row_p[k];
     a[k + 1] = cfms(l, row_p[k + 1], a[k + 1]);

@@ -18,17 +18,22 @@ constexpr int kBlock = 128;  // threads per block of the tracking kernels
 // The stride between groups is 16 bytes past a multiple of 128: the groups
 // of a warp reading their own broadcast word (a point entry, a monomial,
 // the pivot row) then hit different banks.
-// The all-FP64 kernels add eg bytes for the endgame's samples (three complex
-// doubles per lane: the previous sample, its dx/ds, the last prediction).
-__host__ __device__ constexpr int group_smem_bytes(int L, int extra, int acc = 0, int eg = 0) {
-  return ((32 * (L + 2) + acc + (L + extra) * 16 + L * 16 + (L + extra) * 8 + eg + 127) & ~127) +
+// The FP64-state kernels (precision FP64 and double-float) add eg bytes for
+// the endgame's samples (three complex doubles per lane: the previous
+// sample, its dx/ds, the last prediction); the double-float kernels (vx)
+// also a double-float copy of the point, (L + extra) 16.
+__host__ __device__ constexpr int group_smem_bytes(int L, int extra, int acc = 0, int eg = 0,
+                                                   int vx = 0) {
+  return ((32 * (L + 2) + acc + (L + extra) * 16 + L * 16 + (L + extra) * 8 + eg +
+           (vx ? (L + extra) * 16 : 0) + 127) &
+          ~127) +
          16;
 }
 __host__ __device__ constexpr int endgame_smem_bytes(int L, bool mixed) { return mixed ? 0 : 48 * L; }
 // Dynamic shared memory of one tracking block of `threads` threads
 __host__ __device__ constexpr int block_smem_bytes(int L, int extra, int acc = 0,
-                                                   int threads = kBlock, int eg = 0) {
-  return (threads / L) * group_smem_bytes(L, extra, acc, eg);
+                                                   int threads = kBlock, int eg = 0, int vx = 0) {
+  return (threads / L) * group_smem_bytes(L, extra, acc, eg, vx);
 }
 // Threads per block of a launch: one warp for one-path-per-warp launches of
 // the re-tracking tiers (a hard path then holds only its own warp's
@@ -97,6 +102,7 @@ struct DenseArgs {
   LaunchCommon c;
   const cx<float>* D32;
   const cx<double>* D64;
+  const cx<df>* Ddf;         // D as double-floats (double-float kernels)
   const cx<double>* E;
   const cdf* Edf;            // E as double-floats (mixed-precision kernels' residuals)
   int64_t Dstride, Estride;  // complex elements per instance
@@ -148,24 +154,59 @@ struct TermArgs {
   const cdf* dcdf;
 };
 
+// Points at which hc_evaluate evaluates the homotopy (device buffers):
+// point k belongs to instance inst[k], lies at x[k] (n complex) and t[k];
+// outputs dH/dx row-major [k][i][j], H [k][i] and dH/dt [k][i].
+struct EvalPoints {
+  int64_t n_points;
+  const int64_t* inst;
+  const double2* x;
+  const double* t;
+  double2* Hx;
+  double2* H;
+  double2* Ht;
+};
+struct DenseEvalArgs {
+  DenseArgs a;
+  EvalPoints e;
+};
+struct TermEvalArgs {
+  TermArgs a;
+  EvalPoints e;
+};
+
 struct KernelRef {
   const void* fn;   // __global__ function
   int lanes;        // lanes per path (L)
   int extra;        // per-group shared entries behind the point the kernel itself needs
   int acc_bytes;    // bytes of one evaluator accumulator (per lane and row entry), 0: none
-  int eg_bytes;     // per-group endgame sample bytes (all-FP64 kernels), 0: none
+  int eg_bytes;     // per-group endgame sample bytes (FP64-state kernels), 0: none
+  int vx;           // 1: double-float kernel (a double-float copy of the point)
 };
 
 // Lanes per path chosen for n unknowns (one row per lane, groups are powers
 // of two so that a warp holds 32 / L paths).
 inline int lanes_for(int n) { return n <= 4 ? 4 : n <= 8 ? 8 : n <= 16 ? 16 : 32; }
 
-// lanes = 0: default group width; 32: one path per warp (mixed kernels, n <= 16)
-KernelRef dense_kernel(int deg, int n, bool mixed, int lanes);  // fn == nullptr if absent
-KernelRef term_kernel(int n, bool mixed, int lanes);            // fn == nullptr if absent
+// prec: HC_PREC_FP64, HC_PREC_MIXED or HC_PREC_DF.  lanes = 0: default
+// group width; 32: one path per warp (mixed kernels, n <= 16)
+KernelRef dense_kernel(int deg, int n, int prec, int lanes);  // fn == nullptr if absent
+KernelRef term_kernel(int n, int prec, int lanes);            // fn == nullptr if absent
 // Kernel of the re-tracking tiers (few paths): one path per warp with split
 // rows where available, else the default width.
-KernelRef retrack_kernel(int deg, int n, bool mixed);
+KernelRef retrack_kernel(int deg, int n, int prec);
+// Precision of the mixed pipeline's last re-tracking tier: retrack_precision,
+// except with the endgame, which keeps FP64: its cycle-number estimate and
+// Hermite extrapolation use dx/ds at the samples, and near a multiple root
+// the double-float solve loses five bits of it to the Jacobian's condition.
+inline int last_tier_precision(const hc_settings& s) {
+  return s.endgame ? HC_PREC_FP64 : s.retrack_precision;
+}
+
+// Evaluation kernels of hc_evaluate (prec: HC_PREC_FP64, HC_PREC_MIXED =
+// FP32 evaluation, HC_PREC_DF); fn == nullptr if absent.
+KernelRef dense_eval_kernel(int deg, int n, int prec);
+KernelRef term_eval_kernel(int n, int prec);
 
 // Defined in server.cu: frees a server if magic is the server's magic.
 bool destroy_server_if(void* handle, uint32_t magic);

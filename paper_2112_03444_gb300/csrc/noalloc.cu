@@ -125,11 +125,22 @@ __device__ int nested_index(int n, int d, const int* vars, int g) {
 
 // Encodes coefficients given in the canonical dense order
 // coef[inst][i][m] (equation i, monomial m of the graded order) into E, D64
-// and D32, computing the index maps on the fly.
+// and D32 (and Ddf, the double-float table, if given), computing the index
+// maps on the fly.
+__device__ __forceinline__ void put_d(double2* D64, float2* D32, float4* Ddf, int64_t slot,
+                                      double2 v) {
+  D64[slot] = v;
+  D32[slot] = make_float2((float)v.x, (float)v.y);
+  if (Ddf) {  // cx<df> layout: re hi, re lo, im hi, im lo
+    const hc::df re(v.x), im(v.y);
+    Ddf[slot] = make_float4(re.hi, re.lo, im.hi, im.lo);
+  }
+}
+
 __global__ void stage_canonical_kernel(int64_t n_inst, int n, int d, int M, int MP, int L,
                                        const double2* __restrict__ coef, double2* E,
                                        hc::cdf* Edf, int64_t Es, double2* D64, float2* D32,
-                                       int64_t Ds) {
+                                       float4* Ddf, int64_t Ds) {
   const int64_t total = n_inst * n * M;
   for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < total;
        w += (int64_t)gridDim.x * blockDim.x) {
@@ -143,9 +154,7 @@ __global__ void stage_canonical_kernel(int64_t n_inst, int n, int d, int M, int 
     E[eslot] = c;
     Edf[eslot] = hc::to_cdf(hc::cx<double>{c.x, c.y});
     if (g == 0) {
-      const int64_t slot = inst * Ds + hc::dense_slot(n, d, L, n, 0, i);
-      D64[slot] = c;
-      D32[slot] = make_float2((float)c.x, (float)c.y);
+      put_d(D64, D32, Ddf, inst * Ds + hc::dense_slot(n, d, L, n, 0, i), c);
       continue;
     }
     for (int p = 0; p < g; ++p) {
@@ -162,10 +171,8 @@ __global__ void stage_canonical_kernel(int64_t n_inst, int n, int d, int M, int 
         rest[nr++] = vars[q];
       }
       const int mp = rank_graded(n, rest, nr);
-      const int64_t slot = inst * Ds + hc::dense_slot(n, d, L, j, mp, i);
-      const double2 v = make_double2(a * c.x, a * c.y);
-      D64[slot] = v;
-      D32[slot] = make_float2((float)v.x, (float)v.y);
+      put_d(D64, D32, Ddf, inst * Ds + hc::dense_slot(n, d, L, j, mp, i),
+            make_double2(a * c.x, a * c.y));
     }
   }
 }
@@ -196,6 +203,8 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
   if (vs != HC_OK) return vs;
   const bool mixed = settings->precision == HC_PREC_MIXED;
   const bool escalate = mixed && settings->escalate;
+  const bool use_df = settings->precision == HC_PREC_DF ||
+                      (escalate && hc::last_tier_precision(*settings) == HC_PREC_DF);
   const int L = hc::lanes_for(n);
   const int M = binom_h(n + degree, degree);
   const int MP = binom_h(n + degree - 1, degree - 1);
@@ -210,11 +219,13 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
   const size_t edf_b = align256(sizeof(hc::cdf) * Es * n_instances);
   const size_t d64_b = align256(sizeof(double2) * Ds * n_instances);
   const size_t d32_b = align256(sizeof(float2) * Ds * n_instances);
+  const size_t ddf_b = use_df ? align256(sizeof(float4) * Ds * n_instances) : 0;
   const size_t esc_b = escalate ? align256(sizeof(int64_t) * items) : 0;
   const size_t dup_b = esc_b;
   const size_t tio_b = escalate ? align256(sizeof(double) * items) : 0;
   const size_t x32_b = escalate ? align256(sizeof(float2) * n * items) : 0;
-  const size_t need = ctl_b + e_b + edf_b + d64_b + d32_b + esc_b + dup_b + tio_b + x32_b;
+  const size_t need =
+      ctl_b + e_b + edf_b + d64_b + d32_b + ddf_b + esc_b + dup_b + tio_b + x32_b;
   if (need > kNoAllocScratchBytes) {
     char msg[200];
     std::snprintf(msg, sizeof(msg),
@@ -238,6 +249,8 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
   p += d64_b;
   float2* D32 = reinterpret_cast<float2*>(p);
   p += d32_b;
+  float4* Ddf = use_df ? reinterpret_cast<float4*>(p) : nullptr;
+  p += ddf_b;
   int64_t* esc = escalate ? reinterpret_cast<int64_t*>(p) : nullptr;
   p += esc_b;
   int64_t* dup = escalate ? reinterpret_cast<int64_t*>(p) : nullptr;
@@ -255,14 +268,14 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
     }                                                                                   \
   } while (0)
   // the array keeps the previous call's contents: clear what starts at zero
-  NA_CUDA(cudaMemsetAsync(ctl, 0, ctl_b + e_b + edf_b + d64_b + d32_b, st));
+  NA_CUDA(cudaMemsetAsync(ctl, 0, ctl_b + e_b + edf_b + d64_b + d32_b + ddf_b, st));
   NA_CUDA(cudaMemsetAsync(steps_out, 0, sizeof(int32_t) * 3 * items, st));
   {
     const int64_t work = (int64_t)n_instances * n * M;
     const int grid = (int)((work + 255) / 256 < 4096 ? (work + 255) / 256 : 4096);
     stage_canonical_kernel<<<grid, 256, 0, st>>>(n_instances, n, degree, M, MP, L,
                                                  reinterpret_cast<const double2*>(coef), E, Edf,
-                                                 Es, D64, D32, Ds);
+                                                 Es, D64, D32, Ddf, Ds);
     NA_CUDA(cudaGetLastError());
   }
 
@@ -284,6 +297,7 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
   a.c.dup_count = ctl + 7;
   a.D32 = reinterpret_cast<const hc::cx<float>*>(D32);
   a.D64 = reinterpret_cast<const hc::cx<double>*>(D64);
+  a.Ddf = reinterpret_cast<const hc::cx<hc::df>*>(Ddf);
   a.E = reinterpret_cast<const hc::cx<double>*>(E);
   a.Edf = Edf;
   a.Dstride = Ds;
@@ -297,7 +311,8 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
   NA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   auto launch = [&](const hc::KernelRef& k, const hc::DenseArgs& args, int64_t max_items,
                     int threads = hc::kBlock) {
-    const size_t smem = (size_t)hc::block_smem_bytes(k.lanes, k.extra, 0, threads, k.eg_bytes);
+    const size_t smem =
+        (size_t)hc::block_smem_bytes(k.lanes, k.extra, 0, threads, k.eg_bytes, k.vx);
     int blocks = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k.fn, threads, smem) !=
         cudaSuccess)
@@ -311,8 +326,9 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
     return cudaLaunchKernel(k.fn, dim3((unsigned)grid), dim3(threads), argv, smem, st);
   };
   // the autotuner's group width where that variant exists (as hc_track_batch)
-  hc::KernelRef k = hc::dense_kernel(degree, n, mixed, mixed ? settings->lanes : 0);
-  if (!k.fn) k = hc::dense_kernel(degree, n, mixed, 0);
+  hc::KernelRef k =
+      hc::dense_kernel(degree, n, settings->precision, mixed ? settings->lanes : 0);
+  if (!k.fn) k = hc::dense_kernel(degree, n, settings->precision, 0);
   if (!k.fn) {
     hc::set_last_error("hc_track_dense_noalloc: no kernel for this shape");
     return HC_ERR_UNSUPPORTED;
@@ -329,7 +345,7 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
     dd.c.spread = 1;
     dd.c.dup_list = nullptr;
     dd.c.dup_count = nullptr;
-    const hc::KernelRef kr = hc::retrack_kernel(degree, n, true);
+    const hc::KernelRef kr = hc::retrack_kernel(degree, n, HC_PREC_MIXED);
     NA_CUDA(launch(kr, dd, items, hc::retrack_threads(kr.lanes)));
     NA_CUDA(hc::launch_dedupe(items, paths, n, x32, status_out, 1e-6f, dup, ctl + 7, esc, ctl + 2,
                               t_io, st));
@@ -343,7 +359,7 @@ extern "C" hc_status hc_track_dense_noalloc(int32_t n, int32_t degree, const dou
     e.c.spread = 1;
     e.c.dup_list = nullptr;
     e.c.dup_count = nullptr;
-    const hc::KernelRef k64 = hc::retrack_kernel(degree, n, false);
+    const hc::KernelRef k64 = hc::retrack_kernel(degree, n, hc::last_tier_precision(*settings));
     NA_CUDA(launch(k64, e, items, hc::retrack_threads(k64.lanes)));
   }
 #undef NA_CUDA

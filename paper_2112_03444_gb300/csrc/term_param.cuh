@@ -36,16 +36,41 @@ namespace hc {
 // The high-precision copy of V (Vd, 16 bytes per entry) holds complex FP64
 // in the all-FP64 kernels and double-floats (dfloat.cuh) in the
 // mixed-precision ones (DF), whose residuals run in double-float arithmetic.
+// Sum of a lane's value and its partner's (lane xor o), the lower lane's
+// value first on both lanes so that the two copies agree bit for bit.
+template <class R>
+__device__ __forceinline__ R pair_sum(R v, int o, bool upper) {
+  R w;
+  if constexpr (std::is_same<R, df>::value)
+    w = shfl_xor_df(v, o);
+  else
+    w = __shfl_xor_sync(0xffffffffu, v, o);
+  return upper ? w + v : v + w;
+}
+template <class R>
+__device__ __forceinline__ cx<R> pair_sum(cx<R> v, int o, bool upper) {
+  return {pair_sum<R>(v.re, o, upper), pair_sum<R>(v.im, o, upper)};
+}
+__device__ __forceinline__ cdf pair_sum(cdf v, int o, bool upper) {
+  const cdf w{__shfl_xor_sync(0xffffffffu, v.hr, o), __shfl_xor_sync(0xffffffffu, v.hi_, o),
+              __shfl_xor_sync(0xffffffffu, v.lr, o), __shfl_xor_sync(0xffffffffu, v.li, o)};
+  return upper ? cdf_add(w, v) : cdf_add(v, w);
+}
+
 template <int N, int L, bool DF>
 struct TermEval {
-  static constexpr int PARTS = 1;  // one row per lane, no replicas
-  static constexpr int ROWL = L;
+  // One path per warp (L = 32, N <= 16; the autotuner's lanes = 32
+  // candidate): every row on two lanes, each taking every other term slot,
+  // so that the warp's lanes all work.  Otherwise one row per lane.
+  static constexpr int PARTS = (L == 32 && N <= 16) ? 2 : 1;
+  static constexpr int ROWL = L / PARTS;
   const TermArgs* a;
   int64_t inst;
   Group g;
   cx<float>* Vf;
   cx<double>* Vd;
   unsigned char* acc;  // [N + 2][L] accumulators of cx<R>, this lane at column g.gl
+  cx<df>* Vx;          // double-float kernels: V as double-floats; nullptr otherwise
 
   // constant part of V for this path: the 1, dp and p0 (FP32 copies, and
   // for DF double-float copies of dp and p0 in Vd)
@@ -60,8 +85,13 @@ struct TermEval {
       else
         Vd[LS] = mk<double>(1.0, 0.0);
     }
+    if (Vx && g.gl == 0) Vx[LS] = mk<df>(df(1), df(0));
     for (int l = g.gl; l < P; l += L) {
       const cx<double> d = mk<double>(p1[l].x - a->p0[l].x, p1[l].y - a->p0[l].y);
+      if (Vx) {
+        Vx[LS + 1 + P + l] = to_cxdf(d);
+        Vx[LS + 1 + 2 * P + l] = to_cxdf(mk<double>(a->p0[l].x, a->p0[l].y));
+      }
       if constexpr (DF) {
         Vdf[LS + 1 + P + l] = to_cdf(d);
         Vdf[LS + 1 + 2 * P + l] = to_cdf(mk<double>(a->p0[l].x, a->p0[l].y));
@@ -82,18 +112,25 @@ struct TermEval {
   __device__ __forceinline__ cx<R>* vptr() const {
     if constexpr (std::is_same<R, float>::value)
       return Vf;
+    else if constexpr (std::is_same<R, df>::value)
+      return Vx;
     else
       return Vd;
   }
 
   // p(t) into V (each lane a share), then wait for the group.  FP64:
-  // (1-t) p0 + t p1 from the inputs; FP32: p0 + t dp from the FP32 copies.
+  // (1-t) p0 + t p1 from the inputs; FP32: p0 + t dp from the FP32 copies;
+  // double-float: p0 + t dp from the double-float copies, and the point
+  // (which the tracker keeps in FP64 in Vd) split into double-floats.
   template <class R>
   __device__ __forceinline__ void put_params(R t) const {
     const int P = a->P, LS = a->ls;
     if constexpr (std::is_same<R, float>::value) {
       for (int l = g.gl; l < P; l += L)
         Vf[LS + 1 + l] = cfma(mk<float>(t, 0.f), Vf[LS + 1 + P + l], Vf[LS + 1 + 2 * P + l]);
+    } else if constexpr (std::is_same<R, df>::value) {
+      if (g.gl < N) Vx[g.gl] = to_cxdf(Vd[g.gl]);
+      for (int l = g.gl; l < P; l += L) Vx[LS + 1 + l] = Vx[LS + 1 + 2 * P + l] + t * Vx[LS + 1 + P + l];
     } else {
       const double2* p1 = a->p1 + inst * P;
       // DF: the 1 of V is held as a double-float between FP64 residuals
@@ -145,6 +182,9 @@ struct TermEval {
       const float2 c = a->c0f[r], d = a->dcf[rd];
       dcr = mk<float>(d.x, d.y);
       s = cfma(mk<float>(t, 0.f), dcr, mk<float>(c.x, c.y));
+    } else if constexpr (std::is_same<R, df>::value) {
+      dcr = to_cxdf(a->dcdf[rd]);
+      s = to_cxdf(a->c0df[r]) + t * dcr;
     } else {
       const double2 c = a->c0[r], d = a->dc[rd];
       dcr = mk<double>(d.x, d.y);
@@ -157,13 +197,14 @@ struct TermEval {
                                        cx<R>& H, cx<R>& Ht) const {
     put_params<R>(t);
     const cx<R>* V = vptr<R>();
-    const int ii = i < N ? i : 0;
+    const int rr = i & (ROWL - 1), part = i / ROWL;  // row, and share of the term slots
+    const int ii = rr < N ? rr : 0;
     cx<R>* A = reinterpret_cast<cx<R>*>(acc) + g.gl;
 #pragma unroll
     for (int e = 0; e <= N; ++e) A[e * L] = czero<R>();
     cx<R> h = czero<R>();
 #pragma unroll 1
-    for (int k = 0; k < a->TT; ++k) {
+    for (int k = part; k < a->TT; k += PARTS) {
       const int64_t r = (int64_t)k * a->ls + ii;
       const TermRec rc = a->rec[r];
       cx<R> s, dcr = czero<R>();
@@ -171,6 +212,8 @@ struct TermEval {
         coef_at<R>(r, t, s, dcr);
       else if constexpr (std::is_same<R, float>::value)
         s = mk<float>(rc.s.x, rc.s.y);
+      else if constexpr (std::is_same<R, df>::value)
+        s = to_cxdf(a->sdf[r]);
       else
         s = mk<double>(a->s64[r].x, a->s64[r].y);
       cx<R> run = czero<R>();
@@ -188,21 +231,31 @@ struct TermEval {
       // coefficient interpolation: d/dt of (c0 + t dc) x^a is dc x^a
       if (a->coef_mode) A[N * L] = cfma(dcr, run, A[N * L]);
     }
+    if constexpr (PARTS > 1) {  // add the two halves, part 0's first
+      __syncwarp(g.mask);
+      const cx<R>* A0 = reinterpret_cast<const cx<R>*>(acc) + rr;
 #pragma unroll
-    for (int j = 0; j < N; ++j) row[j] = A[j * L];
-    Ht = A[N * L];
-    H = h;
+      for (int j = 0; j < N; ++j) row[j] = A0[j * L] + A0[j * L + ROWL];
+      Ht = A0[N * L] + A0[N * L + ROWL];
+      H = pair_sum(h, ROWL, part == 1);
+    } else {
+#pragma unroll
+      for (int j = 0; j < N; ++j) row[j] = A[j * L];
+      Ht = A[N * L];
+      H = h;
+    }
   }
 
   template <bool SCALE>
   __device__ __forceinline__ void residual64(const cx<double>*, int i, double t, double,
                                              cx<double>& H, double& sc) const {
     put_params<double>(t);
-    const int ii = i < N ? i : 0;
+    const int rr = i & (ROWL - 1), part = i / ROWL;
+    const int ii = rr < N ? rr : 0;
     cx<double> h = czero<double>();
     float s_abs = 0.f;
 #pragma unroll 1
-    for (int k = 0; k < a->TT; ++k) {
+    for (int k = part; k < a->TT; k += PARTS) {
       const int64_t r = (int64_t)k * a->ls + ii;
       const TermRec rc = a->rec[r];
       cx<double> prod = Vd[rc.idx[0]];
@@ -215,6 +268,10 @@ struct TermEval {
         s = mk<double>(a->s64[r].x, a->s64[r].y);
       h = cfma(s, prod, h);
       if (SCALE) s_abs += cabs2(cvt<float>(s)) * cabs2(cvt<float>(prod));
+    }
+    if constexpr (PARTS > 1) {
+      h = pair_sum(h, ROWL, part == 1);
+      if (SCALE) s_abs = pair_sum(s_abs, ROWL, part == 1);
     }
     H = h;
     sc = SCALE ? (double)s_abs : 0.0;
@@ -234,11 +291,12 @@ struct TermEval {
     for (int l = g.gl; l < P; l += L)
       V[LS + 1 + l] = cdf_add(V[LS + 1 + 2 * P + l], cdf_scale(tdf, V[LS + 1 + P + l]));
     __syncwarp(g.mask);
-    const int ii = i < N ? i : 0;
+    const int rr = i & (ROWL - 1), part = i / ROWL;
+    const int ii = rr < N ? rr : 0;
     cdf h = cdf_zero();
     float s_abs = 0.f;
 #pragma unroll 1
-    for (int k = 0; k < a->TT; ++k) {
+    for (int k = part; k < a->TT; k += PARTS) {
       const int64_t r = (int64_t)k * a->ls + ii;
       const TermRec rc = a->rec[r];
       cdf prod = V[rc.idx[0]];
@@ -251,6 +309,10 @@ struct TermEval {
       h = cdf_fma(s, prod, h);
       if (SCALE) s_abs += cdf_abs_hi(s) * cdf_abs_hi(prod);
     }
+    if constexpr (PARTS > 1) {
+      h = pair_sum(h, ROWL, part == 1);
+      if (SCALE) s_abs = pair_sum(s_abs, ROWL, part == 1);
+    }
     H = cdf_to_cf(h);
     sc = SCALE ? s_abs : 0.f;
   }
@@ -262,7 +324,7 @@ struct TermProblem {
   Group g;
   GroupMem sm;
   __device__ __forceinline__ TermEval<N, L, DF> hom(int64_t inst) const {
-    return TermEval<N, L, DF>{a, inst, g, sm.vf, sm.vd, sm.acc};
+    return TermEval<N, L, DF>{a, inst, g, sm.vf, sm.vd, sm.acc, sm.vx};
   }
 };
 
@@ -272,21 +334,27 @@ __host__ __device__ constexpr int term_acc_bytes() {
   return (N + 1) * L * (MIXED ? 8 : 16);
 }
 
-template <int N, bool MIXED, int L>
+// PREC: HC_PREC_MIXED, HC_PREC_FP64 or HC_PREC_DF (as the dense kernels)
+template <int N, int PREC, int L>
 __global__ void __launch_bounds__(kBlock) term_param_kernel(const __grid_constant__ TermArgs a) {
+  constexpr bool MIXED = PREC == HC_PREC_MIXED;
+  constexpr bool XDF = PREC == HC_PREC_DF;
+  using RE = typename std::conditional<XDF, df, double>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   const Group g = make_group<L>();
   const GroupMem sm = make_group_mem<L>(smem, a.extra, term_acc_bytes<N, MIXED, L>(),
-                                        endgame_smem_bytes(L, MIXED));
+                                        endgame_smem_bytes(L, MIXED), XDF ? 1 : 0);
   TermProblem<N, L, MIXED> prob{&a, g, sm};
-  run_tracker<N, L, MIXED>(prob, a.c, g, sm);
+  run_tracker<N, L, MIXED, TermProblem<N, L, MIXED>, RE>(prob, a.c, g, sm);
 }
 
-template <bool MIXED, int N, int LANES = 0>
+template <int PREC, int N, int LANES = 0>
 KernelRef term_ref() {
+  constexpr bool MIXED = PREC == HC_PREC_MIXED;
   constexpr int L = LANES ? LANES : ((N <= 4) ? 4 : (N <= 8) ? 8 : (N <= 16) ? 16 : 32);
-  return KernelRef{reinterpret_cast<const void*>(&term_param_kernel<N, MIXED, L>), L, 0,
-                   term_acc_bytes<N, MIXED, L>(), endgame_smem_bytes(L, MIXED)};
+  return KernelRef{reinterpret_cast<const void*>(&term_param_kernel<N, PREC, L>), L, 0,
+                   term_acc_bytes<N, MIXED, L>(), endgame_smem_bytes(L, MIXED),
+                   PREC == HC_PREC_DF ? 1 : 0};
 }
 
 }  // namespace hc

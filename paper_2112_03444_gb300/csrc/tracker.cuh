@@ -21,40 +21,51 @@
 // body together even when their paths start and end at different times.
 //
 // Precision tiers.
-//   MIXED = false: every operation in complex FP64 (the plain form).
+//   MIXED = false, RE = double: every operation in complex FP64 (the plain form).
+//   MIXED = false, RE = df: the same state, time, step control, corrector
+//     and refinement residuals and classification in FP64, but the RK4
+//     stages, the Jacobians and the solves -- nearly all of the arithmetic --
+//     in complex double-float arithmetic (FP32 pairs, about 48 bits, see
+//     dfloat.cuh) on the FP32 pipe.  After a path's first rejected step the
+//     corrector takes its residual in FP64: iterative refinement with a
+//     48-bit solve, which reaches what an FP64 corrector reaches (a path of
+//     condition 1e10 would otherwise sit at a double-float noise floor of
+//     1e-5), and the FP64 residual costs a fraction of an FP64 evaluation
+//     with its Jacobian.
 //   MIXED = true : for t < t_endgame the state, the RK4 stages and the Newton
 //     iterations are complex FP32 and no FP64 instruction executes; for
 //     t > t_endgame the state is FP64 and the corrector's residual H is
-//     evaluated in double-float arithmetic (FP32 pairs, about 48 bits, see
-//     dfloat.cuh) -- in FP64 once a step of the path has been rejected
-//     there -- while the Jacobian and the solve stay FP32 (mixed precision
-//     iterative refinement, converged to the FP64 tolerance within
-//     max_newton_ir iterations: each contracts only linearly, by about
-//     cond * 6e-8, so one exact Newton step is worth about two); the final
-//     refinement and the backward error use FP64 residuals the same way
-//     (the refinement target, 1e-13, lies below the double-float noise
-//     floor times the condition of most endpoints).
+//     evaluated in double-float arithmetic -- in FP64 once a step of the
+//     path has been rejected there -- while the Jacobian and the solve stay
+//     FP32 (mixed precision iterative refinement, converged to the FP64
+//     tolerance within max_newton_ir iterations: each contracts only
+//     linearly, by about cond * 6e-8, so one exact Newton step is worth
+//     about two); the final refinement and the backward error use
+//     double-float residuals the same way (their error, about 2^-48 times
+//     the backward-error scale, lies three orders below the refinement
+//     target 1e-13 and five below the finite-root bound 1e-10).
 //     A path whose FP32 steps fall below dt_min_fp32 (the corrector stalls
 //     at the FP32 noise floor near an ill-conditioned stretch) or exhaust
-//     max_steps_fp32 switches to that FP64-residual mode at once.  GB300
-//     issues FP64 FMAs at about 1/74 of its FP32 rate (measured), so the
-//     corrector residuals run on the FP32 pipe where their precision
-//     suffices.  Paths that still fail,
-//     paths whose endpoints collide (a path jump) and endpoints whose FP32
-//     condition estimate is suspect are re-tracked by the all-FP64 kernel.
+//     max_steps_fp32 switches to that high-precision-residual mode at once.
+//     GB300 issues FP64 FMAs at about 1/74 of its FP32 rate (measured), so
+//     the residuals run on the FP32 pipe where their precision suffices.
+//     Paths that still fail, paths whose endpoints collide (a path jump) and
+//     endpoints whose FP32 condition estimate is suspect are re-tracked by
+//     an FP64-state kernel (RE = df by default, settings.retrack_precision).
 //
 // Evaluator interface (HOM):
 //   template <class R> eval(x[N], i, t, 1-t, row[N+1], H, Ht)
 //       row[j] = dH_i/dx_j (j < N), H = H_i, Ht = dH_i/dt, all at (x, t)
 //   residual64<SCALE>(xs, i, t, 1-t, H, scale)   H_i in FP64 at the point
 //       xs[0..N) (shared memory), and with SCALE the backward-error
-//       denominator sum |c| |x^a| of row i (all-FP64 kernels)
+//       denominator sum |c| |x^a| of row i (FP64-state kernels)
 //   residual_df<SCALE>(xs, i, t, H, scale)         the same in double-float
 //       arithmetic, xs as double-floats, H rounded to FP32 (mixed kernels)
 //   start(path, i)                                 start component x_i(0)
 //   init(g)                                        per-path set-up (once per path)
 // Evaluators read the point from the group's shared copy written by the
-// tracker before every evaluation (vf for FP32, vd for FP64) or from x[].
+// tracker before every evaluation (vf for FP32, vd for FP64; the
+// double-float evaluations split vd into their own copy vx) or from x[].
 #pragma once
 
 #include <type_traits>
@@ -86,14 +97,18 @@ struct GroupMem {
   cx<double>* vd;
   cx<double>* sb;  // holds L values of cx<R>
   cx<float>* vf;
-  cx<double>* eg;  // all-FP64 kernels: endgame samples [3][L] (previous sample,
+  cx<double>* eg;  // FP64-state kernels: endgame samples [3][L] (previous sample,
                    // its dx/ds, the last prediction), 16-byte aligned
+  cx<df>* vx;      // double-float kernels: the evaluator's double-float copy of
+                   // vd (L + extra entries), 16-byte aligned; nullptr otherwise
 };
 
 template <int L>
 __device__ __forceinline__ GroupMem make_group_mem(unsigned char* smem, int extra,
-                                                   int acc_bytes = 0, int eg_bytes = 0) {
-  unsigned char* b = smem + (threadIdx.x / L) * group_smem_bytes(L, extra, acc_bytes, eg_bytes);
+                                                   int acc_bytes = 0, int eg_bytes = 0,
+                                                   int vx = 0) {
+  unsigned char* b =
+      smem + (threadIdx.x / L) * group_smem_bytes(L, extra, acc_bytes, eg_bytes, vx);
   GroupMem m;
   m.pv = b;
   b += 32 * (L + 2);
@@ -101,6 +116,8 @@ __device__ __forceinline__ GroupMem make_group_mem(unsigned char* smem, int extr
   b += acc_bytes;
   m.eg = reinterpret_cast<cx<double>*>(b);
   b += eg_bytes;
+  m.vx = vx ? reinterpret_cast<cx<df>*>(b) : nullptr;
+  b += vx ? (L + extra) * 16 : 0;
   m.vd = reinterpret_cast<cx<double>*>(b);
   m.sb = reinterpret_cast<cx<double>*>(b + (L + extra) * 16);
   m.vf = reinterpret_cast<cx<float>*>(b + (L + extra) * 16 + L * 16);
@@ -127,12 +144,21 @@ __device__ __forceinline__ cx<double> hermite_at_zero(double wb, cx<double> xb, 
 }
 
 // Persistent loop of one lane group over the work items of a launch.
-// PROB::hom(inst) binds the evaluator to an instance.
-template <int N, int L, bool MIXED, class PROB>
+// PROB::hom(inst) binds the evaluator to an instance.  RE: the arithmetic of
+// the evaluation and the solve in the FP64-state kernels (MIXED = false):
+// double, or df for the double-float kernels, whose state, step control,
+// refinement residual and classification stay in FP64 exactly as in the
+// FP64 kernels.
+template <int N, int L, bool MIXED, class PROB, class RE = double>
 __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon& c,
                                             const Group& g, const GroupMem& sm) {
-  using R = typename std::conditional<MIXED, float, double>::type;
+  using R = typename std::conditional<MIXED, float, RE>::type;
   using HOM = decltype(prob.hom(0));
+  // double-float kernels: their Newton corrector takes its residual in FP64
+  // once a step of the path has been rejected (before that, from the
+  // double-float evaluation), as the mixed kernels' FP64-state phase does,
+  // and always with the endgame, whose samples need FP64 accuracy
+  constexpr bool XDF = std::is_same<R, df>::value;
   const DevSettings& s = c.s;
   cx<R>* sb = reinterpret_cast<cx<R>*>(sm.sb);
   const bool act = g.gl < N;
@@ -481,7 +507,7 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
         te = t1;
         ter = (R)t1;
         omt = (R)(1.0 - t1);
-        need64 = MIXED;
+        need64 = MIXED || (XDF && (res64 || eg_on));
         if (act) put_hi(xpd, !res64);
         if (act) sm.vf[g.gl] = cvt<float>(xpd);
       } else {
@@ -491,14 +517,14 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
       }
     } else {  // M_REFINE, M_COND: at the endpoint, t = 1
       need64 = (mode == M_REFINE);
-      if (act && (need64 || !MIXED)) put_hi(xd, false);
+      if (act && (need64 || !MIXED)) put_hi(xd, MIXED);
       if (act) sm.vf[g.gl] = cvt<float>(xd);
     }
     __syncwarp(g.mask);
     if constexpr (MIXED) {
       load_vec<N, float, float>(sm.vf, x);
     } else {
-      load_vec<N, double, double>(sm.vd, x);
+      load_vec<N, double, R>(sm.vd, x);
     }
 
     // ---- 2. row i of [dH/dx | rhs] and the solve
@@ -519,7 +545,7 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
         const int grow = g.gl & (HOM::ROWL - 1);
         row[N] = mk<R>((grow < N && grow == stage) ? R(1) : R(0), R(0));
       } else if (need64) {
-        if (MIXED && mode == M_NEWTON && !res64) {
+        if (MIXED && (mode == M_REFINE || !res64)) {
           cx<float> Hf;
           float sc;
           hom.template residual_df<false>(reinterpret_cast<const cdf*>(sm.vd), g.gl, te, Hf, sc);
@@ -551,7 +577,7 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
         // stage 1 at a sample point gives its dx/dt
         if (stage == 0 && eg_pending) {
           eg_pending = false;
-          if (sok && eg_sample(d)) {
+          if (sok && eg_sample(cvt<double>(d))) {
             eg_finish();
             continue;
           }
@@ -639,12 +665,21 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
           mode = M_DONE;
         } else {
           __syncwarp(g.mask);
-          if (act) put_hi(xd, false);
+          if (act) put_hi(xd, MIXED);
           __syncwarp(g.mask);
-          cx<double> H64;
-          double sc;
-          hom.template residual64<true>(sm.vd, g.gl, 1.0, 0.0, H64, sc);
-          const double r = (double)cabs2(cvt<float>(H64));
+          double r, sc;
+          if constexpr (MIXED) {  // double-float residual: its error is ~2^-48 sc
+            cx<float> Hf;
+            float scf;
+            hom.template residual_df<true>(reinterpret_cast<const cdf*>(sm.vd), g.gl, 1.0, Hf,
+                                           scf);
+            r = (double)cabs2(Hf);
+            sc = (double)scf;
+          } else {
+            cx<double> H64;
+            hom.template residual64<true>(sm.vd, g.gl, 1.0, 0.0, H64, sc);
+            r = (double)cabs2(cvt<float>(H64));
+          }
           const double bei = act ? (sc > 0.0 ? r / sc : r) : 0.0;
           be = gmaxf(g, (float)bei);
           if (!((double)be <= s.finite_tol)) {

@@ -29,7 +29,7 @@ HC_OK, HC_PENDING = 0, 1
 HC_ERR_INVALID, HC_ERR_OOM, HC_ERR_CUDA, HC_ERR_TIMEOUT = -1, -2, -3, -4
 HC_ERR_NUMERIC, HC_ERR_BUSY, HC_ERR_UNSUPPORTED = -5, -6, -7
 HC_TOTAL_DEGREE, HC_PARAMETER, HC_COEFFICIENT = 0, 1, 2
-HC_PREC_FP64, HC_PREC_MIXED = 0, 1
+HC_PREC_FP64, HC_PREC_MIXED, HC_PREC_DF = 0, 1, 2
 HC_DEVICE_PTRS, HC_BLOCKING_ADMIT = 1, 2
 PATH_FINITE, PATH_DIVERGED, PATH_FAIL_STEP, PATH_FAIL_MAXSTEPS = 1, 2, 3, 4
 PATH_FAIL_NAN, PATH_SINGULAR, PATH_FAIL_REFINE, PATH_REAL = 5, 6, 7, 0x80
@@ -49,7 +49,7 @@ class hc_settings(ctypes.Structure):
                 ("lanes", ctypes.c_int32), ("max_newton_ir", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("endgame", ctypes.c_int32),
                 ("eg_cmax", ctypes.c_int32), ("eg_samples", ctypes.c_int32),
-                ("eg_reserved", ctypes.c_int32), ("eg_s0", ctypes.c_double),
+                ("retrack_precision", ctypes.c_int32), ("eg_s0", ctypes.c_double),
                 ("eg_ratio", ctypes.c_double), ("eg_tol", ctypes.c_double)]
 
     def as_dict(self):
@@ -175,7 +175,11 @@ EXPORTED = ("hc_status_string", "hc_last_error", "hc_default_settings", "hc_crea
             "hc_measure_fma_peak", "hc_track_dense_noalloc", "hc_server_default_config",
             "hc_server_create", "hc_server_submit", "hc_server_wait", "hc_server_stats",
             "hc_autotune", "hc_plan_create", "hc_plan_run", "hc_set_memory_cap",
-            "hc_batched_solve", "hc_monodromy_solve", "hc_autotune_cached")
+            "hc_batched_solve", "hc_monodromy_solve", "hc_autotune_cached", "hc_evaluate")
+
+_lib.hc_evaluate.restype = ctypes.c_int32
+_lib.hc_evaluate.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int64, _P, _P, _P,
+                             _P, _P, _P]
 
 
 def problem_query(problem: int) -> dict:
@@ -481,6 +485,27 @@ class Problem:
         b.be_out = _addr(be_out)
         return b, dict(x=x_out, status=status_out, steps=steps_out, be=be_out, coef=coef, p1=p1,
                        path_ids=path_ids)
+
+    def evaluate(self, x, t, instance=None, coef=None, p1=None, precision=HC_PREC_FP64):
+        """H, dH/dx, dH/dt of the homotopy at points x [k][n] and times t [k]
+        with the device evaluator (hc_evaluate); instance [k] indexes the rows
+        of coef (total degree; None: the problem's coefficients) or p1
+        (parameter families).  Returns (H [k][n], Hx [k][n][n], Ht [k][n])."""
+        x = _host(np.atleast_2d(x), np.complex128)
+        k = x.shape[0]
+        t = _host(np.broadcast_to(np.asarray(t, np.float64), (k,)), np.float64)
+        inst = _host(np.zeros(k) if instance is None else instance, np.int64)
+        data = p1 if self.kind != HC_TOTAL_DEGREE else coef
+        if data is not None:
+            data = _host(np.atleast_2d(data), np.complex128)
+        n_inst = 1 if data is None else data.shape[0]
+        H = np.zeros((k, self.n), np.complex128)
+        Hx = np.zeros((k, self.n, self.n), np.complex128)
+        Ht = np.zeros((k, self.n), np.complex128)
+        _check(_lib.hc_evaluate(self.h, int(precision), n_inst, _addr(data) if data is not None
+                                else None, k, _addr(inst), _addr(x), _addr(t), _addr(H),
+                                _addr(Hx), _addr(Ht)), "hc_evaluate")
+        return H, Hx, Ht
 
     def track(self, n_instances=1, coef=None, p1=None, stream=None, device_out=None,
               x_out=None, status_out=None, steps_out=None, be_out=None, device=False,

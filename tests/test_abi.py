@@ -44,6 +44,7 @@ def test_default_settings_and_strings(hc):
     s = hc.default_settings()
     assert s.dt_min == 1e-6 and s.dt_max == 0.05 and s.max_newton == 3
     assert s.precision == hc.HC_PREC_MIXED and s.newton_tol == 1e-8
+    assert s.retrack_precision == hc.HC_PREC_DF
     assert hc._lib.hc_status_string(hc.HC_ERR_INVALID) == b"invalid argument"
     assert hc._lib.hc_status_string(12345) == b"unknown status"
 
@@ -112,7 +113,8 @@ def test_null_handles_are_rejected(hc):
 
 @pytest.mark.parametrize("field,value", [("max_newton_ir", 0), ("max_newton_ir", 33),
                                          ("block_threads", 16), ("block_threads", 256),
-                                         ("lanes", 16), ("endgame", 2), ("eg_reserved", 1)])
+                                         ("lanes", 16), ("endgame", 2), ("retrack_precision", 1),
+                                         ("retrack_precision", 3), ("precision", 3)])
 def test_create_problem_rejects_bad_iteration_limits(hc, field, value):
     from paper_2112_03444_gb300 import inputs
     d, keep = _desc(hc, inputs.dense_system(2, 2, 0))

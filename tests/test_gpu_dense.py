@@ -37,7 +37,7 @@ def _oracle(base, coef, gamma, **kw):
     return oracle.OracleProblem(base, gamma=gamma, coef=coef).track(**kw)
 
 
-@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("precision", [0, 1, 2], ids=["fp64", "mixed", "df"])
 @pytest.mark.parametrize("n,d,seeds", [
     (6, 2, list(range(10))),        # the n = 6 quadratic workload, 10 systems
     (1, 2, [3, 4]), (2, 2, [5]), (3, 2, [6, 7]), (5, 2, [8]), (7, 2, [9]),
@@ -123,10 +123,12 @@ def _golden():
     return json.load(open(path))
 
 
+@pytest.mark.parametrize("retrack", [2, 0], ids=["retrack_df", "retrack_fp64"])
 @pytest.mark.parametrize("ci", range(5), ids=["q8", "q10", "q12", "c6", "c8"])
-def test_dense_sweep_matches_oracle_golden(hc, ci):
+def test_dense_sweep_matches_oracle_golden(hc, ci, retrack):
     """The benchmarked sweep (16 systems per size class, mixed precision, the
-    bench's seeds) against the oracle's stored outcome on every path
+    bench's seeds; the last re-tracking tier in double-float or FP64
+    arithmetic) against the oracle's stored outcome on every path
     (tests/golden/dense_sweep_oracle.json):
       - every path the oracle ends at a finite root, the GPU does too;
       - within every system the GPU's finite roots are pairwise distinct
@@ -138,7 +140,7 @@ def test_dense_sweep_matches_oracle_golden(hc, ci):
     w = inputs.dense_sweep(0)[ci]
     g = _golden()["classes"][ci]
     assert (g["n"], g["d"]) == (w["n"], w["d"])
-    pr = hc.Problem(w["base"], gamma=w["gamma"])
+    pr = hc.Problem(w["base"], gamma=w["gamma"], settings=dict(retrack_precision=retrack))
     b = pr.track(n_instances=len(w["seeds"]), coef=w["coefs"]).wait()
     P = w["d"] ** w["n"]
     for s, gs in enumerate(g["systems"]):

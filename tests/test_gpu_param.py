@@ -70,7 +70,7 @@ def _check(hc, system, p0, p1s, start, precision, symmetries=(), kind=None):
     return b
 
 
-@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("precision", [0, 1, 2], ids=["fp64", "mixed", "df"])
 @pytest.mark.parametrize("n,d,seed", [(1, 3, 71), (3, 2, 72), (4, 2, 73), (2, 3, 74), (5, 2, 75)])
 def test_dense_parameter_family_matches_oracle(hc, n, d, seed, precision):
     from paper_2112_03444_gb300 import inputs
@@ -81,7 +81,7 @@ def test_dense_parameter_family_matches_oracle(hc, n, d, seed, precision):
     _check(hc, sys_, p0, [p1, p1b], start, precision)
 
 
-@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("precision", [0, 1, 2], ids=["fp64", "mixed", "df"])
 def test_triangulation_matches_oracle(hc, precision):
     from paper_2112_03444_gb300 import inputs
     fam = inputs.triangulation_family(4)
@@ -99,7 +99,7 @@ def _family(name):
 
 
 @pytest.mark.parametrize("sym", [False, True], ids=["all_starts", "orbit_reps"])
-@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("precision", [0, 1, 2], ids=["fp64", "mixed", "df"])
 @pytest.mark.parametrize("name", ["p3p", "triangulation2", "pose5_depth"])
 def test_more_vision_problems_match_oracle(hc, name, precision, sym):
     """The other formulations of Sec. 4: P3P in the depths (3 x 3), two-view
@@ -114,7 +114,7 @@ def test_more_vision_problems_match_oracle(hc, name, precision, sym):
            symmetries=fam.sign_masks if sym else ())
 
 
-@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("precision", [0, 1, 2], ids=["fp64", "mixed", "df"])
 @pytest.mark.parametrize("name", ["triangulation4", "p3p", "pose5_depth"])
 def test_coefficient_interpolation_matches_oracle(hc, name, precision):
     """The coefficient-interpolation homotopy of Sec. 6 (HC_COEFFICIENT: the
@@ -314,7 +314,7 @@ EDGE_CASES = {
 }
 
 
-@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("precision", [0, 1, 2], ids=["fp64", "mixed", "df"])
 @pytest.mark.parametrize("case", sorted(EDGE_CASES))
 def test_edge_cases_match_oracle_exactly(hc, case, precision):
     """The method's degenerate cases (paths to infinity, a double root, real
@@ -338,7 +338,7 @@ def test_edge_cases_match_oracle_exactly(hc, case, precision):
     assert oracle.status_counts(td["status"]) == oracle.status_counts(ref["status"])
 
 
-@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("precision", [0, 1, 2], ids=["fp64", "mixed", "df"])
 def test_path_to_infinity_is_diverged_like_the_oracle(hc, precision):
     """F(x; p) = (p x - y, p y - 1) has the single root y = 1/p, x = 1/p^2;
     from p = 1 to p = 0 the path leaves every bounded set like (1-t)^-2 and
@@ -368,14 +368,14 @@ ENDGAME_CASES = {
 }
 
 
-@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("precision", [0, 1, 2], ids=["fp64", "mixed", "df"])
 @pytest.mark.parametrize("case", sorted(ENDGAME_CASES))
 def test_endgame_matches_oracle(hc, case, precision):
     """The power-series endgame (settings.endgame = 1) against the oracle's
     own endgame: statuses path by path (singular endpoints of multiple roots
     included) and the finite and singular endpoints within 1e-8.  In mixed
-    precision the endgame runs in the all-FP64 re-tracking tier, which gets
-    the paths that fail near their end."""
+    precision the endgame runs in the last re-tracking tier (double-float
+    arithmetic by default), which gets the paths that fail near their end."""
     from paper_2112_03444_gb300 import inputs
     n, polys, gseed = ENDGAME_CASES[case]
     fam, p0, p1, start = inputs.total_degree_as_parameter_family(_poly(n, polys),

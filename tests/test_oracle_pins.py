@@ -515,3 +515,26 @@ def test_endgame_makes_no_prediction_for_paths_to_infinity():
     sys_ = poly_system(2, [{(1, 1): 1, (0, 0): -1}, {(1, 1): 1, (1, 0): 1, (0, 0): -2}])
     r = OracleProblem(sys_, gamma=inputs.unit_gamma(9)).track(settings=dict(endgame=1))
     assert oracle.status_counts(r["status"])["finite"] == 1
+
+
+def test_oracle_jacobian_matches_the_paper_term_tuples():
+    """Sec. 6 worked example: the oracle's dH/dx entries (1,1) and (2,1) of
+    the example family equal the paper's printed tuple representations of A
+    and B evaluated at a(t) = (1 - t) a(0) + t a(1) (x3 = 1), at random
+    points; and the tuple padded with s = 0 adds nothing."""
+    import sec6_example as ex
+    tup = ex.tuples()
+    fam = ex.family()
+    p0, p1 = ex.parameters(1)
+    op = OracleProblem(fam, kind=KIND_PARAMETER, p0=p0, p1=p1)
+    rng = np.random.default_rng(7)
+    for _ in range(5):
+        x = rng.normal(size=2) + 1j * rng.normal(size=2)
+        t = float(rng.uniform())
+        a = (1 - t) * p0 + t * p1
+        _, Hx, _ = op.eval(x, t)
+        A = ex.tuple_value(tup["A"], a, x)
+        B = ex.tuple_value(tup["B"], a, x)
+        assert abs(Hx[0, 0] - A) <= 1e-13 * (1 + abs(A)), (Hx[0, 0], A)
+        assert abs(Hx[1, 0] - B) <= 1e-13 * (1 + abs(B)), (Hx[1, 0], B)
+        assert ex.tuple_value(tup["B"][2:], a, x) == 0

@@ -26,7 +26,7 @@ def env():
     return torch, hc, inputs
 
 
-def _compare(env, n, d, seeds):
+def _compare(env, n, d, seeds, settings=None):
     torch, hc, inputs = env
     dev = torch.device("cuda")
     base, coefs = inputs.dense_batch(n, d, seeds)
@@ -34,7 +34,7 @@ def _compare(env, n, d, seeds):
     I = len(seeds)
     P = d ** n
     # allocating entry point
-    pr = hc.Problem(base, gamma=gamma)
+    pr = hc.Problem(base, gamma=gamma, settings=settings)
     ref = pr.track(n_instances=I, coef=coefs).wait()
     # allocation-free entry point, device buffers owned by the caller
     cf = torch.from_numpy(np.ascontiguousarray(coefs)).to(dev)
@@ -59,6 +59,33 @@ def _compare(env, n, d, seeds):
 def test_no_alloc_matches_allocating_entry_point_twice(env):
     _compare(env, 6, 2, [201, 202, 203])
     _compare(env, 3, 3, [204, 205])
+
+
+def test_no_alloc_all_fp64(env):
+    # precision FP64: one all-FP64 tracking launch, no escalation lists
+    _, hc, _ = env
+    _compare(env, 4, 2, [211, 212], dict(precision=hc.HC_PREC_FP64))
+
+
+def test_no_alloc_mixed_without_escalation(env):
+    # mixed without re-tracking: the escalation, duplicate and restart
+    # buffers are absent and failed FP32 paths stay failed
+    _, hc, _ = env
+    _compare(env, 4, 2, [213, 214], dict(escalate=0))
+    _compare(env, 3, 3, [215, 216], dict(escalate=0))
+
+
+def test_no_alloc_double_float(env):
+    # precision DF: the double-float kernel (one path per warp) and its table
+    _, hc, _ = env
+    _compare(env, 4, 2, [217, 218], dict(precision=hc.HC_PREC_DF))
+    _compare(env, 3, 3, [219], dict(precision=hc.HC_PREC_DF))
+
+
+def test_no_alloc_fp64_last_tier(env):
+    # mixed with the last re-tracking tier in FP64 rather than double-floats
+    _, hc, _ = env
+    _compare(env, 6, 2, [220, 221], dict(retrack_precision=hc.HC_PREC_FP64))
 
 
 def test_no_alloc_rejects_batches_beyond_its_scratch(env):
