@@ -76,8 +76,9 @@ def test_family_evaluation_matches_oracle(hc, name, kind, precision):
     p1 = rng.normal(size=(3, P)) + 1j * rng.normal(size=(3, P))
     hk = hc.HC_PARAMETER if kind == KIND_PARAMETER else hc.HC_COEFFICIENT
     pr = hc.Problem(fam.system, kind=hk, p0=z["p0"], start=z["start"][:4])
-    x = z["start"][:24] + 0.1 * (rng.normal(size=(24, fam.system.n)) +
-                                  1j * rng.normal(size=(24, fam.system.n)))
+    S = len(z["start"])
+    x = z["start"][np.arange(24) % S] + 0.1 * (rng.normal(size=(24, fam.system.n)) +
+                                                1j * rng.normal(size=(24, fam.system.n)))
     t = rng.uniform(size=24)
     inst = np.arange(24) % 3
     H, Hx, Ht = pr.evaluate(x, t, instance=inst, p1=p1, precision=precision)
