@@ -468,6 +468,12 @@ def run_gpu(args):
                              fp64_requests=0)[0]
         serving_tf = serve_rows(hc, [args.serve_rate / 4], args.serve_duration, trifocal=True,
                                 fp64_requests=0)[0]
+    # continuous admission into a resident launch against the batch server,
+    # single-kind Poisson streams at rising rates (the saturation knee)
+    admission = None
+    if not args.no_serving_leg and not args.no_admission_leg:
+        admission = stream_rows(hc, [float(r) for r in args.admission_rates.split(",")],
+                                args.admission_duration)
 
     line = dict(
         metric=METRIC, value=matched_all / (ms * 1e-3), unit="paths/s",
@@ -508,6 +514,7 @@ def run_gpu(args):
                                 "counters"),
         serving=serving,
         serving_with_trifocal=serving_tf,
+        admission=admission,
         batched_solve=solve,
         parameter_workloads=params,
         clocks=clocks,
@@ -789,6 +796,76 @@ def serve_run(hc, probs, rate, count, streams, max_batch, seed):
                 p50_ms_by_kind={k: float(np.percentile(v, 50)) for k, v in sorted(per_kind.items())})
 
 
+def stream_run(hc, problem, gen, rate, count, slots, seed, cap_s=20.0):
+    """Poisson arrivals of `count` requests of one kind at `rate` per second
+    into a resident launch (hc.Stream, continuous admission): one host
+    thread submits each request at its arrival time and collects finished
+    ones in between; latency = arrival to collection.  Stops after cap_s
+    (the requests collected by then are reported)."""
+    rng = np.random.default_rng([seed, int(rate), 7])
+    arrive = np.cumsum(rng.exponential(1.0 / rate, size=count))
+    payload = [gen(20_000 + j) for j in range(count)]
+    st = hc.Stream(problem, slots=slots, idle_us=20000)
+    kind = problem.kind
+    pending, lat, paths, finite = [], [], 0, 0
+    j = 0
+    t0 = time.perf_counter()
+    while (j < count or pending) and time.perf_counter() - t0 < cap_s:
+        now = time.perf_counter() - t0
+        if j < count and now >= arrive[j]:
+            try:
+                tk = st.submit(p1=payload[j]) if kind != hc.HC_TOTAL_DEGREE else \
+                    st.submit(coef=payload[j])
+                pending.append((j, tk))
+                j += 1
+                continue
+            except hc.HCError:  # every slot in use: collect below
+                pass
+        if pending:
+            jj, tk = pending[0]
+            r = st.poll(tk, timeout_us=0 if j < count else 200)
+            if r is not None:
+                pending.pop(0)
+                lat.append((time.perf_counter() - t0 - arrive[jj]) * 1e3)
+                paths += len(r[1])
+                finite += int(np.sum((r[1] & 0x7F) == hc.PATH_FINITE))
+                continue
+        if j < count:
+            time.sleep(max(0.0, min(50e-6, arrive[j] - (time.perf_counter() - t0))))
+    wall = time.perf_counter() - t0
+    st.close()
+    done = len(lat)
+    return dict(offered_per_s=rate, requests=count, completed=done, systems_per_s=done / wall,
+                paths_per_s=finite / wall, p50_ms=float(np.percentile(lat, 50)) if lat else None,
+                p99_ms=float(np.percentile(lat, 99)) if lat else None,
+                recovery=finite / paths if paths else None)
+
+
+def stream_rows(hc, rates, duration):
+    """Continuous admission against the batch server on single-kind Poisson
+    streams: dense quadratics n = 8 (256 paths per request, almost no
+    re-tracking) at the given rates, and 4-view triangulation (296 paths, a
+    quarter of them re-tracked) at the lowest rate."""
+    z = np.load(os.path.join(START_DIR, "triangulation4.npz"))
+    kinds = [("triangulation4", hc.Problem(inputs.triangulation_family(4).system,
+                                           kind=hc.HC_PARAMETER, p0=z["p0"], start=z["start"]),
+              lambda s: inputs.triangulation_scene(s)[0]),
+             ("quad8", hc.Problem(inputs.dense_system(8, 2, 708), gamma=inputs.unit_gamma(708)),
+              lambda s: inputs.dense_coefficients(8, 2, s).reshape(-1))]
+    rows = []
+    for name, pr, gen in kinds[::-1]:
+        for rate in (rates if name == "quad8" else rates[:1]):
+            count = int(max(50, min(rate * duration, 20000)))
+            rows.append(dict(kind=name, form="resident launch (hc_stream)",
+                             **stream_run(hc, pr, gen, rate, count, 256, 3)))
+            rows.append(dict(kind=name, form="batch server (hc_server)",
+                             **{k: v for k, v in serve_run(hc, [(name, pr, gen)], rate, count, 4,
+                                                           64, 3).items()
+                                if k not in ("batches", "max_inflight_batches",
+                                             "p50_ms_by_kind")}))
+    return rows
+
+
 def serve_rows(hc, rates, duration, trifocal=True, fp64_requests=0):
     mixed = serving_problems(hc, hc.HC_PREC_MIXED, trifocal)
     rows = []
@@ -831,6 +908,9 @@ def main():
     ap.add_argument("--no-serving-leg", action="store_true")
     ap.add_argument("--no-solve-leg", action="store_true")
     ap.add_argument("--no-param-legs", action="store_true")
+    ap.add_argument("--no-admission-leg", action="store_true")
+    ap.add_argument("--admission-rates", default="400,2000,8000")
+    ap.add_argument("--admission-duration", type=float, default=1.0)
     ap.add_argument("--tri-instances", type=int, default=10_000)
     ap.add_argument("--trifocal-instances", type=int, default=64)
     ap.add_argument("--serve-rate", type=float, default=400.0,

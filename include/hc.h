@@ -318,6 +318,45 @@ typedef struct hc_problem_info {
 hc_status hc_problem_query(const hc_problem* p, hc_problem_info* out);
 
 /*
+ * Continuous admission (not in the paper, which tracks the paths of one
+ * system per run; serving systems as they arrive is this library's): a
+ * stream holds `slots` instance slots of a problem
+ * on the device and a resident tracking launch whose lane groups take the
+ * next path of the next submitted instance as soon as they free up, instead
+ * of each batch waiting for a launch of its own.  The launch polls a
+ * host-published counter in mapped memory with sleeps between polls and
+ * ends after idle_us without work (the next submit or poll starts it
+ * again); a slot whose paths are done gets the re-tracking tiers of the
+ * mixed pipeline on a side stream, as hc_track_batch runs them for a batch.
+ * Results are those of hc_track_batch on the same inputs, path for path.
+ * One thread at a time may use a stream.  Sign symmetries are not applied
+ * (every start is tracked).
+ *   hc_stream_create  slots 1..4096, idle_us 1..1e7; allocates the ring
+ *                     (inputs, tables, outputs, lists per slot) and mapped
+ *                     control words; the problem must outlive the stream.
+ *   hc_stream_submit  inputs as one instance of hc_batch_desc (coef [T] for
+ *                     total degree, NULL: the problem's own; p1 [n_params]
+ *                     otherwise), host memory; copies and stages them,
+ *                     publishes the instance's paths and returns its ticket
+ *                     (0, 1, 2, ...).  HC_ERR_BUSY when the ticket's slot
+ *                     (ticket mod slots) still holds an uncollected request.
+ *   hc_stream_poll    waits up to timeout_us (< 0: no limit, 0: check once)
+ *                     for ticket's results and copies them to the host
+ *                     buffers (x_out [paths][n] complex, status_out
+ *                     [paths], optional steps_out [paths][3] and be_out
+ *                     [paths]); HC_ERR_TIMEOUT if not done yet; the slot is
+ *                     free again after a successful poll.
+ *   hc_stream_destroy stops the resident launch (its groups leave after
+ *                     their current paths), waits for it and frees the stream.
+ */
+typedef struct hc_stream hc_stream;
+hc_status hc_stream_create(hc_problem* p, int32_t slots, int64_t idle_us, hc_stream** out);
+hc_status hc_stream_submit(hc_stream* s, const double* inputs, int64_t* ticket);
+hc_status hc_stream_poll(hc_stream* s, int64_t ticket, int64_t timeout_us, double* x_out,
+                         uint8_t* status_out, int32_t* steps_out, double* be_out);
+hc_status hc_stream_destroy(hc_stream* s);
+
+/*
  * Sec. 6 ("Parallel Evaluations of the Jacobian and Vectors": dH/dx, dH/dt
  * and H evaluated together from the terms of the equations) and Sec. 3 (H):
  * evaluate the problem's homotopy at n_points points with the tracker's own

@@ -2535,3 +2535,545 @@ extern "C" hc_status hc_evaluate(const hc_problem* p, int32_t precision, int32_t
   if (cur != p->device) cudaSetDevice(cur);
   return rc;
 }
+
+// ------------------------------------------------------------------ hc_stream
+// Continuous admission into a running launch: a ring of instance slots in
+// device memory, a resident tracking launch that takes the next path of the
+// next published slot whenever one of its lane groups frees up, and per slot
+// the re-tracking tiers of enqueue_compute (duplicate check, high-precision
+// residual re-track, last tier) once the slot's paths are done.
+struct hc_stream {
+  uint32_t magic = 0x48435354u;  // "HCST"
+  hc_problem* p = nullptr;
+  int S = 0;                     // slots
+  int64_t paths = 0;
+  int64_t idle_ns = 0;
+  int64_t next_ticket = 0;
+  bool launched = false;
+  int grid = 0, threads = 0;
+  size_t smem = 0;
+  hc::KernelRef kt{}, kr{}, kl{};  // tracking, re-tracking, last tier
+  cudaStream_t ks = nullptr, cs = nullptr;  // resident launch, copies and staging
+  std::vector<cudaStream_t> es;             // re-tracking streams, slot k on es[k % size]
+  cudaEvent_t kdone = nullptr;
+  std::vector<cudaEvent_t> edone;
+  std::vector<int> state;        // 0 free, 1 tracking, 2 escalating
+  std::vector<int64_t> ticket;   // ticket held by each slot
+  // pinned host words: completion flags (mapped, written by the device) and
+  // the sources of the tail and stop copies
+  unsigned long long* h_flag = nullptr;
+  unsigned long long* h_tailv = nullptr;  // [S] tail value published with each slot
+  unsigned int* h_stopv = nullptr;
+  unsigned long long* d_flag = nullptr;   // device view of h_flag
+  unsigned long long* d_tail = nullptr;   // device memory
+  unsigned int* d_stop = nullptr;         // device memory
+  // device ring
+  std::vector<void*> mem;
+  unsigned long long* d_queue = nullptr;
+  unsigned int* d_done = nullptr;
+  unsigned long long* d_esc = nullptr;  // [S] per-slot counters
+  unsigned long long* d_dup = nullptr;  // [S]
+  unsigned long long* d_sctl = nullptr; // [S][8] per-slot queues and step sums
+  double2* d_in = nullptr;              // [S][T] coefficients or [S][P] parameters
+  double2 *E = nullptr, *D64 = nullptr;
+  hc::cdf* Edf = nullptr;
+  float2* D32 = nullptr;
+  float4* Ddf = nullptr;
+  double2* dc = nullptr;
+  float2* dcf = nullptr;
+  hc::cdf* dcdf = nullptr;
+  double2* x = nullptr;
+  uint8_t* st = nullptr;
+  int32_t* steps = nullptr;
+  double* be = nullptr;
+  int64_t* esc_list = nullptr;
+  int64_t* dup_list = nullptr;
+  double* t_io = nullptr;
+  float2* x32 = nullptr;
+};
+
+namespace {
+constexpr uint32_t kStreamMagic = 0x48435354u;
+
+void free_stream(hc_stream* s) {
+  if (s->ks) cudaStreamSynchronize(s->ks);
+  for (cudaStream_t e : s->es)
+    if (e) cudaStreamSynchronize(e);
+  if (s->cs) cudaStreamSynchronize(s->cs);
+  for (void* q : s->mem) cudaFree(q);
+  for (cudaEvent_t e : s->edone)
+    if (e) cudaEventDestroy(e);
+  if (s->kdone) cudaEventDestroy(s->kdone);
+  if (s->ks) cudaStreamDestroy(s->ks);
+  if (s->cs) cudaStreamDestroy(s->cs);
+  for (cudaStream_t e : s->es)
+    if (e) cudaStreamDestroy(e);
+  if (s->h_flag) cudaFreeHost(s->h_flag);
+  delete s;
+}
+
+// the launch descriptor common to the resident launch and a slot's tiers
+hc::LaunchCommon stream_common(const hc_stream* s) {
+  hc::LaunchCommon c;
+  std::memset(&c, 0, sizeof(c));
+  c.s = dev_settings(s->p->s);
+  c.paths = s->paths;
+  return c;
+}
+}  // namespace
+
+extern "C" hc_status hc_stream_create(hc_problem* p, int32_t slots, int64_t idle_us,
+                                      hc_stream** out) {
+  if (!p || p->magic != kProblemMagic || !out || slots < 1 || slots > 4096 || idle_us < 1 ||
+      idle_us > 10000000) {
+    set_err("hc_stream_create: invalid arguments (slots 1..4096, idle_us 1..1e7)");
+    return HC_ERR_INVALID;
+  }
+  *out = nullptr;
+  const int prec = p->s.precision;
+  const bool mixed = prec == HC_PREC_MIXED;
+  const int n = p->n;
+  hc_stream* s = new hc_stream();
+  s->p = p;
+  s->S = slots;
+  s->paths = p->paths;
+  s->idle_ns = idle_us * 1000;
+  s->state.assign(slots, 0);
+  s->ticket.assign(slots, -1);
+  s->edone.assign(slots, nullptr);
+  if (p->terms) {
+    s->kt = hc::term_kernel(n, prec, mixed ? p->s.lanes : 0);
+    s->kr = s->kt;
+    s->kl = hc::term_kernel(n, hc::last_tier_precision(p->s), 0);
+  } else {
+    s->kt = hc::dense_kernel(p->deg, n, prec, mixed ? p->s.lanes : 0);
+    if (!s->kt.fn) s->kt = hc::dense_kernel(p->deg, n, prec, 0);
+    s->kr = retrack_kernel(p->deg, n, HC_PREC_MIXED);
+    s->kl = retrack_kernel(p->deg, n, hc::last_tier_precision(p->s));
+  }
+  if (!s->kt.fn || !s->kr.fn || !s->kl.fn) {
+    delete s;
+    set_err("hc_stream_create: no kernel for this problem shape");
+    return HC_ERR_UNSUPPORTED;
+  }
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != p->device && cudaSetDevice(p->device) != cudaSuccess) {
+    delete s;
+    set_err("hc_stream_create: cudaSetDevice failed");
+    return HC_ERR_CUDA;
+  }
+  auto fail = [&](hc_status rc, const char* what) {
+    set_err(std::string("hc_stream_create: ") + what);
+    free_stream(s);
+    if (cur != p->device) cudaSetDevice(cur);
+    return rc;
+  };
+  auto dalloc = [&](size_t bytes, auto** q) -> bool {
+    void* v = nullptr;
+    if (cudaMalloc(&v, std::max<size_t>(bytes, 16)) != cudaSuccess) return false;
+    s->mem.push_back(v);
+    *q = reinterpret_cast<std::remove_pointer_t<decltype(q)>>(v);
+    return cudaMemset(v, 0, std::max<size_t>(bytes, 16)) == cudaSuccess;
+  };
+  if (cudaStreamCreateWithFlags(&s->ks, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->kdone, cudaEventDisableTiming) != cudaSuccess)
+    return fail(HC_ERR_CUDA, "stream or event creation failed");
+  // the slots' re-tracking tiers overlap on several streams (one stream
+  // would queue every slot's latency-bound tail behind the previous one)
+  s->es.assign(std::min(slots, 32), nullptr);
+  for (auto& e : s->es)
+    if (cudaStreamCreateWithFlags(&e, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(HC_ERR_CUDA, "stream creation failed");
+  for (int k = 0; k < slots; ++k)
+    if (cudaEventCreateWithFlags(&s->edone[k], cudaEventDisableTiming) != cudaSuccess)
+      return fail(HC_ERR_CUDA, "event creation failed");
+  // pinned host words: one completion flag per slot (mapped), the tail value
+  // of each slot's publication and the stop word (copy sources)
+  void* h = nullptr;
+  const size_t hbytes = 16 * (size_t)slots + 16;
+  if (cudaHostAlloc(&h, hbytes, cudaHostAllocMapped) != cudaSuccess)
+    return fail(HC_ERR_OOM, "cudaHostAlloc failed");
+  std::memset(h, 0, hbytes);
+  s->h_flag = static_cast<unsigned long long*>(h);
+  s->h_tailv = s->h_flag + slots;
+  s->h_stopv = reinterpret_cast<unsigned int*>(s->h_tailv + slots);
+  void* dh = nullptr;
+  if (cudaHostGetDevicePointer(&dh, h, 0) != cudaSuccess)
+    return fail(HC_ERR_CUDA, "cudaHostGetDevicePointer failed");
+  s->d_flag = static_cast<unsigned long long*>(dh);
+  const int64_t ring = (int64_t)slots * s->paths;
+  const size_t in_per = p->terms ? (size_t)p->P : (size_t)p->T;
+  bool ok = dalloc(8, &s->d_queue) && dalloc(8, &s->d_tail) && dalloc(8, &s->d_stop) &&
+            dalloc(4 * (size_t)slots, &s->d_done) &&
+            dalloc(8 * (size_t)slots, &s->d_esc) && dalloc(8 * (size_t)slots, &s->d_dup) &&
+            dalloc(64 * (size_t)slots, &s->d_sctl) &&
+            dalloc(sizeof(double2) * in_per * slots, &s->d_in) &&
+            dalloc(sizeof(double2) * n * ring, &s->x) && dalloc((size_t)ring, &s->st) &&
+            dalloc(sizeof(int32_t) * 3 * ring, &s->steps) && dalloc(sizeof(double) * ring, &s->be) &&
+            dalloc(sizeof(int64_t) * ring, &s->esc_list) &&
+            dalloc(sizeof(int64_t) * ring, &s->dup_list) && dalloc(sizeof(double) * ring, &s->t_io) &&
+            dalloc(sizeof(float2) * n * ring, &s->x32);
+  if (ok && !p->terms) {
+    const int last = hc::last_tier_precision(p->s);
+    const size_t es = (size_t)p->Estride * slots, ds = (size_t)p->Dstride * slots;
+    ok = dalloc(sizeof(double2) * es, &s->E) &&
+         (!mixed || (dalloc(sizeof(hc::cdf) * es, &s->Edf) && dalloc(sizeof(float2) * ds, &s->D32))) &&
+         ((prec != HC_PREC_FP64 && !(mixed && last == HC_PREC_FP64)) ||
+          dalloc(sizeof(double2) * ds, &s->D64)) &&
+         ((prec != HC_PREC_DF && !(mixed && last == HC_PREC_DF)) ||
+          dalloc(sizeof(float4) * ds, &s->Ddf));
+  }
+  if (ok && p->terms && p->coef_mode) {
+    const size_t e = (size_t)p->TT * p->L * slots;
+    ok = dalloc(sizeof(double2) * e, &s->dc) && dalloc(sizeof(float2) * e, &s->dcf) &&
+         dalloc(sizeof(hc::cdf) * e, &s->dcdf);
+  }
+  if (!ok) return fail(HC_ERR_OOM, "device allocation failed");
+  // the resident launch leaves a quarter of the SMs' block slots to the
+  // staging and re-tracking launches that run beside it
+  s->threads = std::max(main_threads(p->s), s->kt.lanes);
+  s->smem = p->terms ? (size_t)hc::block_smem_bytes(s->kt.lanes, p->extra, s->kt.acc_bytes,
+                                                     s->threads, s->kt.eg_bytes, s->kt.vx)
+                     : (size_t)hc::block_smem_bytes(s->kt.lanes, s->kt.extra, 0, s->threads,
+                                                    s->kt.eg_bytes, s->kt.vx);
+  if (s->smem > 48 * 1024 &&
+      cudaFuncSetAttribute(s->kt.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)s->smem) != cudaSuccess)
+    return fail(HC_ERR_CUDA, "shared memory attribute");
+  const Occ o = occupancy(s->kt.fn, s->smem, s->threads);
+  s->grid = std::max(o.sms, (o.blocks * o.sms * 3) / 4);
+  if (cur != p->device) cudaSetDevice(cur);
+  *out = s;
+  return HC_OK;
+}
+
+namespace {
+// Tracking arguments for slot `slot` viewed as a one-instance batch (slot <
+// 0: the whole ring, for the resident launch).
+hc::DenseArgs stream_dense_args(const hc_stream* s, int64_t slot) {
+  const hc_problem* p = s->p;
+  const int64_t o = slot < 0 ? 0 : slot;
+  hc::DenseArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.c = stream_common(s);
+  a.D32 = s->D32 ? (const cx<float>*)(s->D32 + o * p->Dstride) : nullptr;
+  a.D64 = s->D64 ? (const cx<double>*)(s->D64 + o * p->Dstride) : nullptr;
+  a.Ddf = s->Ddf ? (const cx<hc::df>*)(s->Ddf + o * p->Dstride) : nullptr;
+  a.E = (const cx<double>*)(s->E + o * p->Estride);
+  a.Edf = s->Edf ? s->Edf + o * p->Estride : nullptr;
+  a.Dstride = p->Dstride;
+  a.Estride = p->Estride;
+  a.gamma = cx<double>{p->gamma[0], p->gamma[1]};
+  a.gamma32 = cx<float>{(float)p->gamma[0], (float)p->gamma[1]};
+  a.gammadf = hc::split_cdf_host(p->gamma[0], p->gamma[1]);
+  return a;
+}
+
+hc::TermArgs stream_term_args(const hc_stream* s, int64_t slot) {
+  const hc_problem* p = s->p;
+  const int64_t o = slot < 0 ? 0 : slot;
+  hc::TermArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.c = stream_common(s);
+  a.rec = p->d_rec;
+  a.s64 = p->d_s64;
+  a.sdf = p->d_sdf;
+  a.TT = p->TT;
+  a.P = p->P;
+  a.ls = p->L;
+  a.extra = p->extra;
+  a.p0 = p->d_p0;
+  a.p1 = s->d_in + o * p->P;
+  a.start = p->d_start;
+  if (p->coef_mode) {
+    const int64_t e = (int64_t)p->TT * p->L * o;
+    a.coef_mode = 1;
+    a.c0 = p->d_c0;
+    a.c0f = p->d_c0f;
+    a.c0df = p->d_c0df;
+    a.dc = s->dc + e;
+    a.dcf = s->dcf + e;
+    a.dcdf = s->dcdf + e;
+  }
+  return a;
+}
+
+// outputs and re-tracking state of one slot (or the ring, slot < 0)
+void stream_outputs(const hc_stream* s, int64_t slot, hc::LaunchCommon& c) {
+  const int64_t o = (slot < 0 ? 0 : slot) * s->paths;
+  const int n = s->p->n;
+  const bool esc = s->p->s.precision == HC_PREC_MIXED && s->p->s.escalate;
+  c.x_out = reinterpret_cast<double*>(s->x + o * n);
+  c.status_out = s->st + o;
+  c.steps_out = s->steps + o * 3;
+  c.be_out = s->be + o;
+  if (esc) {
+    c.esc_list = s->esc_list + o;
+    c.dup_list = s->dup_list + o;
+    c.t_io = s->t_io + o;
+    c.x32_out = s->x32 + o * n;
+    c.esc_count = s->d_esc + (slot < 0 ? 0 : slot);
+    c.dup_count = s->d_dup + (slot < 0 ? 0 : slot);
+  }
+}
+
+bool stream_running(hc_stream* s) {
+  return s->launched && cudaEventQuery(s->kdone) == cudaErrorNotReady;
+}
+
+// (Re)launch the resident tracking launch if it is not running and a
+// published slot still has paths to claim.
+hc_status stream_kick(hc_stream* s) {
+  bool pending = false;
+  for (int k = 0; k < s->S; ++k)
+    if (s->state[k] == 1 &&
+        __atomic_load_n(&s->h_flag[k], __ATOMIC_ACQUIRE) != (unsigned long long)(s->ticket[k] / s->S + 1))
+      pending = true;
+  if (!pending || stream_running(s)) return HC_OK;
+  hc::LaunchCommon c = stream_common(s);
+  stream_outputs(s, -1, c);
+  c.queue = s->d_queue;
+  c.ring_items = (unsigned long long)s->S * s->paths;
+  c.ring_tail = s->d_tail;
+  c.ring_stop = s->d_stop;
+  c.ring_idle_ns = (unsigned long long)s->idle_ns;
+  c.ring_done = s->d_done;
+  c.ring_flag = s->d_flag;
+  void* argp;
+  hc::DenseArgs da;
+  hc::TermArgs ta;
+  if (s->p->terms) {
+    ta = stream_term_args(s, -1);
+    ta.c = c;
+    argp = &ta;
+  } else {
+    da = stream_dense_args(s, -1);
+    da.c = c;
+    argp = &da;
+  }
+  void* argv[] = {argp};
+  HC_CUDA(cudaLaunchKernel(s->kt.fn, dim3((unsigned)s->grid), dim3(s->threads), argv, s->smem,
+                           s->ks));
+  HC_CUDA(cudaEventRecord(s->kdone, s->ks));
+  s->launched = true;
+  return HC_OK;
+}
+}  // namespace
+
+namespace {
+// The re-tracking tiers of one slot whose tracking is complete (as
+// enqueue_compute runs them for a batch), then the slot's completion event.
+hc_status stream_escalate(hc_stream* s, int64_t slot) {
+  const hc_problem* p = s->p;
+  const bool esc = p->s.precision == HC_PREC_MIXED && p->s.escalate;
+  cudaStream_t es = s->es[slot % (int64_t)s->es.size()];
+  if (esc) {
+    const int n = p->n;
+    const int64_t P = s->paths, o = slot * P;
+    unsigned long long* ctl = s->d_sctl + slot * 8;
+    HC_CUDA(hc::launch_dedupe(P, P, n, s->x32 + o * n, s->st + o, 1e-6f, nullptr, nullptr,
+                              s->dup_list + o, s->d_dup + slot, s->t_io + o, es));
+    hc::LaunchCommon cd = stream_common(s);
+    stream_outputs(s, slot, cd);
+    cd.count_dev = s->d_dup + slot;
+    cd.items = s->dup_list + o;
+    cd.queue = ctl + 0;
+    cd.start_hi = 1;
+    cd.spread = 1;
+    cd.dup_list = nullptr;
+    cd.dup_count = nullptr;
+    hc::LaunchCommon ce = stream_common(s);
+    stream_outputs(s, slot, ce);
+    ce.count_dev = s->d_esc + slot;
+    ce.items = s->esc_list + o;
+    ce.queue = ctl + 1;
+    ce.esc_list = nullptr;
+    ce.x32_out = nullptr;
+    ce.esc_steps = ctl + 2;
+    ce.spread = 1;
+    ce.dup_list = nullptr;
+    ce.dup_count = nullptr;
+    // one warp per block: the blocks must fit beside the resident launch's
+    // (the double-float kernels hold up to 255 registers a thread)
+    auto run = [&](const hc::KernelRef& k, const hc::LaunchCommon& c) -> hc_status {
+      const int th = 32;
+      if (p->terms) {
+        hc::TermArgs a = stream_term_args(s, slot);
+        a.c = c;
+        const size_t sm = (size_t)hc::block_smem_bytes(k.lanes, p->extra, k.acc_bytes, th,
+                                                       k.eg_bytes, k.vx);
+        return launch_generic(k, &a, sm, P, es, th);
+      }
+      hc::DenseArgs a = stream_dense_args(s, slot);
+      a.c = c;
+      return launch_tracker(k, a, P, es, th);
+    };
+    hc_status rc;
+    if ((rc = run(s->kr, cd)) != HC_OK) return rc;
+    HC_CUDA(hc::launch_dedupe(P, P, n, s->x32 + o * n, s->st + o, 1e-6f, s->dup_list + o,
+                              s->d_dup + slot, s->esc_list + o, s->d_esc + slot, s->t_io + o,
+                              es));
+    if ((rc = run(s->kl, ce)) != HC_OK) return rc;
+  }
+  HC_CUDA(cudaEventRecord(s->edone[slot], es));
+  return HC_OK;
+}
+}  // namespace
+
+namespace {
+// Starts the re-tracking tiers of every slot whose tracking is complete and
+// (re)launches the resident launch if published paths wait for it.
+hc_status stream_progress(hc_stream* s) {
+  for (int k = 0; k < s->S; ++k)
+    if (s->state[k] == 1 && __atomic_load_n(&s->h_flag[k], __ATOMIC_ACQUIRE) ==
+                                (unsigned long long)(s->ticket[k] / s->S + 1)) {
+      const hc_status rc = stream_escalate(s, k);
+      if (rc != HC_OK) return rc;
+      s->state[k] = 2;
+    }
+  return stream_kick(s);
+}
+}  // namespace
+
+extern "C" hc_status hc_stream_submit(hc_stream* s, const double* inputs, int64_t* ticket) {
+  if (!s || s->magic != kStreamMagic || !ticket || (s->p->kind != HC_TOTAL_DEGREE && !inputs)) {
+    set_err("hc_stream_submit: invalid arguments");
+    return HC_ERR_INVALID;
+  }
+  const hc_problem* p = s->p;
+  const int64_t k = s->next_ticket;
+  const int slot = (int)(k % s->S);
+  if (s->state[slot] != 0) {
+    const hc_status rc = stream_progress(s);
+    if (rc != HC_OK) return rc;
+    set_err("hc_stream_submit: every slot holds a request that has not been collected");
+    return HC_ERR_BUSY;
+  }
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != p->device) HC_CUDA(cudaSetDevice(p->device));
+  auto body = [&]() -> hc_status {
+    const size_t in_per = p->terms ? (size_t)p->P : (size_t)p->T;
+    double2* in = s->d_in + (size_t)slot * in_per;
+    if (inputs)
+      HC_CUDA(cudaMemcpyAsync(in, inputs, sizeof(double2) * in_per, cudaMemcpyHostToDevice, s->cs));
+    else
+      HC_CUDA(cudaMemcpyAsync(in, p->d_coef, sizeof(double2) * in_per, cudaMemcpyDeviceToDevice,
+                              s->cs));
+    HC_CUDA(cudaMemsetAsync(s->d_esc + slot, 0, 8, s->cs));
+    HC_CUDA(cudaMemsetAsync(s->d_dup + slot, 0, 8, s->cs));
+    HC_CUDA(cudaMemsetAsync(s->d_sctl + (size_t)slot * 8, 0, 64, s->cs));
+    HC_CUDA(cudaMemsetAsync(s->steps + (size_t)slot * s->paths * 3, 0,
+                            sizeof(int32_t) * 3 * s->paths, s->cs));
+    if (!p->terms) {
+      const size_t Es = p->Estride, Ds = p->Dstride;
+      HC_CUDA(cudaMemsetAsync(s->E + slot * Es, 0, sizeof(double2) * Es, s->cs));
+      if (s->Edf) HC_CUDA(cudaMemsetAsync(s->Edf + slot * Es, 0, sizeof(hc::cdf) * Es, s->cs));
+      if (s->D32) HC_CUDA(cudaMemsetAsync(s->D32 + slot * Ds, 0, sizeof(float2) * Ds, s->cs));
+      if (s->D64) HC_CUDA(cudaMemsetAsync(s->D64 + slot * Ds, 0, sizeof(double2) * Ds, s->cs));
+      if (s->Ddf) HC_CUDA(cudaMemsetAsync(s->Ddf + slot * Ds, 0, sizeof(float4) * Ds, s->cs));
+      const int grid = (int)std::min<int64_t>((p->T + p->ndc + 255) / 256, 4096);
+      stage_dense_kernel<<<std::max(grid, 1), 256, 0, s->cs>>>(
+          1, p->T, in, 0, p->d_emap, p->ndc, p->d_dterm, p->d_dslot, p->d_dmult,
+          s->E + slot * Es, s->Edf ? s->Edf + slot * Es : nullptr, Es,
+          s->D32 ? s->D32 + slot * Ds : nullptr, s->D64 ? s->D64 + slot * Ds : nullptr,
+          s->Ddf ? s->Ddf + slot * Ds : nullptr, Ds);
+      HC_CUDA(cudaGetLastError());
+    } else if (p->coef_mode) {
+      const int64_t slots = (int64_t)p->TT * p->L;
+      const int gs = (int)std::min<int64_t>((slots + 255) / 256, 4096);
+      stage_coef_kernel<<<std::max(gs, 1), 256, 0, s->cs>>>(
+          1, slots, std::max(p->maxpf, 1), p->d_cpar, p->d_s64, p->d_c0, in, p->P,
+          s->dc + slot * slots, s->dcf + slot * slots, s->dcdf + slot * slots);
+      HC_CUDA(cudaGetLastError());
+    }
+    // publish the slot's tickets behind its inputs on the same stream (the
+    // resident launch reads the tail with acquire semantics)
+    s->h_tailv[slot] = (unsigned long long)(k + 1) * s->paths;
+    HC_CUDA(cudaMemcpyAsync(s->d_tail, s->h_tailv + slot, 8, cudaMemcpyHostToDevice, s->cs));
+    s->ticket[slot] = k;
+    s->state[slot] = 1;
+    ++s->next_ticket;
+    *ticket = k;
+    return stream_progress(s);
+  };
+  const hc_status rc = body();
+  if (cur != p->device) cudaSetDevice(cur);
+  return rc;
+}
+
+extern "C" hc_status hc_stream_poll(hc_stream* s, int64_t ticket, int64_t timeout_us,
+                                    double* x_out, uint8_t* status_out, int32_t* steps_out,
+                                    double* be_out) {
+  if (!s || s->magic != kStreamMagic || ticket < 0 || !x_out || !status_out) {
+    set_err("hc_stream_poll: invalid arguments");
+    return HC_ERR_INVALID;
+  }
+  const int slot = (int)(ticket % s->S);
+  if (s->ticket[slot] != ticket || s->state[slot] == 0) {
+    set_err("hc_stream_poll: unknown or already collected ticket");
+    return HC_ERR_INVALID;
+  }
+  const hc_problem* p = s->p;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != p->device) HC_CUDA(cudaSetDevice(p->device));
+  const auto t0 = std::chrono::steady_clock::now();
+  auto body = [&]() -> hc_status {
+    for (;;) {
+      {  // every waiting slot's next stage, not only this ticket's
+        const hc_status rc = stream_progress(s);
+        if (rc != HC_OK) return rc;
+      }
+      if (s->state[slot] == 2) {
+        const cudaError_t q = cudaEventQuery(s->edone[slot]);
+        if (q == cudaSuccess) {
+          const int64_t P = s->paths, o = (int64_t)slot * P;
+          const int n = p->n;
+          HC_CUDA(cudaMemcpyAsync(x_out, s->x + o * n, sizeof(double2) * n * P,
+                                  cudaMemcpyDeviceToHost, s->cs));
+          HC_CUDA(cudaMemcpyAsync(status_out, s->st + o, (size_t)P, cudaMemcpyDeviceToHost, s->cs));
+          if (steps_out)
+            HC_CUDA(cudaMemcpyAsync(steps_out, s->steps + o * 3, sizeof(int32_t) * 3 * P,
+                                    cudaMemcpyDeviceToHost, s->cs));
+          if (be_out)
+            HC_CUDA(cudaMemcpyAsync(be_out, s->be + o, sizeof(double) * P, cudaMemcpyDeviceToHost,
+                                    s->cs));
+          HC_CUDA(cudaStreamSynchronize(s->cs));
+          s->state[slot] = 0;
+          return HC_OK;
+        }
+        if (q != cudaErrorNotReady) HC_CUDA(q);
+      }
+      const double us =
+          std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count();
+      if (timeout_us >= 0 && us >= (double)timeout_us) return HC_ERR_TIMEOUT;
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+  };
+  const hc_status rc = body();
+  if (cur != p->device) cudaSetDevice(cur);
+  return rc;
+}
+
+extern "C" hc_status hc_stream_destroy(hc_stream* s) {
+  if (!s) return HC_OK;
+  if (s->magic != kStreamMagic) {
+    set_err("hc_stream_destroy: not a stream");
+    return HC_ERR_INVALID;
+  }
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != s->p->device) cudaSetDevice(s->p->device);
+  // the resident launch's groups leave at their next fetch
+  *s->h_stopv = 1u;
+  cudaMemcpyAsync(s->d_stop, s->h_stopv, 4, cudaMemcpyHostToDevice, s->cs);
+  cudaStreamSynchronize(s->cs);
+  s->magic = 0;
+  const int dev = s->p->device;
+  free_stream(s);
+  if (cur != dev) cudaSetDevice(cur);
+  return HC_OK;
+}

@@ -96,6 +96,23 @@ struct LaunchCommon {
   int spread;                   // first round of items round-robin over the blocks (one
                                 // per block before any second), then the queue: a short
                                 // list of FP64-heavy paths lands on as many SMs as it can
+  // Resident launches (hc_stream): items come from a ring of instance slots
+  // that the host fills while the launch runs.  Ticket q (claimed from
+  // *queue only while q < *ring_tail, which the host's staging stream writes
+  // after the slot's inputs) is item q mod ring_items, slot
+  // (q mod ring_items) / paths.  A group that finds no ticket sleeps (backing
+  // off) and polls, and leaves the launch once *ring_stop is set or
+  // ring_idle_ns pass without a ticket.  The last path of a slot to finish
+  // stores the ticket's generation (q / ring_items + 1) into ring_flag[slot]
+  // (mapped host memory).  Re-tracking lists are kept per slot,
+  // slot-relative: esc_list / dup_list + slot * paths, counters
+  // esc_count / dup_count + slot.
+  unsigned long long ring_items;         // 0: not resident
+  const unsigned long long* ring_tail;   // device memory
+  const unsigned int* ring_stop;         // device memory
+  unsigned long long ring_idle_ns;
+  unsigned int* ring_done;               // [slots] paths finished (device)
+  unsigned long long* ring_flag;         // [slots] mapped host memory
 };
 
 struct DenseArgs {

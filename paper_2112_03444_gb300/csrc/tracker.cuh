@@ -124,6 +124,28 @@ __device__ __forceinline__ GroupMem make_group_mem(unsigned char* smem, int extr
   return m;
 }
 
+// Accesses to the resident launch's control words: the published tail and
+// the stop word in device memory (written by copies on the host's staging
+// stream), the completion flags in mapped host memory.
+__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned int ld_relaxed_gpu(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_sys(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // max over the group of a double (butterfly over the group's L lanes)
 template <int L>
 __device__ __forceinline__ double gmaxd(const Group& g, double v) {
@@ -181,6 +203,7 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
   // ---- per-path state (identical control state in all lanes of the group)
   HOM hom = prob.hom(0);
   int64_t item = 0;
+  unsigned long long ticket = 0;  // resident launches: the claimed ticket
   cx<double> xd = czero<double>();  // FP64 state
   cx<float> xf = czero<float>();    // FP32 state
   bool hi = !MIXED;                 // the state lives in xd rather than xf
@@ -383,12 +406,15 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
               c.t_io[item] = (base == ST_FAIL_STEP || base == ST_FAIL_MAXSTEPS) ? (hi ? t : (double)tf)
                              : (base == ST_SINGULAR)                            ? 1.0
                                                                                : 0.0;
+            // resident launches: per-slot lists of slot-relative items
+            const int64_t slot = c.ring_items ? item / c.paths : 0;
+            const int64_t rel = item - slot * c.paths;
             if (to64) {
-              const unsigned long long pos = atomicAdd(c.esc_count, 1ull);
-              c.esc_list[pos] = item;
+              const unsigned long long pos = atomicAdd(c.esc_count + slot, 1ull);
+              c.esc_list[slot * c.paths * (c.ring_items != 0) + pos] = c.ring_items ? rel : item;
             } else {
-              const unsigned long long pos = atomicAdd(c.dup_count, 1ull);
-              c.dup_list[pos] = item;
+              const unsigned long long pos = atomicAdd(c.dup_count + slot, 1ull);
+              c.dup_list[slot * c.paths * (c.ring_items != 0) + pos] = c.ring_items ? rel : item;
             }
           } else if (c.t_io) {
             c.t_io[item] = 0.0;
@@ -404,7 +430,52 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
           }
         }
       }
+      if (c.ring_items) {
+        // the slot's last path tells the host (mapped memory) that the
+        // slot's tracking launch work is complete
+        __threadfence();
+        __syncwarp(g.mask);
+        if (g.gl == 0) {
+          const int64_t slot = item / c.paths;
+          const unsigned prev = atomicAdd(c.ring_done + slot, 1u);
+          if ((int64_t)prev + 1 == c.paths) {
+            atomicExch(c.ring_done + slot, 0u);
+            __threadfence_system();
+            st_release_sys(c.ring_flag + slot, ticket / c.ring_items + 1);
+          }
+        }
+      }
       mode = M_FETCH;
+    }
+    if (mode == M_FETCH && c.ring_items) {
+      // resident launch: claim the next published ticket, or sleep and poll
+      // (bounded: the stop word or ring_idle_ns without work end the launch)
+      unsigned long long q = 0;
+      unsigned got = 0;
+      if (g.gl == 0) {
+        const unsigned long long t_wait = global_ns();
+        unsigned sleep_ns = 500;
+        for (;;) {
+          if (ld_relaxed_gpu(c.ring_stop)) break;
+          const unsigned long long pub = ld_acquire_gpu(c.ring_tail);
+          const unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(c.queue);
+          if (cur < pub) {
+            if (atomicCAS(c.queue, cur, cur + 1) == cur) {
+              q = cur;
+              got = 1;
+              break;
+            }
+            continue;
+          }
+          if (global_ns() - t_wait > c.ring_idle_ns) break;
+          __nanosleep(sleep_ns);  // back off while there is no work
+          sleep_ns = min(2u * sleep_ns, 32000u);
+        }
+      }
+      if (!__shfl_sync(g.mask, got, leader)) break;
+      ticket = __shfl_sync(g.mask, q, leader);
+      (void)ld_acquire_gpu(c.ring_tail);  // every lane: the slot's inputs are visible
+      item = (int64_t)(ticket % c.ring_items);
     }
     if (mode == M_FETCH) {
       if (c.step_budget && !c.items) {
@@ -414,7 +485,9 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
         if (__shfl_sync(g.mask, spent, leader) >= c.step_budget) break;
       }
       unsigned long long q = 0;
-      if (c.spread && first_fetch) {
+      if (c.ring_items) {
+        // item claimed above
+      } else if (c.spread && first_fetch) {
         // ticket = slot * blocks + block: consecutive items on different blocks
         // (and so, for the first blocks of the grid, on different SMs)
         q = (unsigned long long)(threadIdx.x / L) * gridDim.x + blockIdx.x;
@@ -424,8 +497,10 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
         q = __shfl_sync(g.mask, q, leader);
         if (c.spread) q += (unsigned long long)gridDim.x * (blockDim.x / L);
       }
-      if ((int64_t)q >= total) break;
-      item = c.items ? c.items[q] : (int64_t)q;
+      if (!c.ring_items) {
+        if ((int64_t)q >= total) break;
+        item = c.items ? c.items[q] : (int64_t)q;
+      }
       const int64_t inst = item / c.paths;
       const int64_t k_in = item - inst * c.paths;
       const int64_t path = c.path_ids ? c.path_ids[item] : c.path_map ? c.path_map[k_in] : k_in;

@@ -175,7 +175,17 @@ EXPORTED = ("hc_status_string", "hc_last_error", "hc_default_settings", "hc_crea
             "hc_measure_fma_peak", "hc_track_dense_noalloc", "hc_server_default_config",
             "hc_server_create", "hc_server_submit", "hc_server_wait", "hc_server_stats",
             "hc_autotune", "hc_plan_create", "hc_plan_run", "hc_set_memory_cap",
-            "hc_batched_solve", "hc_monodromy_solve", "hc_autotune_cached", "hc_evaluate")
+            "hc_batched_solve", "hc_monodromy_solve", "hc_autotune_cached", "hc_evaluate",
+            "hc_stream_create", "hc_stream_submit", "hc_stream_poll", "hc_stream_destroy")
+
+_lib.hc_stream_create.restype = ctypes.c_int32
+_lib.hc_stream_create.argtypes = [_P, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(_P)]
+_lib.hc_stream_submit.restype = ctypes.c_int32
+_lib.hc_stream_submit.argtypes = [_P, _P, ctypes.POINTER(ctypes.c_int64)]
+_lib.hc_stream_poll.restype = ctypes.c_int32
+_lib.hc_stream_poll.argtypes = [_P, ctypes.c_int64, ctypes.c_int64, _P, _P, _P, _P]
+_lib.hc_stream_destroy.restype = ctypes.c_int32
+_lib.hc_stream_destroy.argtypes = [_P]
 
 _lib.hc_evaluate.restype = ctypes.c_int32
 _lib.hc_evaluate.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int64, _P, _P, _P,
@@ -624,6 +634,51 @@ class Batch:
     def close(self):
         if getattr(self, "h", None):
             destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+
+class Stream:
+    """Continuous admission into a resident tracking launch (hc_stream_*):
+    submit(inputs) returns a ticket as soon as the instance is staged; its
+    paths start as lane groups of the running launch free up.  poll(ticket)
+    returns (x [paths][n], status [paths], steps [paths][3], be [paths]) or
+    None while it is not done (timeout_us elapsed)."""
+
+    def __init__(self, problem, slots=64, idle_us=20000):
+        self.problem = problem
+        h = _P()
+        _check(_lib.hc_stream_create(problem.h, int(slots), int(idle_us), ctypes.byref(h)),
+               "hc_stream_create")
+        self.h = h.value
+        self.paths = problem.paths
+
+    def submit(self, coef=None, p1=None):
+        data = p1 if self.problem.kind != HC_TOTAL_DEGREE else coef
+        buf = None if data is None else _host(np.ravel(data), np.complex128)
+        t = ctypes.c_int64()
+        _check(_lib.hc_stream_submit(self.h, _addr(buf) if buf is not None else None,
+                                     ctypes.byref(t)), "hc_stream_submit")
+        return t.value
+
+    def poll(self, ticket, timeout_us=-1):
+        n = self.problem.n
+        x = np.zeros((self.paths, n), np.complex128)
+        st = np.zeros(self.paths, np.uint8)
+        steps = np.zeros((self.paths, 3), np.int32)
+        be = np.zeros(self.paths, np.float64)
+        code = _lib.hc_stream_poll(self.h, int(ticket), int(timeout_us), _addr(x), _addr(st),
+                                   _addr(steps), _addr(be))
+        if code == HC_ERR_TIMEOUT:
+            return None
+        _check(code, "hc_stream_poll")
+        return x, st, steps, be
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.hc_stream_destroy(self.h)
             self.h = None
 
     def __del__(self):
