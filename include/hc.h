@@ -329,7 +329,9 @@ hc_status hc_problem_query(const hc_problem* p, hc_problem_info* out);
  * again); a slot whose paths are done gets the re-tracking tiers of the
  * mixed pipeline on a side stream, as hc_track_batch runs them for a batch.
  * Results are those of hc_track_batch on the same inputs, path for path.
- * One thread at a time may use a stream.  Sign symmetries are not applied
+ * One thread at a time may use a stream.  Streams track in mixed precision
+ * with the default group width (settings.lanes is not applied; other
+ * precisions return HC_ERR_UNSUPPORTED), and apply no sign symmetries
  * (every start is tracked).
  *   hc_stream_create  slots 1..4096, idle_us 1..1e7; allocates the ring
  *                     (inputs, tables, outputs, lists per slot) and mapped

@@ -41,7 +41,7 @@ constexpr int kTrackMinBlocks = 4;
 // solve).  The double-float kernels hold every complex number in four
 // registers and run one path per warp: they get the registers of one block
 // per SM rather than of four.
-template <int N, int DEG, int PREC, int L>
+template <int N, int DEG, int PREC, int L, bool RING = false>
 __global__ void __launch_bounds__(kBlock, PREC == HC_PREC_DF ? 1 : kTrackMinBlocks)
     dense_td_kernel(const DenseArgs a) {
   constexpr bool MIXED = PREC == HC_PREC_MIXED;
@@ -52,14 +52,15 @@ __global__ void __launch_bounds__(kBlock, PREC == HC_PREC_DF ? 1 : kTrackMinBloc
   const GroupMem sm = make_group_mem<L>(smem, DenseShape<N, DEG>::EXTRA, 0,
                                         endgame_smem_bytes(L, MIXED), XDF ? 1 : 0);
   DenseProblem<N, DEG, L> prob{&a, sm, g.mask};
-  run_tracker<N, L, MIXED, DenseProblem<N, DEG, L>, RE>(prob, a.c, g, sm);
+  run_tracker<N, L, MIXED, DenseProblem<N, DEG, L>, RE, RING>(prob, a.c, g, sm);
 }
 
-// lanes = 0: the default lanes_for(N); otherwise that group width.
-template <int DEG, int PREC, int N, int LANES = 0>
+// lanes = 0: the default lanes_for(N); otherwise that group width.  RING:
+// the resident-launch variant (hc_stream).
+template <int DEG, int PREC, int N, int LANES = 0, bool RING = false>
 KernelRef dense_ref() {
   constexpr int L = LANES ? LANES : ((N <= 4) ? 4 : (N <= 8) ? 8 : (N <= 16) ? 16 : 32);
-  return KernelRef{reinterpret_cast<const void*>(&dense_td_kernel<N, DEG, PREC, L>), L,
+  return KernelRef{reinterpret_cast<const void*>(&dense_td_kernel<N, DEG, PREC, L, RING>), L,
                    DenseShape<N, DEG>::EXTRA, 0, endgame_smem_bytes(L, PREC == HC_PREC_MIXED),
                    PREC == HC_PREC_DF ? 1 : 0};
 }

@@ -2633,6 +2633,10 @@ extern "C" hc_status hc_stream_create(hc_problem* p, int32_t slots, int64_t idle
   const int prec = p->s.precision;
   const bool mixed = prec == HC_PREC_MIXED;
   const int n = p->n;
+  if (!mixed) {
+    set_err("hc_stream_create: streams track in mixed precision (settings.precision)");
+    return HC_ERR_UNSUPPORTED;
+  }
   hc_stream* s = new hc_stream();
   s->p = p;
   s->S = slots;
@@ -2641,13 +2645,11 @@ extern "C" hc_status hc_stream_create(hc_problem* p, int32_t slots, int64_t idle
   s->state.assign(slots, 0);
   s->ticket.assign(slots, -1);
   s->edone.assign(slots, nullptr);
+  s->kt = hc::ring_kernel(p->terms, p->deg, n);
   if (p->terms) {
-    s->kt = hc::term_kernel(n, prec, mixed ? p->s.lanes : 0);
-    s->kr = s->kt;
+    s->kr = hc::term_kernel(n, HC_PREC_MIXED, 0);
     s->kl = hc::term_kernel(n, hc::last_tier_precision(p->s), 0);
   } else {
-    s->kt = hc::dense_kernel(p->deg, n, prec, mixed ? p->s.lanes : 0);
-    if (!s->kt.fn) s->kt = hc::dense_kernel(p->deg, n, prec, 0);
     s->kr = retrack_kernel(p->deg, n, HC_PREC_MIXED);
     s->kl = retrack_kernel(p->deg, n, hc::last_tier_precision(p->s));
   }

@@ -220,6 +220,10 @@ inline int last_tier_precision(const hc_settings& s) {
   return s.endgame ? HC_PREC_FP64 : s.retrack_precision;
 }
 
+// Resident-launch (hc_stream) variant of the mixed tracking kernel for a
+// problem: term tables or dense of degree deg; fn == nullptr if absent.
+KernelRef ring_kernel(bool terms, int deg, int n);
+
 // Evaluation kernels of hc_evaluate (prec: HC_PREC_FP64, HC_PREC_MIXED =
 // FP32 evaluation, HC_PREC_DF); fn == nullptr if absent.
 KernelRef dense_eval_kernel(int deg, int n, int prec);

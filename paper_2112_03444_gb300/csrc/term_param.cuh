@@ -335,7 +335,7 @@ __host__ __device__ constexpr int term_acc_bytes() {
 }
 
 // PREC: HC_PREC_MIXED, HC_PREC_FP64 or HC_PREC_DF (as the dense kernels)
-template <int N, int PREC, int L>
+template <int N, int PREC, int L, bool RING = false>
 __global__ void __launch_bounds__(kBlock) term_param_kernel(const __grid_constant__ TermArgs a) {
   constexpr bool MIXED = PREC == HC_PREC_MIXED;
   constexpr bool XDF = PREC == HC_PREC_DF;
@@ -345,14 +345,14 @@ __global__ void __launch_bounds__(kBlock) term_param_kernel(const __grid_constan
   const GroupMem sm = make_group_mem<L>(smem, a.extra, term_acc_bytes<N, MIXED, L>(),
                                         endgame_smem_bytes(L, MIXED), XDF ? 1 : 0);
   TermProblem<N, L, MIXED> prob{&a, g, sm};
-  run_tracker<N, L, MIXED, TermProblem<N, L, MIXED>, RE>(prob, a.c, g, sm);
+  run_tracker<N, L, MIXED, TermProblem<N, L, MIXED>, RE, RING>(prob, a.c, g, sm);
 }
 
-template <int PREC, int N, int LANES = 0>
+template <int PREC, int N, int LANES = 0, bool RING = false>
 KernelRef term_ref() {
   constexpr bool MIXED = PREC == HC_PREC_MIXED;
   constexpr int L = LANES ? LANES : ((N <= 4) ? 4 : (N <= 8) ? 8 : (N <= 16) ? 16 : 32);
-  return KernelRef{reinterpret_cast<const void*>(&term_param_kernel<N, PREC, L>), L, 0,
+  return KernelRef{reinterpret_cast<const void*>(&term_param_kernel<N, PREC, L, RING>), L, 0,
                    term_acc_bytes<N, MIXED, L>(), endgame_smem_bytes(L, MIXED),
                    PREC == HC_PREC_DF ? 1 : 0};
 }

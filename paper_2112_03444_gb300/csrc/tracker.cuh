@@ -170,8 +170,10 @@ __device__ __forceinline__ cx<double> hermite_at_zero(double wb, cx<double> xb, 
 // the evaluation and the solve in the FP64-state kernels (MIXED = false):
 // double, or df for the double-float kernels, whose state, step control,
 // refinement residual and classification stay in FP64 exactly as in the
-// FP64 kernels.
-template <int N, int L, bool MIXED, class PROB, class RE = double>
+// FP64 kernels.  RING: the resident launch of a stream (hc_stream), whose
+// items come from the host-filled ring (LaunchCommon ring_*); compiled only
+// into the kernels the streams use.
+template <int N, int L, bool MIXED, class PROB, class RE = double, bool RING = false>
 __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon& c,
                                             const Group& g, const GroupMem& sm) {
   using R = typename std::conditional<MIXED, float, RE>::type;
@@ -204,6 +206,7 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
   HOM hom = prob.hom(0);
   int64_t item = 0;
   unsigned long long ticket = 0;  // resident launches: the claimed ticket
+  (void)ticket;
   cx<double> xd = czero<double>();  // FP64 state
   cx<float> xf = czero<float>();    // FP32 state
   bool hi = !MIXED;                 // the state lives in xd rather than xf
@@ -407,14 +410,14 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
                              : (base == ST_SINGULAR)                            ? 1.0
                                                                                : 0.0;
             // resident launches: per-slot lists of slot-relative items
-            const int64_t slot = c.ring_items ? item / c.paths : 0;
-            const int64_t rel = item - slot * c.paths;
+            const int64_t slot = RING ? item / c.paths : 0;
+            const int64_t rec = RING ? item - slot * c.paths : item;
             if (to64) {
               const unsigned long long pos = atomicAdd(c.esc_count + slot, 1ull);
-              c.esc_list[slot * c.paths * (c.ring_items != 0) + pos] = c.ring_items ? rel : item;
+              c.esc_list[slot * c.paths + pos] = rec;
             } else {
               const unsigned long long pos = atomicAdd(c.dup_count + slot, 1ull);
-              c.dup_list[slot * c.paths * (c.ring_items != 0) + pos] = c.ring_items ? rel : item;
+              c.dup_list[slot * c.paths + pos] = rec;
             }
           } else if (c.t_io) {
             c.t_io[item] = 0.0;
@@ -430,7 +433,7 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
           }
         }
       }
-      if (c.ring_items) {
+      if constexpr (RING) {
         // the slot's last path tells the host (mapped memory) that the
         // slot's tracking launch work is complete
         __threadfence();
@@ -447,7 +450,7 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
       }
       mode = M_FETCH;
     }
-    if (mode == M_FETCH && c.ring_items) {
+    if (RING && mode == M_FETCH) {
       // resident launch: claim the next published ticket, or sleep and poll
       // (bounded: the stop word or ring_idle_ns without work end the launch)
       unsigned long long q = 0;
@@ -485,7 +488,7 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
         if (__shfl_sync(g.mask, spent, leader) >= c.step_budget) break;
       }
       unsigned long long q = 0;
-      if (c.ring_items) {
+      if (RING) {
         // item claimed above
       } else if (c.spread && first_fetch) {
         // ticket = slot * blocks + block: consecutive items on different blocks
@@ -497,7 +500,7 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
         q = __shfl_sync(g.mask, q, leader);
         if (c.spread) q += (unsigned long long)gridDim.x * (blockDim.x / L);
       }
-      if (!c.ring_items) {
+      if (!RING) {
         if ((int64_t)q >= total) break;
         item = c.items ? c.items[q] : (int64_t)q;
       }
