@@ -114,3 +114,21 @@ def test_evaluate_rejects_bad_instance(hc):
     pr = hc.Problem(base)
     with pytest.raises(hc.HCError):
         pr.evaluate(np.zeros((1, 2)), [0.5], instance=[3], coef=coefs)
+
+
+@pytest.mark.parametrize("precision", [0, 2], ids=["fp64", "df"])
+def test_dense_evaluation_far_from_the_origin(hc, precision):
+    """Points of norm ~1e3 (a diverging path's range): the double-float
+    evaluation keeps its relative accuracy (FP32 exponent range suffices)."""
+    from paper_2112_03444_gb300 import inputs
+    base, coefs = inputs.dense_batch(6, 3, [77])
+    gamma = inputs.unit_gamma(77)
+    pr = hc.Problem(base, gamma=gamma)
+    x, t = _points(6, 12, 9, scale=1e3)
+    H, Hx, Ht = pr.evaluate(x, t, coef=coefs, precision=precision)
+    op = oracle.OracleProblem(base, gamma=gamma, coef=coefs[0])
+    for k in range(12):
+        ref = op.eval(x[k], t[k])
+        _close(H[k], ref[0], TOL[precision])
+        _close(Hx[k], ref[1], TOL[precision])
+        _close(Ht[k], ref[2], TOL[precision])

@@ -94,3 +94,50 @@ def test_stream_restarts_after_idle_and_times_out_politely(hc):
             s.poll(t1)  # collected already
     finally:
         s.close()
+
+
+def test_stream_coefficient_family_and_fp64_last_tier(hc):
+    """Coefficient interpolation (per-slot staged dc tables) and a stream
+    whose last re-tracking tier runs in FP64: still path for path equal to
+    the batch on the same settings."""
+    from paper_2112_03444_gb300 import inputs
+    fam = inputs.p3p_family()
+    z = np.load(os.path.join(STARTS, "p3p.npz"))
+    rng = np.random.default_rng(3)
+    P = len(z["p0"])
+    p1 = rng.normal(size=(5, P)) + 1j * rng.normal(size=(5, P))
+    for kind, settings in ((hc.HC_COEFFICIENT, None), (hc.HC_PARAMETER, dict(retrack_precision=0))):
+        pr = hc.Problem(fam.system, kind=kind, p0=z["p0"], start=z["start"], settings=settings)
+        ref = pr.track(n_instances=len(p1), p1=p1).wait()
+        s = hc.Stream(pr, slots=2, idle_us=5000)
+        try:
+            for i in range(len(p1)):
+                tk = s.submit(p1=p1[i])
+                _same(s.poll(tk), ref.x[i], ref.status[i], ref.steps[i])
+        finally:
+            s.close()
+
+
+def test_stream_destroy_with_requests_in_flight(hc):
+    """Destroying a stream whose resident launch still has published work
+    returns: the stop word ends the launch after the paths in progress."""
+    from paper_2112_03444_gb300 import inputs
+    base, coefs = inputs.dense_batch(8, 3, [911, 912, 913])
+    pr = hc.Problem(base, gamma=inputs.unit_gamma(911))
+    s = hc.Stream(pr, slots=4, idle_us=2000)
+    for i in range(3):
+        s.submit(coef=coefs[i])
+    t0 = time.perf_counter()
+    s.close()
+    assert time.perf_counter() - t0 < 30.0
+    # the problem (and the device) stay usable
+    b = pr.track(n_instances=1, coef=coefs[:1]).wait()
+    assert (b.status[0] & 0x7F == 1).sum() > 0
+
+
+def test_stream_rejects_other_precisions(hc):
+    from paper_2112_03444_gb300 import inputs
+    base, _ = inputs.dense_batch(3, 2, [1])
+    pr = hc.Problem(base, settings=dict(precision=hc.HC_PREC_FP64))
+    with pytest.raises(hc.HCError):
+        hc.Stream(pr, slots=2)
