@@ -173,15 +173,6 @@ typedef struct hc_settings {
   double eg_s0;           /* 0.1 */
   double eg_ratio;        /* 0.5 */
   double eg_tol;          /* agreement of two predictions, relative: 1e-8 */
-  /* End-of-step acceptance check of the FP32 phase (mixed precision; the
-   * paper's corrector, Sec. 3 Eqs. 5-6, is FP64 throughout): with
-   * accept_check = 1 a converged FP32 corrector step is accepted only if
-   * the backward error of H at the corrected point, evaluated in
-   * double-float arithmetic, is at most accept_tol; otherwise the step is
-   * rejected like a corrector failure.  Off by default.                      */
-  int32_t accept_check;   /* 0 */
-  int32_t accept_reserved; /* 0 */
-  double accept_tol;      /* 1e-5 */
 } hc_settings;
 
 /*

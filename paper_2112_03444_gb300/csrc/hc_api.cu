@@ -567,8 +567,6 @@ hc::DevSettings dev_settings(const hc_settings& s) {
   d.eg_s0 = s.eg_s0;
   d.eg_ratio = s.eg_ratio;
   d.eg_tol = s.eg_tol;
-  d.accept_check = s.accept_check;
-  d.accept_tol = s.accept_tol;
   return d;
 }
 
@@ -584,8 +582,7 @@ hc_status validate_settings(const hc_settings& s) {
       (s.lanes != 0 && s.lanes != 32) || s.max_newton_ir < 1 || s.max_newton_ir > 32 ||
       (s.block_threads != 0 && s.block_threads != 32 && s.block_threads != 64 &&
        s.block_threads != 128) ||
-      (s.endgame != 0 && s.endgame != 1) || (s.accept_check != 0 && s.accept_check != 1) ||
-      s.accept_reserved != 0 || (s.accept_check && !(s.accept_tol > 0)) ||
+      (s.endgame != 0 && s.endgame != 1) ||
       (s.endgame && (!(s.eg_s0 > 0 && s.eg_s0 < 1) || !(s.eg_ratio > 0 && s.eg_ratio < 1) ||
                      !(s.eg_tol > 0) || s.eg_cmax < 1 || s.eg_cmax > 16 || s.eg_samples < 1 ||
                      s.eg_samples > 60))) {
@@ -1087,9 +1084,6 @@ hc_settings hc_default_settings(void) {
   s.eg_s0 = 0.1;
   s.eg_ratio = 0.5;
   s.eg_tol = 1e-8;
-  s.accept_check = 0;
-  s.accept_reserved = 0;
-  s.accept_tol = 1e-5;
   return s;
 }
 

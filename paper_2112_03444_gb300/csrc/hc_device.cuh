@@ -295,9 +295,9 @@ struct DevSettings {
   double dt_min, dt_max, dt_init, newton_tol, newton_tol_fp32, max_first_corr;
   double refine_tol, r_inf, finite_tol, real_tol, singular_cond, t_endgame;
   double dt_min_fp32, max_first_corr_fp32;
-  double eg_s0, eg_ratio, eg_tol, accept_tol;
+  double eg_s0, eg_ratio, eg_tol;
   int max_newton, max_steps, grow_after, refine_iters, max_steps_fp32, max_newton_ir;
-  int endgame, eg_cmax, eg_samples, accept_check;
+  int endgame, eg_cmax, eg_samples;
 };
 
 enum : int {

@@ -690,24 +690,7 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
       const float dn = sqrt_approx(gmaxf(g, act ? (float)cnorm2(d) : 0.f));
       const bool bad = !sok || !(dn <= 3.0e38f) || !(xn <= 3.0e38f) ||
                        (it == 0 && dn > (HI() ? corr64 : corr32) * (1.f + xn));
-      const bool conv = !bad && dn <= (HI() ? tol64 : tol32) * (1.f + xn);
-      // optional end-of-step check of an FP32 step: the backward error of H
-      // at the corrected point in double-float arithmetic
-      bool pass = true;
-      if constexpr (MIXED) {
-        if (conv && !HI() && s.accept_check) {
-          __syncwarp(g.mask);
-          if (act) put_hi(cvt<double>(xpf), true);
-          __syncwarp(g.mask);
-          cx<float> Hf;
-          float scf;
-          hom.template residual_df<true>(reinterpret_cast<const cdf*>(sm.vd), g.gl, (double)t1f,
-                                         Hf, scf);
-          const float r = act ? cabs2(Hf) : 0.f;
-          pass = gmaxf(g, act ? (scf > 0.f ? r / scf : r) : 0.f) <= (float)s.accept_tol;
-        }
-      }
-      if (conv && pass) {
+      if (!bad && dn <= (HI() ? tol64 : tol32) * (1.f + xn)) {
         // accept the step
         bool at_end;
         ++nacc;
@@ -739,7 +722,7 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
           }
           begin_step();
         }
-      } else if (bad || !pass || ++it >= ((MIXED && HI()) ? s.max_newton_ir : s.max_newton)) {
+      } else if (bad || ++it >= ((MIXED && HI()) ? s.max_newton_ir : s.max_newton)) {
         reject();
       }
     } else if (mode == M_REFINE) {

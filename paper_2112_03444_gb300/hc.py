@@ -50,9 +50,7 @@ class hc_settings(ctypes.Structure):
                 ("block_threads", ctypes.c_int32), ("endgame", ctypes.c_int32),
                 ("eg_cmax", ctypes.c_int32), ("eg_samples", ctypes.c_int32),
                 ("retrack_precision", ctypes.c_int32), ("eg_s0", ctypes.c_double),
-                ("eg_ratio", ctypes.c_double), ("eg_tol", ctypes.c_double),
-                ("accept_check", ctypes.c_int32), ("accept_reserved", ctypes.c_int32),
-                ("accept_tol", ctypes.c_double)]
+                ("eg_ratio", ctypes.c_double), ("eg_tol", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -35,7 +35,7 @@ def test_every_declared_symbol_is_exported(hc):
 
 def test_struct_layouts_match_header_sizes(hc):
     # hc_settings: 14 doubles + 10 int32, then 4 int32 + 3 doubles of the endgame
-    assert ctypes.sizeof(hc.hc_settings) == 208
+    assert ctypes.sizeof(hc.hc_settings) == 192
     assert ctypes.sizeof(hc.hc_batch_result) == 18 * 8
     assert ctypes.sizeof(hc.hc_batch_desc) == 4 + 4 + 7 * 8 + 8 + 4 + 4 + 8
 
@@ -114,8 +114,7 @@ def test_null_handles_are_rejected(hc):
 @pytest.mark.parametrize("field,value", [("max_newton_ir", 0), ("max_newton_ir", 33),
                                          ("block_threads", 16), ("block_threads", 256),
                                          ("lanes", 16), ("endgame", 2), ("retrack_precision", 1),
-                                         ("retrack_precision", 3), ("precision", 3),
-                                         ("accept_check", 2), ("accept_reserved", 1)])
+                                         ("retrack_precision", 3), ("precision", 3)])
 def test_create_problem_rejects_bad_iteration_limits(hc, field, value):
     from paper_2112_03444_gb300 import inputs
     d, keep = _desc(hc, inputs.dense_system(2, 2, 0))
