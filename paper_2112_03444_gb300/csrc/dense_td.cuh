@@ -118,9 +118,26 @@ struct DenseTD {
   // m-th outer index of a part: zigzag over blocks of PARTS indices, so that
   // triangular inner loops give every part the same work (identity for
   // PARTS = 1)
+  template <int P = PARTS>
   __device__ __forceinline__ static int zigzag(int m, int part) {
-    return (m & 1) ? ((m + 1) * PARTS - 1 - part) : (m * PARTS + part);
+    return (m & 1) ? ((m + 1) * P - 1 - part) : (m * P + part);
   }
+
+  // Residuals of the mixed kernels whose groups are narrower than a warp
+  // (several paths per warp).  A residual there is needed by one group at a
+  // time (its path is in the FP64-state phase or at its endpoint while the
+  // other paths of the warp track in FP32), and a group computing it alone
+  // keeps the rest of the warp idle for the whole Horner evaluation.  So the
+  // tracker has every lane of the warp compute a share of it: the outer
+  // index j is split over WP = 32 / L parts (zigzag, as for split rows), the
+  // parts are added by a butterfly over the warp, and the group then holds
+  // the rows' residuals (the *_coop functions below).  Where a group must
+  // compute a residual alone (the resident-launch kernels, whose groups wait
+  // for work independently), it forms the same WP partial sums one after the
+  // other and adds them in the butterfly's order (the *_seq functions), so
+  // that both forms give the same bits.
+  static constexpr bool kCoop = (PARTS == 1 && L_GROUP < 32);
+  static constexpr int WP = 32 / L;
 
   // Two consecutive complex numbers (16-byte aligned): one 16-byte load in
   // FP32, two in FP64.
@@ -264,22 +281,30 @@ struct DenseTD {
   // ratio test) is returned in sc.  Runtime loops: this code runs a few
   // times per path and must not crowd the tracking loop out of the
   // instruction cache.  Split over PARTS lanes like eval (outer index j).
-  template <bool SCALE_T>
+  // EP > 1 (groups narrower than a warp): the WP-part order of the
+  // cooperative form, computed by the group alone.
+  template <bool SCALE_T, int EP = 1>
   __device__ __forceinline__ void residual64(const cx<double>* xs, int i, double t, double omt,
                                              cx<double>& H, double& sc) const {
-    residual64_impl(xs, i, t, omt, SCALE_T, H, sc);
+    if constexpr (EP > 1) {
+      static_assert(EP == WP && kCoop, "sequential parts: groups narrower than a warp");
+      residual64_seq(xs, i, t, omt, SCALE_T, H, sc);
+    } else {
+      residual64_impl(xs, i, t, omt, SCALE_T, H, sc);
+    }
   }
 
-  __device__ __noinline__ void residual64_impl(const cx<double>* xs, int i, double t, double omt,
-                                               bool scale, cx<double>& H, double& sc) const {
-    const int r = i & (L - 1);
-    const int part = (PARTS > 1) ? i / L : 0;
+  // partial sums of row r over the outer indices j of part `part` of a
+  // P-way split: F (the constant term in part 0) and the scale's share S
+  template <int P>
+  __device__ __noinline__ void residual64_part(const cx<double>* xs, int r, int part, bool scale,
+                                               cx<double>& Fo, float& So) const {
     const cx<double>* e = E + (r < N ? r : 0);
     cx<double> F = part == 0 ? e[0] : czero<double>();
     float Ssum = (scale && part == 0) ? cabs2(cvt<float>(e[0])) : 0.f;
 #pragma unroll 1
     for (int mm = 0;; ++mm) {
-      const int j = zigzag(mm, part);
+      const int j = zigzag<P>(mm, part);
       if (j >= N) break;
       // first Horner coefficient of block j: 1 + sum over earlier blocks
       // (block j' holds 1 + sum_{k <= j'} (DEG == 2 ? 1 : k + 2) entries)
@@ -316,13 +341,14 @@ struct DenseTD {
       F = cfma(xj, in, F);
       if (scale) Ssum += cabs2(cvt<float>(xj)) * ins;
     }
-    if constexpr (PARTS > 1) {
-      F = part_sum(F);
-      if (scale) {
-#pragma unroll
-        for (int o = L; o < L * PARTS; o <<= 1) Ssum += __shfl_xor_sync(0xffffffffu, Ssum, o);
-      }
-    }
+    Fo = F;
+    So = Ssum;
+  }
+
+  // H = t F + (1 - t) gamma G_r and the scale, from the summed parts
+  __device__ __noinline__ void residual64_finish(const cx<double>* xs, int r, double t, double omt,
+                                                 bool scale, cx<double> F, float Ssum,
+                                                 cx<double>& H, double& sc) const {
     const cx<double> xi = xs[r < N ? r : 0];
     const cx<double> xi2 = xi * xi;
     const cx<double> G = (DEG == 2 ? xi2 : xi2 * xi) - mk<double>(1.0, 0.0);
@@ -335,43 +361,106 @@ struct DenseTD {
     }
   }
 
+  __device__ __forceinline__ void residual64_impl(const cx<double>* xs, int i, double t, double omt,
+                                                  bool scale, cx<double>& H, double& sc) const {
+    const int r = i & (L - 1);
+    const int part = (PARTS > 1) ? i / L : 0;
+    cx<double> F;
+    float Ssum;
+    residual64_part<PARTS>(xs, r, part, scale, F, Ssum);
+    if constexpr (PARTS > 1) {
+      F = part_sum(F);
+      if (scale) {
+#pragma unroll
+        for (int o = L; o < L * PARTS; o <<= 1) Ssum += __shfl_xor_sync(0xffffffffu, Ssum, o);
+      }
+    }
+    residual64_finish(xs, r, t, omt, scale, F, Ssum, H, sc);
+  }
+
+  // the WP parts one after the other, added in the butterfly's order
+  __device__ __forceinline__ void residual64_seq(const cx<double>* xs, int i, double t, double omt,
+                                                 bool scale, cx<double>& H, double& sc) const {
+    const int r = i & (L - 1);
+    cx<double> F[WP];
+    float S[WP];
+#pragma unroll
+    for (int p = 0; p < WP; ++p) residual64_part<WP>(xs, r, p, scale, F[p], S[p]);
+#pragma unroll
+    for (int w = 1; w < WP; w <<= 1) {
+#pragma unroll
+      for (int p = 0; p < WP; p += 2 * w) {
+        F[p] = F[p] + F[p + w];
+        S[p] = S[p] + S[p + w];
+      }
+    }
+    residual64_finish(xs, r, t, omt, scale, F[0], S[0], H, sc);
+  }
+
+  // Cooperative form: called by every lane of the warp (wl = lane index)
+  // for the group whose point xs is; lane wl computes part wl / L of row
+  // wl mod L, and after the butterfly every lane holds its row's residual.
+  __device__ __forceinline__ void residual64_coop(const cx<double>* xs, int wl, double t,
+                                                  bool scale, cx<double>& H, double& sc) const {
+    static_assert(kCoop, "cooperative residuals: groups narrower than a warp");
+    const int r = wl & (L - 1);
+    cx<double> F;
+    float S;
+    residual64_part<WP>(xs, r, wl / L, scale, F, S);
+#pragma unroll
+    for (int o = L; o < 32; o <<= 1) {
+      cx<double> w;
+      w.re = __shfl_xor_sync(0xffffffffu, F.re, o);
+      w.im = __shfl_xor_sync(0xffffffffu, F.im, o);
+      F = F + w;
+      S = S + __shfl_xor_sync(0xffffffffu, S, o);
+    }
+    residual64_finish(xs, r, t, 1.0 - t, scale, F, S, H, sc);
+  }
+
   // The residual of row i in double-float arithmetic (mixed-precision
   // kernels): the nested Horner order of residual64 over Edf, the point read
   // as double-floats from the group's shared copy.  H is returned rounded to
   // FP32: its error is a small multiple of 2^-48 times the size of the terms
   // (the backward-error scale sc, formed as in residual64), far below the
   // tolerances the FP64 residual serves, and only the FP32 solve consumes it.
-  template <bool SCALE_T>
+  template <bool SCALE_T, int EP = 1>
   __device__ __forceinline__ void residual_df(const cdf* xs, int i, double t, cx<float>& H,
                                               float& sc) const {
-    residual_df_impl(xs, i, t, SCALE_T, H, sc);
+    if constexpr (EP > 1) {
+      static_assert(EP == WP && kCoop, "sequential parts: groups narrower than a warp");
+      residual_df_seq(xs, i, t, SCALE_T, H, sc);
+    } else {
+      residual_df_impl(xs, i, t, SCALE_T, H, sc);
+    }
   }
 
   __device__ static cdf part_sum_cdf(cdf v) {
     if constexpr (PARTS > 1) {
 #pragma unroll
-      for (int o = L; o < L * PARTS; o <<= 1) {
-        cdf w;
-        w.hr = __shfl_xor_sync(0xffffffffu, v.hr, o);
-        w.hi_ = __shfl_xor_sync(0xffffffffu, v.hi_, o);
-        w.lr = __shfl_xor_sync(0xffffffffu, v.lr, o);
-        w.li = __shfl_xor_sync(0xffffffffu, v.li, o);
-        v = cdf_add(v, w);
-      }
+      for (int o = L; o < L * PARTS; o <<= 1) v = cdf_add(v, shfl_xor_cdf(v, o));
     }
     return v;
   }
+  __device__ __forceinline__ static cdf shfl_xor_cdf(cdf v, int o) {
+    cdf w;
+    w.hr = __shfl_xor_sync(0xffffffffu, v.hr, o);
+    w.hi_ = __shfl_xor_sync(0xffffffffu, v.hi_, o);
+    w.lr = __shfl_xor_sync(0xffffffffu, v.lr, o);
+    w.li = __shfl_xor_sync(0xffffffffu, v.li, o);
+    return w;
+  }
 
-  __device__ __noinline__ void residual_df_impl(const cdf* xs, int i, double t, bool scale,
-                                                cx<float>& H, float& sc) const {
-    const int r = i & (L - 1);
-    const int part = (PARTS > 1) ? i / L : 0;
+  // partial sums of row r over part `part` of a P-way split (as residual64_part)
+  template <int P>
+  __device__ __noinline__ void residual_df_part(const cdf* xs, int r, int part, bool scale,
+                                                cdf& Fo, float& So) const {
     const cdf* e = Edf + (r < N ? r : 0);
     cdf F = part == 0 ? e[0] : cdf_zero();
     float Ssum = (scale && part == 0) ? cdf_abs_hi(e[0]) : 0.f;
 #pragma unroll 1
     for (int mm = 0;; ++mm) {
-      const int j = zigzag(mm, part);
+      const int j = zigzag<P>(mm, part);
       if (j >= N) break;
       int m = 1;
 #pragma unroll 1
@@ -406,13 +495,14 @@ struct DenseTD {
       F = cdf_fma(xj, in, F);
       if (scale) Ssum += cdf_abs_hi(xj) * ins;
     }
-    if constexpr (PARTS > 1) {
-      F = part_sum_cdf(F);
-      if (scale) {
-#pragma unroll
-        for (int o = L; o < L * PARTS; o <<= 1) Ssum += __shfl_xor_sync(0xffffffffu, Ssum, o);
-      }
-    }
+    Fo = F;
+    So = Ssum;
+  }
+
+  // H = t F + (1 - t) gamma G_r rounded to FP32, and the scale
+  __device__ __noinline__ void residual_df_finish(const cdf* xs, int r, double t, bool scale,
+                                                  cdf F, float Ssum, cx<float>& H,
+                                                  float& sc) const {
     const cdf xi = xs[r < N ? r : 0];
     const cdf xi2 = cdf_mul(xi, xi);
     const cdf one{1.f, 0.f, 0.f, 0.f};
@@ -425,6 +515,58 @@ struct DenseTD {
     } else {
       sc = 0.f;
     }
+  }
+
+  __device__ __forceinline__ void residual_df_impl(const cdf* xs, int i, double t, bool scale,
+                                                   cx<float>& H, float& sc) const {
+    const int r = i & (L - 1);
+    const int part = (PARTS > 1) ? i / L : 0;
+    cdf F;
+    float Ssum;
+    residual_df_part<PARTS>(xs, r, part, scale, F, Ssum);
+    if constexpr (PARTS > 1) {
+      F = part_sum_cdf(F);
+      if (scale) {
+#pragma unroll
+        for (int o = L; o < L * PARTS; o <<= 1) Ssum += __shfl_xor_sync(0xffffffffu, Ssum, o);
+      }
+    }
+    residual_df_finish(xs, r, t, scale, F, Ssum, H, sc);
+  }
+
+  // the WP parts one after the other, added in the butterfly's order
+  __device__ __forceinline__ void residual_df_seq(const cdf* xs, int i, double t, bool scale,
+                                                  cx<float>& H, float& sc) const {
+    const int r = i & (L - 1);
+    cdf F[WP];
+    float S[WP];
+#pragma unroll
+    for (int p = 0; p < WP; ++p) residual_df_part<WP>(xs, r, p, scale, F[p], S[p]);
+#pragma unroll
+    for (int w = 1; w < WP; w <<= 1) {
+#pragma unroll
+      for (int p = 0; p < WP; p += 2 * w) {
+        F[p] = cdf_add(F[p], F[p + w]);
+        S[p] = S[p] + S[p + w];
+      }
+    }
+    residual_df_finish(xs, r, t, scale, F[0], S[0], H, sc);
+  }
+
+  // Cooperative form (as residual64_coop)
+  __device__ __forceinline__ void residual_df_coop(const cdf* xs, int wl, double t, bool scale,
+                                                   cx<float>& H, float& sc) const {
+    static_assert(kCoop, "cooperative residuals: groups narrower than a warp");
+    const int r = wl & (L - 1);
+    cdf F;
+    float S;
+    residual_df_part<WP>(xs, r, wl / L, scale, F, S);
+#pragma unroll
+    for (int o = L; o < 32; o <<= 1) {
+      F = cdf_add(F, shfl_xor_cdf(F, o));
+      S = S + __shfl_xor_sync(0xffffffffu, S, o);
+    }
+    residual_df_finish(xs, r, t, scale, F, S, H, sc);
   }
 
   // per path: the pad entries behind the point (odd N) and behind the

@@ -64,6 +64,8 @@ struct TermEval {
   // so that the warp's lanes all work.  Otherwise one row per lane.
   static constexpr int PARTS = (L == 32 && N <= 16) ? 2 : 1;
   static constexpr int ROWL = L / PARTS;
+  // residuals are computed by each group alone (no cooperative form)
+  static constexpr bool kCoop = false;
   const TermArgs* a;
   int64_t inst;
   Group g;
@@ -246,7 +248,7 @@ struct TermEval {
     }
   }
 
-  template <bool SCALE>
+  template <bool SCALE, int EP = 1>
   __device__ __forceinline__ void residual64(const cx<double>*, int i, double t, double,
                                              cx<double>& H, double& sc) const {
     put_params<double>(t);
@@ -281,7 +283,7 @@ struct TermEval {
   // factors and coefficient (table sdf) as in residual64.  H is returned
   // rounded to FP32 (its error is a small multiple of 2^-48 times the
   // backward-error scale sc).
-  template <bool SCALE>
+  template <bool SCALE, int EP = 1>
   __device__ __forceinline__ void residual_df(const cdf*, int i, double t, cx<float>& H,
                                               float& sc) const {
     const int P = a->P, LS = a->ls;

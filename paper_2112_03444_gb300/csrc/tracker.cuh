@@ -81,7 +81,9 @@ __device__ __forceinline__ void load_vec(const cx<S>* buf, cx<R> (&x)[N]) {
   for (int k = 0; k < N; ++k) x[k] = cvt<R>(buf[k]);
 }
 
-enum : int { M_RK = 0, M_NEWTON = 1, M_REFINE = 2, M_COND = 3, M_DONE = 4, M_FETCH = 5 };
+// M_IDLE: a group without work waiting for the other groups of its warp
+// (kernels with cooperative residuals, which keep the warp together)
+enum : int { M_RK = 0, M_NEWTON = 1, M_REFINE = 2, M_COND = 3, M_DONE = 4, M_FETCH = 5, M_IDLE = 6 };
 
 // Shared memory of one lane group: pv = two pivot-row buffers of the solve,
 // acc = evaluator accumulators (term evaluator only), vd = high-precision
@@ -101,15 +103,17 @@ struct GroupMem {
                    // its dx/ds, the last prediction), 16-byte aligned
   cx<df>* vx;      // double-float kernels: the evaluator's double-float copy of
                    // vd (L + extra entries), 16-byte aligned; nullptr otherwise
+  int stride;      // bytes from one group's memory to the next group's
 };
 
 template <int L>
 __device__ __forceinline__ GroupMem make_group_mem(unsigned char* smem, int extra,
                                                    int acc_bytes = 0, int eg_bytes = 0,
                                                    int vx = 0) {
-  unsigned char* b =
-      smem + (threadIdx.x / L) * group_smem_bytes(L, extra, acc_bytes, eg_bytes, vx);
+  const int stride = group_smem_bytes(L, extra, acc_bytes, eg_bytes, vx);
+  unsigned char* b = smem + (threadIdx.x / L) * stride;
   GroupMem m;
+  m.stride = stride;
   m.pv = b;
   b += 32 * (L + 2);
   m.acc = b;
@@ -183,6 +187,17 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
   // double-float evaluation), as the mixed kernels' FP64-state phase does,
   // and always with the endgame, whose samples need FP64 accuracy
   constexpr bool XDF = std::is_same<R, df>::value;
+  // Cooperative residuals (mixed kernels with several paths per warp, see
+  // the dense evaluator): every high-precision residual the warp's groups
+  // need in an iteration is computed by the whole warp at one point of the
+  // loop (COOP).  The whole warp stays in the loop until all of its groups
+  // are out of work (M_IDLE), and that point holds the loop's only
+  // warp-wide synchronisation, so every lane meets every other lane there.
+  // The resident-launch kernels (whose groups wait for tickets on their own)
+  // compute the same partial sums in the same order group by group (EP).
+  constexpr bool COOP_EVAL = MIXED && HOM::kCoop;
+  constexpr bool COOP = COOP_EVAL && !RING;
+  constexpr int EP = COOP_EVAL ? 32 / L : 1;
   const DevSettings& s = c.s;
   cx<R>* sb = reinterpret_cast<cx<R>*>(sm.sb);
   const bool act = g.gl < N;
@@ -205,6 +220,8 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
   // ---- per-path state (identical control state in all lanes of the group)
   HOM hom = prob.hom(0);
   int64_t item = 0;
+  int64_t inst_cur = 0;    // the instance of the group's path
+  bool be_bad = false;     // COOP: the endpoint failed the backward-error test
   unsigned long long ticket = 0;  // resident launches: the claimed ticket
   (void)ticket;
   cx<double> xd = czero<double>();  // FP64 state
@@ -481,15 +498,16 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
       item = (int64_t)(ticket % c.ring_items);
     }
     if (mode == M_FETCH) {
+      bool stop = false;  // no further path for this group
       if (c.step_budget && !c.items) {
         // the budget stops new paths of the launch; started ones finish
         unsigned long long spent = 0;
         if (g.gl == 0) spent = *reinterpret_cast<volatile unsigned long long*>(c.step_total);
-        if (__shfl_sync(g.mask, spent, leader) >= c.step_budget) break;
+        stop = __shfl_sync(g.mask, spent, leader) >= c.step_budget;
       }
       unsigned long long q = 0;
-      if (RING) {
-        // item claimed above
+      if (stop || RING) {
+        // nothing to claim, or the item was claimed above
       } else if (c.spread && first_fetch) {
         // ticket = slot * blocks + block: consecutive items on different blocks
         // (and so, for the first blocks of the grid, on different SMs)
@@ -500,52 +518,58 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
         q = __shfl_sync(g.mask, q, leader);
         if (c.spread) q += (unsigned long long)gridDim.x * (blockDim.x / L);
       }
-      if (!RING) {
-        if ((int64_t)q >= total) break;
-        item = c.items ? c.items[q] : (int64_t)q;
-      }
-      const int64_t inst = item / c.paths;
-      const int64_t k_in = item - inst * c.paths;
-      const int64_t path = c.path_ids ? c.path_ids[item] : c.path_map ? c.path_map[k_in] : k_in;
-      hom = prob.hom(inst);
-      hom.init(g);  // per-path constants of the evaluator (shared memory)
-      // a path handed over by the FP32 tier resumes from its last accepted point
-      const double t0 = (!MIXED && c.t_io) ? c.t_io[item] : 0.0;
-      __syncwarp(g.mask);
-      xd = czero<double>();
-      if (act) {
-        if (t0 > 0.0) {
-          const double2 v = reinterpret_cast<const double2*>(c.x_out)[item * N + g.gl];
-          xd = mk<double>(v.x, v.y);
-        } else {
-          xd = hom.start(path, g.gl);
+      if (!RING && !stop) stop = (int64_t)q >= total;
+      if (stop) {
+        if constexpr (COOP)
+          mode = M_IDLE;
+        else
+          break;
+      } else {
+        if (!RING) item = c.items ? c.items[q] : (int64_t)q;
+        const int64_t inst = item / c.paths;
+        inst_cur = inst;
+        const int64_t k_in = item - inst * c.paths;
+        const int64_t path = c.path_ids ? c.path_ids[item] : c.path_map ? c.path_map[k_in] : k_in;
+        hom = prob.hom(inst);
+        hom.init(g);  // per-path constants of the evaluator (shared memory)
+        // a path handed over by the FP32 tier resumes from its last accepted point
+        const double t0 = (!MIXED && c.t_io) ? c.t_io[item] : 0.0;
+        __syncwarp(g.mask);
+        xd = czero<double>();
+        if (act) {
+          if (t0 > 0.0) {
+            const double2 v = reinterpret_cast<const double2*>(c.x_out)[item * N + g.gl];
+            xd = mk<double>(v.x, v.y);
+          } else {
+            xd = hom.start(path, g.gl);
+          }
         }
+        xf = cvt<float>(xd);
+        hi = !MIXED || c.start_hi;
+        t = t0 > 0.0 ? t0 : 0.0;
+        dt = s.dt_init;
+        tf = (float)t;
+        dtf = (float)s.dt_init;
+        consec = nacc = nrej = nnewt = status = 0;
+        res64 = false;
+        be = 0.f;
+        // endgame: the first sample time after the start point
+        eg_count = 0;
+        eg_c = 1;
+        eg_dnprev = 0.0;
+        eg_landing = eg_pending = eg_have = eg_sing = false;
+        eg_next = 0;
+        eg_s = s.eg_s0;
+        if (eg_on)
+          while (eg_next < s.eg_samples && 1.0 - eg_s <= t) {
+            eg_s *= s.eg_ratio;
+            ++eg_next;
+          }
+        if (t >= 1.0)
+          enter_refine();
+        else
+          begin_step();
       }
-      xf = cvt<float>(xd);
-      hi = !MIXED || c.start_hi;
-      t = t0 > 0.0 ? t0 : 0.0;
-      dt = s.dt_init;
-      tf = (float)t;
-      dtf = (float)s.dt_init;
-      consec = nacc = nrej = nnewt = status = 0;
-      res64 = false;
-      be = 0.f;
-      // endgame: the first sample time after the start point
-      eg_count = 0;
-      eg_c = 1;
-      eg_dnprev = 0.0;
-      eg_landing = eg_pending = eg_have = eg_sing = false;
-      eg_next = 0;
-      eg_s = s.eg_s0;
-      if (eg_on)
-        while (eg_next < s.eg_samples && 1.0 - eg_s <= t) {
-          eg_s *= s.eg_ratio;
-          ++eg_next;
-        }
-      if (t >= 1.0)
-        enter_refine();
-      else
-        begin_step();
     }
     if (mode == M_RK && stage == 0) {
       if (nacc + nrej >= s.max_steps) {
@@ -563,6 +587,9 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
     double te = 1.0;      // FP64-state phases
     R ter = R(1), omt = R(0);  // the time the evaluator sees, and 1 - t
     bool need64 = false;
+    // COOP: the residual this group needs at te (0 none, 1 double-float,
+    // 2 FP64, 3 double-float with the backward-error scale)
+    int res_code = 0;
     if (mode == M_RK) {
       if (HI()) {
         const double cst = (stage == 0) ? 0.0 : (stage == 3 ? 1.0 : 0.5);
@@ -586,6 +613,7 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
         ter = (R)t1;
         omt = (R)(1.0 - t1);
         need64 = MIXED || (XDF && (res64 || eg_on));
+        if (MIXED) res_code = res64 ? 2 : 1;
         if (act) put_hi(xpd, !res64);
         if (act) sm.vf[g.gl] = cvt<float>(xpd);
       } else {
@@ -593,9 +621,13 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
         omt = (R)(1.f - t1f);
         if (act) sm.vf[g.gl] = xpf;
       }
-    } else {  // M_REFINE, M_COND: at the endpoint, t = 1
+    } else {  // M_REFINE, M_COND (M_IDLE: nothing to evaluate): at the endpoint, t = 1
       need64 = (mode == M_REFINE);
-      if (act && (need64 || !MIXED)) put_hi(xd, MIXED);
+      // COOP: the backward error of a refined endpoint comes with the first
+      // condition pass (the same point)
+      const bool be_now = COOP && mode == M_COND && stage == 0;
+      if (act && (need64 || be_now || !MIXED)) put_hi(xd, MIXED);
+      if (MIXED) res_code = need64 ? 1 : be_now ? 3 : 0;
       if (act) sm.vf[g.gl] = cvt<float>(xd);
     }
     __syncwarp(g.mask);
@@ -603,6 +635,52 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
       load_vec<N, float, float>(sm.vf, x);
     } else {
       load_vec<N, double, R>(sm.vd, x);
+    }
+
+    if constexpr (COOP) {
+      // The loop's one warp-wide meeting point: leave together once every
+      // group is idle, else compute the groups' residuals one group at a
+      // time with all lanes of the warp.  A lane of the group served keeps
+      // its row's residual (FP32-rounded) and scale in its own entry of the
+      // group's scatter buffer, which is free until the solve.
+      const unsigned live = __ballot_sync(0xffffffffu, g.gl == 0 && mode != M_IDLE);
+      if (live == 0u) break;
+      const unsigned want = __ballot_sync(0xffffffffu, g.gl == 0 && res_code != 0);
+      if (want != 0u) {
+        __syncwarp(0xffffffffu);  // the groups' point copies, before other groups read them
+        unsigned rem = want;
+        while (rem != 0u) {
+          const int src = __ffs(rem) - 1;  // leader lane of the group served
+          rem &= rem - 1u;
+          const int code = __shfl_sync(0xffffffffu, res_code, src);
+          const double tG = __shfl_sync(0xffffffffu, te, src);
+          const long long iG = __shfl_sync(0xffffffffu, (long long)inst_cur, src);
+          const HOM hG = prob.hom((int64_t)iG);
+          const unsigned char* vdG =
+              reinterpret_cast<const unsigned char*>(sm.vd) + (src / L - g.wl / L) * sm.stride;
+          cx<float> hf;
+          float scf = 0.f;
+          if (code == 2) {
+            cx<double> h64;
+            double sc64;
+            hG.residual64_coop(reinterpret_cast<const cx<double>*>(vdG), g.wl, tG, false, h64,
+                               sc64);
+            hf = cvt<float>(h64);
+          } else {
+            hG.residual_df_coop(reinterpret_cast<const cdf*>(vdG), g.wl, tG, code == 3, hf, scf);
+          }
+          if ((g.wl / L) == (src / L))
+            reinterpret_cast<float4*>(sm.sb)[g.gl] = make_float4(hf.re, hf.im, scf, 0.f);
+        }
+        __syncwarp(0xffffffffu);  // every read of the point copies done
+      }
+      if (res_code == 3) {  // backward error of the refined endpoint
+        const float4 v = reinterpret_cast<const float4*>(sm.sb)[g.gl];
+        const double r = (double)cabs2(mk<float>(v.x, v.y)), sc = (double)v.z;
+        const double bei = act ? (sc > 0.0 ? r / sc : r) : 0.0;
+        be = gmaxf(g, (float)bei);
+        be_bad = !((double)be <= s.finite_tol);
+      }
     }
 
     // ---- 2. row i of [dH/dx | rhs] and the solve
@@ -623,15 +701,19 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
         const int grow = g.gl & (HOM::ROWL - 1);
         row[N] = mk<R>((grow < N && grow == stage) ? R(1) : R(0), R(0));
       } else if (need64) {
-        if (MIXED && (mode == M_REFINE || !res64)) {
+        if constexpr (COOP) {
+          const float4 v = reinterpret_cast<const float4*>(sm.sb)[g.gl];
+          row[N] = mk<R>(-v.x, -v.y);
+        } else if (MIXED && (mode == M_REFINE || !res64)) {
           cx<float> Hf;
           float sc;
-          hom.template residual_df<false>(reinterpret_cast<const cdf*>(sm.vd), g.gl, te, Hf, sc);
+          hom.template residual_df<false, EP>(reinterpret_cast<const cdf*>(sm.vd), g.gl, te, Hf,
+                                              sc);
           row[N] = cvt<R>(-Hf);
         } else {
           cx<double> H64;
           double sc;
-          hom.template residual64<false>(sm.vd, g.gl, te, 1.0 - te, H64, sc);
+          hom.template residual64<false, EP>(sm.vd, g.gl, te, 1.0 - te, H64, sc);
           row[N] = cvt<R>(-H64);
         }
       } else {
@@ -741,6 +823,10 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
         } else if (xnf > rinf_f) {
           status = ST_DIVERGED;
           mode = M_DONE;
+        } else if constexpr (COOP) {
+          mode = M_COND;  // the backward error comes with the first condition pass
+          stage = 0;
+          cond_inorm = 0.f;
         } else {
           __syncwarp(g.mask);
           if (act) put_hi(xd, MIXED);
@@ -749,8 +835,8 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
           if constexpr (MIXED) {  // double-float residual: its error is ~2^-48 sc
             cx<float> Hf;
             float scf;
-            hom.template residual_df<true>(reinterpret_cast<const cdf*>(sm.vd), g.gl, 1.0, Hf,
-                                           scf);
+            hom.template residual_df<true, EP>(reinterpret_cast<const cdf*>(sm.vd), g.gl, 1.0,
+                                               Hf, scf);
             r = (double)cabs2(Hf);
             sc = (double)scf;
           } else {
@@ -773,7 +859,10 @@ __device__ __forceinline__ void run_tracker(const PROB& prob, const LaunchCommon
           }
         }
       }
-    } else {  // M_COND
+    } else if (mode == M_COND && COOP && stage == 0 && be_bad) {
+      status = ST_FAIL_REFINE;  // the refined endpoint failed the backward-error test
+      mode = M_DONE;
+    } else if (mode == M_COND) {
       if (!sok) cond_inorm = INFINITY;
       cond_inorm =
           fmaxf(cond_inorm, gsum<L, float>(g, (act && col >= 0) ? cabs2(cvt<float>(d)) : 0.f));
