@@ -175,16 +175,11 @@ struct DenseTD {
       __syncwarp(gmask);
     }
     if constexpr (DEG == 3) {
-      // x_k x_l for k <= l in graded order, the group's lanes sharing the work
+      // x_k x_l for k <= l in graded order: row k of the triangle, lane i
+      // forming x_k x_(k+i) (no index search, no divergence)
 #pragma unroll 1
-      for (int m = i; m < S::NQ; m += L_GROUP) {
-        int k = 0, rem = m;
-        while (rem >= N - k) {
-          rem -= N - k;
-          ++k;
-        }
-        Q[m] = V[k] * V[k + rem];
-      }
+      for (int k = 0; k < N; ++k)
+        if (i < N - k) Q[S::idx2(k, k + i) - 1 - N] = V[k] * V[k + i];
       __syncwarp(gmask);
     }
     cx<R> a1[N];
