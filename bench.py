@@ -572,6 +572,7 @@ def param_legs(hc, args):
     out["triangulation4"] = dict(
         instances=I, paths=r["paths"], device_ms=r["device_ms"], wall_ms=wall * 1e3,
         systems_per_s=I / (r["device_ms"] * 1e-3), paths_per_s=r["finite"] / (r["device_ms"] * 1e-3),
+        track_ms=r["track_ms"], retrack_ms=r["escalate_ms"],
         finite=r["finite"], escalated=r["escalated"], oracle_checks=checks,
         form="one hc_track_batch, mixed precision")
     del b
