@@ -913,7 +913,7 @@ def main():
     ap.add_argument("--admission-rates", default="400,2000,8000")
     ap.add_argument("--admission-duration", type=float, default=1.0)
     ap.add_argument("--tri-instances", type=int, default=10_000)
-    ap.add_argument("--trifocal-instances", type=int, default=64)
+    ap.add_argument("--trifocal-instances", type=int, default=1000)
     ap.add_argument("--serve-rate", type=float, default=400.0,
                     help="offered requests/s of the serving leg")
     ap.add_argument("--serve-duration", type=float, default=2.0)
